@@ -1,0 +1,401 @@
+"""Benchmark: orders evaluated per second by the exhaustive search, plus the
+heuristic, over 64 groups of 10 tasks (half dominant-kernel, half
+dominant-transfer) under both device models (one and two DMA engines).
+
+One step = the whole hot path over that batch: for each of the 128 group
+evaluations, every one of the 10! = 3,628,800 orders is evaluated with the
+temporal execution model and reduced to best / worst / sum / mean with the
+first best / worst order, and the reordering heuristic (Algorithm 1) picks an
+order.  128 x 10! = 464,486,400 orders per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tm|reference]
+
+Prints one JSON line (rank 0).  `value` is device-timed with inputs resident
+in HBM; `e2e` goes through the host-pointer C ABI with host<->device copies
+inside the timed region.  `--impl reference` times the CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1806_10113_gb300 import inputs  # noqa: E402
+
+METRIC = "orderings evaluated/s (exact model, N=10/12); task groups scheduled/s at <=1% gap"
+UNIT = "orders/s"
+GROUPS, N_TASKS, SEED = 64, 10, 1
+WORKLOAD = ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
+            "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
+            "exhaustive 10! orders + heuristic per group")
+# Integer operations per evaluated order that the method needs with prefix
+# sharing: 5 per step of the recurrence (3 adds, 2 maxes) times
+# sum_{m<n} 1/m! ~ e tree nodes per leaf, plus 4 for the reduction
+# (min, max, 64-bit add).
+ALG_OPS_PER_ORDER = 5 * math.e + 4
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# Issue-limited int32 peak: 4 schedulers x 32 lanes per SM per clock.
+INT32_PEAK_TOPS = SM_COUNT * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e12
+PROFILE = os.path.join(ROOT, "profiles", "exhaustive_enum_kernel_n10_g128.md")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload(rank: int = 0):
+    return inputs.dk_dt_groups(groups=GROUPS, n=N_TASKS, seed=SEED + 1000 * rank)
+
+
+def orders_per_step(b) -> int:
+    return int(sum(math.factorial(int(n)) for n in b.sizes()))
+
+
+# ---- distributed helpers --------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend: str):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- clocks during the timed region ----------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bus_id_of(device_index: int) -> str | None:
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device_index)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ---- roofline inputs from the committed ncu summary --------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("exhaustive.cu", "tm_device.cuh", "tm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1806_10113_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per enumeration launch from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return int(m_bytes.group(1))
+
+
+# ---- CPU oracle timing ------------------------------------------------------------
+
+def oracle_sample(b, items_per_group: int, nthreads: int = 0):
+    """Times the oracle on the orders under `items_per_group` two-task
+    prefixes of every group (8! = 40,320 orders each for n = 10)."""
+    import oracle
+    groups, prefixes = [], []
+    for g in range(b.G):
+        n = int(b.sizes()[g])
+        k = 0
+        for a in range(n):
+            for c in range(n):
+                if a != c and k < items_per_group:
+                    groups.append(g)
+                    prefixes.append((a, c))
+                    k += 1
+    t0 = time.perf_counter()
+    oracle.exhaustive_prefixes(b.tasks, b.offsets, b.dma, groups, prefixes, nthreads)
+    dt = time.perf_counter() - t0
+    n_orders = sum(math.factorial(int(b.sizes()[g]) - 2) for g in groups)
+    return n_orders, dt
+
+
+def cpu_baseline(b, items_per_group: int = 2) -> dict:
+    import oracle
+    cores = oracle.hardware_threads()
+    n_orders, dt = oracle_sample(b, items_per_group)
+    return {"value": n_orders / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{items_per_group} two-task prefixes x 8! orders of each of the "
+                       f"{b.G} group evaluations ({n_orders} orders, event-driven "
+                       f"simulation per order, {cores} threads, {dt:.2f} s)")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    b = workload(0)
+    import oracle
+    cores = oracle.hardware_threads()
+    per_group = 1
+    for _ in range(args.warmup):
+        oracle_sample(b, per_group)
+    total_orders, total_s = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = oracle_sample(b, per_group)
+        total_orders += n
+        total_s += dt
+    value = total_orders / total_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (each step: the orders under one two-task "
+                   "prefix of every group evaluation)", "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step {b.G} x 8! = {b.G * math.factorial(8)} orders"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# ---- the CUDA path ----------------------------------------------------------------
+
+def run_tm(args):
+    import torch
+    from paper_1806_10113_gb300 import tm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    stream = torch.cuda.current_stream()
+
+    b = workload(rank)
+    G, T = b.G, int(b.tasks.shape[0])
+    n_orders = orders_per_step(b)
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_offsets = torch.from_numpy(b.offsets).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    d_status = torch.zeros(G, dtype=torch.int32, device=dev)
+    d_orders = torch.zeros(T, dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
+    plan = tm.Plan(b.offsets)
+    launches_per_step = plan.launches() + 1
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        tm.tm_exhaustive_batch_dev(plan, d_tasks, d_dma, d_stats, d_status, stream)
+        tm.tm_heuristic_batch_dev(d_tasks, d_offsets, G, d_dma, d_orders, d_ms, d_status, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = d_status.cpu().numpy()
+    if (status != 0).any():
+        raise RuntimeError(f"device status errors: {status}")
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    ek = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    sampler = ClockSampler(bus_id_of(local))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()                        # evict L2 between timed steps
+        plan.set_timing(*ek[k])
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.set_timing(None, None)
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    enum_ms = [a.elapsed_time(c) for a, c in ek]
+    total_s = sum(step_ms) / 1000.0
+    total_s = max_over_ranks(dist, total_s, dev)
+    all_orders = sum_over_ranks(dist, float(n_orders * K), dev)
+    value = all_orders / total_s
+
+    # end to end through the host-pointer ABI: inputs from pinned host memory,
+    # results read back every step
+    h_tasks = torch.from_numpy(b.tasks).pin_memory().numpy()
+    h_offsets = torch.from_numpy(b.offsets).pin_memory().numpy()
+    h_dma = torch.from_numpy(b.dma).pin_memory().numpy()
+    e2e_steps = max(3, min(K, 50))
+    for _ in range(2):
+        tm.tm_exhaustive_batch(h_tasks, h_offsets, h_dma)
+        tm.tm_heuristic_batch(h_tasks, h_offsets, h_dma)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st = tm.tm_exhaustive_batch(h_tasks, h_offsets, h_dma)
+        ho, hms = tm.tm_heuristic_batch(h_tasks, h_offsets, h_dma)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(dist, e2e_s, dev)
+    h2d = (2 * h_tasks.nbytes + 2 * h_dma.nbytes + h_offsets.nbytes)
+    d2h = st.nbytes + 4 * G + ho.nbytes + hms.nbytes + 4 * G
+
+    ws_total = ws
+    result = None
+    if rank == 0:
+        enum_avg_s = statistics.mean(enum_ms) / 1000.0
+        alg_ops = ALG_OPS_PER_ORDER * n_orders
+        achieved = alg_ops / enum_avg_s / 1e12
+        traffic = profiled_traffic()
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_total, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "groups": G, "orders_per_step": n_orders,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{ws_total}, no collective on the data path"},
+            "groups_per_s": G * K * ws_total / total_s,
+            "e2e": {"value": n_orders * ws_total / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": 1000 * e2e_s},
+            "gpu_launches": launches_per_step * K,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": INT32_PEAK_TOPS,
+                         "unit": "Tops/s (int32)", "frac": achieved / INT32_PEAK_TOPS,
+                         "traffic": traffic,
+                         "kernel": "enum_kernel (exhaustive enumeration)",
+                         "kernel_ms": 1000 * enum_avg_s,
+                         "ops_per_order": round(ALG_OPS_PER_ORDER, 3),
+                         "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+        if ws_total == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(b)
+        print(json.dumps(result))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["tm", "reference"], default="tm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * tm.h -- C ABI of libtm.so: the temporal execution model, exhaustive order
+ * search and task reordering heuristic of Lazaro-Munoz et al., "Improving
+ * tasks throughput on accelerators using OpenCL command concurrency"
+ * (arXiv 1806.10113), evaluated by hand-written CUDA kernels for sm_103a.
+ *
+ * THE MODEL (Sec. 4.1, Figs. 4 and 6).  A task group TG is n independent
+ * tasks; task j is an HtD transfer, a kernel K and a DtH transfer, run in
+ * that order, with durations htd_j, k_j, dth_j (int32 nanoseconds).  For an
+ * order (a permutation tau of 0..n-1), commands enter FIFO queues in that
+ * order and each starts once its queue is free and the previous stage of
+ * its own task has finished.  There is one kernel queue (no concurrent
+ * kernel execution).  With two DMA engines (Sec. 3.2, Fig. 3) HtD and DtH
+ * have their own queues and overlap at full speed; with one DMA engine
+ * (Sec. 3.2, Fig. 2) one transfer queue carries every HtD and then every
+ * DtH.  The result ("makespan") is the end of the last command.  Concurrent
+ * HtD/DtH transfers are modelled at full speed: the paper's partial-overlap
+ * slowdown (Sec. 4.2.1) gives no formula.
+ *
+ * CONVENTIONS.
+ *  - Every function returns TM_OK (0) or a negative tm_status code; on error
+ *    no output is written.  tm_strerror() names a code.
+ *  - Functions without the _dev suffix take HOST pointers, run on the
+ *    calling thread's current CUDA device and return when the results are
+ *    in the caller's buffers.  They keep no caller pointer after returning.
+ *    Their device buffers are owned by the library, one set per host thread,
+ *    reused across calls and grown when needed.
+ *  - _dev functions take DEVICE pointers and a CUDA stream (passed as
+ *    void*, NULL = legacy default stream) and are stream-ordered: they
+ *    return after enqueuing work.  Their per-group input checks run on the
+ *    device and are reported in an optional int32 status[G] array (0 or a
+ *    tm_status code); a group that fails its check gets no output.
+ *  - Ragged batches: group g owns tasks[offsets[g] .. offsets[g+1]),
+ *    offsets[0] = 0, offsets nondecreasing, 1 <= offsets[g+1]-offsets[g].
+ *    Orders are given and returned with the same layout, holding task
+ *    indices local to their group (0 .. n_g - 1).
+ *  - Input limits: durations >= 0 (else TM_ENEG); the sum of all durations
+ *    of a group <= INT32_MAX (else TM_EOVERFLOW), which bounds every time
+ *    the model produces; n <= TM_MAX_TASKS (16); exhaustive search needs
+ *    n <= TM_MAX_EXHAUSTIVE (12, so that n! < 2^32) (else TM_ETOOBIG).
+ *  - The library is thread-safe across host threads.  A tm_plan must not be
+ *    used by two launches that can run at the same time.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TM_MAX_TASKS 16
+#define TM_MAX_EXHAUSTIVE 12
+
+typedef enum tm_status {
+    TM_OK = 0,
+    TM_EINVAL = -1,     /* NULL pointer, n or G out of range, bad offsets,
+                           dma_engines not 1 or 2, order not a permutation */
+    TM_ENEG = -2,       /* a negative duration */
+    TM_EOVERFLOW = -3,  /* a group's durations sum above INT32_MAX */
+    TM_ETOOBIG = -4,    /* exhaustive search asked for n > 12 */
+    TM_ECUDA = -5,      /* a CUDA runtime call failed */
+    TM_ETIMEOUT = -6,   /* a bounded device-side wait expired */
+    TM_ENOMEM = -7      /* device or host allocation failed */
+} tm_status;
+
+/* One task (Sec. 4.1): durations of its three stages in ns.  A null stage is
+ * 0; a stage made of several commands is given as their sum.  12 bytes. */
+typedef struct tm_task {
+    int32_t htd, k, dth;
+} tm_task;
+
+/* Device model (Sec. 3.2): the number of DMA engines, 1 or 2. */
+typedef struct tm_device {
+    int32_t dma_engines;
+} tm_device;
+
+/* Result of an exhaustive search over all n! orders of one group.
+ * Ranks are lexicographic ranks of the order (rank 0 = 0,1,...,n-1); ties
+ * for best / worst go to the lowest rank.  Entries of best_order /
+ * worst_order past n are 0xFF.  72 bytes, 8-byte aligned. */
+typedef struct tm_stats {
+    int32_t best;           /* minimum makespan (ns) */
+    int32_t worst;          /* maximum makespan (ns) */
+    int64_t sum;            /* exact sum of all n! makespans */
+    double mean;            /* (double)sum / (double)n!, IEEE round-to-nearest */
+    uint64_t best_rank;
+    uint64_t worst_rank;
+    uint8_t best_order[16];
+    uint8_t worst_order[16];
+} tm_stats;
+
+/* ---- single group, host pointers --------------------------------------- */
+
+/* Makespan of one order (Sec. 4.1).  tasks[n], order[n] (a permutation of
+ * 0..n-1); writes *makespan.  1 <= n <= 16. */
+int tm_predict(const tm_task* tasks, int n, const int32_t* order,
+               const tm_device* dev, int32_t* makespan);
+
+/* Evaluates all n! orders (the brute-force search of Sec. 1 that the paper
+ * calls infeasible at run time) and reduces them to best / worst / sum /
+ * mean with the first best and worst order.  1 <= n <= 12.  `mean` may be
+ * NULL; otherwise it receives stats->mean. */
+int tm_exhaustive(const tm_task* tasks, int n, const tm_device* dev,
+                  tm_stats* stats, double* mean);
+
+/* Batch Reordering heuristic (Sec. 5.1, Algorithm 1) with these readings:
+ *  select_first_task: largest k - htd; ties -> larger dth -> lower index.
+ *  update(OT): the model run on the ordered set OT alone; t_HTD, t_K, t_DTH
+ *    are the ends of its last HtD, K and DtH.
+ *  select_next_task: minimise |(t_K - t_HTD) - htd_j| + |(t_DTH - s_j) - k_j|
+ *    with s_j = max(t_K, t_HTD + htd_j); ties -> larger k -> lower index.
+ *  select_last_tasks: with two tasks left, the completion with the smaller
+ *    makespan; ties -> the one whose last task has the smaller dth -> lower
+ *    index first.  n = 1 gives [0]; n = 2 applies select_last_tasks to both.
+ * Writes order_out[n] and, if not NULL, *makespan_out.  1 <= n <= 16. */
+int tm_heuristic(const tm_task* tasks, int n, const tm_device* dev,
+                 int32_t* order_out, int32_t* makespan_out);
+
+/* ---- ragged batches, host pointers -------------------------------------- */
+
+/* devs[G]: one device model per group.  orders / makespans as above. */
+int tm_predict_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                     const int32_t* orders, const tm_device* devs,
+                     int32_t* makespans);
+
+int tm_exhaustive_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                        const tm_device* devs, tm_stats* stats);
+
+int tm_heuristic_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                       const tm_device* devs, int32_t* orders_out,
+                       int32_t* makespans_out /* may be NULL */);
+
+/* ---- ragged batches, device pointers, stream-ordered --------------------- */
+
+int tm_predict_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                         int G, const int32_t* d_orders,
+                         const tm_device* d_devs, int32_t* d_makespans,
+                         int32_t* d_status /* may be NULL */, void* stream);
+
+int tm_heuristic_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                           int G, const tm_device* d_devs,
+                           int32_t* d_orders_out,
+                           int32_t* d_makespans_out /* may be NULL */,
+                           int32_t* d_status /* may be NULL */, void* stream);
+
+/* An exhaustive-search plan fixes the group sizes of a batch and the work
+ * decomposition over them; it owns the device work list and the per-group
+ * reduction words.  Creating it checks sizes (TM_EINVAL, TM_ETOOBIG) and
+ * allocates device memory on the current device; executing it allocates
+ * nothing.  h_offsets: host array of G + 1 offsets. */
+typedef struct tm_plan tm_plan;
+
+int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
+void tm_plan_destroy(tm_plan* plan);
+
+/* Runs the exhaustive search of every group of the plan.  d_tasks must use
+ * the plan's offsets; d_stats[G].  Stream-ordered; launches of one plan must
+ * not overlap. */
+int tm_exhaustive_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
+                            const tm_device* d_devs, tm_stats* d_stats,
+                            int32_t* d_status /* may be NULL */, void* stream);
+
+/* Number of kernel launches one tm_exhaustive_batch_dev call enqueues. */
+int tm_plan_launches(const tm_plan* plan);
+
+/* Optional timing hook: cudaEvent_t handles (passed as void*, created by the
+ * caller with timing enabled) that every later tm_exhaustive_batch_dev call
+ * on this plan records on its stream immediately before and after its
+ * enumeration kernel.  NULL, NULL turns it off.  The plan does not own the
+ * events; the caller keeps them alive while the hook is set. */
+int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
+
+/* ---- misc ---------------------------------------------------------------- */
+
+const char* tm_strerror(int code);
+
+/* Library version, e.g. "tm 0.1 sm_103a". */
+const char* tm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H */

@@ -75,9 +75,12 @@ def _load():
         lib.orc_heuristic_batch.argtypes = [P(OrcTask), P(ctypes.c_int32), ctypes.c_int,
                                             P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32),
                                             P(ctypes.c_int64)]
+        lib.orc_exhaustive_prefixes.argtypes = [P(OrcTask), P(ctypes.c_int32), P(ctypes.c_int32),
+                                                P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, P(OrcStats)]
         lib.orc_hardware_threads.argtypes = []
         for f in ("orc_predict", "orc_exhaustive", "orc_exhaustive_batch", "orc_heuristic",
-                  "orc_heuristic_batch", "orc_hardware_threads"):
+                  "orc_heuristic_batch", "orc_hardware_threads", "orc_exhaustive_prefixes"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -149,6 +152,28 @@ def exhaustive_batch(tasks, offsets, dma_engines, nthreads: int = 0) -> list:
                                       _ptr(dma, ctypes.c_int32), int(nthreads), out)
     _check(rc, "exhaustive_batch")
     return [_stats_dict(out[g], int(off[g + 1] - off[g])) for g in range(G)]
+
+
+def exhaustive_prefixes(tasks, offsets, dma_engines, item_group, item_prefix,
+                        nthreads: int = 0) -> list:
+    """Statistics of the orders under fixed prefixes (bounded timing samples).
+
+    item_group[i] is a group index; item_prefix[i] the first positions of
+    every order enumerated for item i (all items share one prefix length)."""
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    dma = np.ascontiguousarray(np.broadcast_to(np.asarray(dma_engines, dtype=np.int32), (G,)))
+    grp = np.ascontiguousarray(np.asarray(item_group, dtype=np.int32))
+    pre = np.ascontiguousarray(np.asarray(item_prefix, dtype=np.int32).reshape(grp.shape[0], -1))
+    plen = pre.shape[1]
+    out = (OrcStats * max(grp.shape[0], 1))()
+    rc = _load().orc_exhaustive_prefixes(_ptr(t, OrcTask), _ptr(off, ctypes.c_int32),
+                                         _ptr(dma, ctypes.c_int32), _ptr(grp, ctypes.c_int32),
+                                         _ptr(pre, ctypes.c_int32), plen, grp.shape[0],
+                                         int(nthreads), out)
+    _check(rc, "exhaustive_prefixes")
+    return [_stats_dict(out[i], int(off[grp[i] + 1] - off[grp[i]])) for i in range(grp.shape[0])]
 
 
 def heuristic(tasks, dma_engines: int):

@@ -181,6 +181,41 @@ struct Partial {
     std::vector<int32_t> best_order, worst_order;
 };
 
+/* Lexicographic rank of the first order that starts with prefix[0..plen). */
+uint64_t prefix_rank(const int32_t* prefix, int plen, int n)
+{
+    std::vector<char> used(n, 0);
+    uint64_t rank = 0;
+    for (int i = 0; i < plen; ++i) {
+        int smaller = 0;
+        for (int e = 0; e < prefix[i]; ++e) smaller += !used[e];
+        rank += (uint64_t)smaller * factorial(n - 1 - i);
+        used[prefix[i]] = 1;
+    }
+    return rank;
+}
+
+/* Every order that starts with prefix[0..plen), in lexicographic order. */
+Partial search_prefix(const orc_task* tasks, int n, int dma, const int32_t* prefix,
+                      int plen)
+{
+    Partial r;
+    std::vector<int32_t> p(prefix, prefix + plen);
+    std::vector<char> used(n, 0);
+    for (int i = 0; i < plen; ++i) used[prefix[i]] = 1;
+    for (int e = 0; e < n; ++e)
+        if (!used[e]) p.push_back(e);
+    uint64_t rank = prefix_rank(prefix, plen, n);
+    do {
+        int64_t ms = simulate(tasks, n, p.data(), dma, nullptr);
+        r.sum += ms;
+        if (ms < r.best) { r.best = ms; r.best_rank = rank; r.best_order = p; }
+        if (ms > r.worst) { r.worst = ms; r.worst_rank = rank; r.worst_order = p; }
+        ++rank;
+    } while (std::next_permutation(p.begin() + plen, p.end()));
+    return r;
+}
+
 Partial search(const orc_task* tasks, int n, int dma, int first)
 {
     Partial r;
@@ -415,6 +450,37 @@ int orc_exhaustive_batch(const orc_task* tasks, const int32_t* offsets, int G,
         }
         fill_stats(acc, n, out + g);
     }
+    return 0;
+}
+
+int orc_exhaustive_prefixes(const orc_task* tasks, const int32_t* offsets,
+                            const int32_t* dma_engines, const int32_t* item_group,
+                            const int32_t* item_prefix, int plen, int nitems,
+                            int nthreads, orc_stats* out)
+{
+    if (!tasks || !offsets || !dma_engines || !item_group || !out || nitems < 0 ||
+        plen < 0 || (plen > 0 && !item_prefix))
+        return -1;
+    for (int i = 0; i < nitems; ++i) {
+        int g = item_group[i];
+        int n = offsets[g + 1] - offsets[g];
+        if (n < 1 || n > 12 || plen > n) return -1;
+        if (dma_engines[g] != 1 && dma_engines[g] != 2) return -1;
+        std::vector<char> seen(n, 0);
+        for (int j = 0; j < plen; ++j) {
+            int e = item_prefix[plen * i + j];
+            if (e < 0 || e >= n || seen[e]) return -1;
+            seen[e] = 1;
+        }
+    }
+    parallel_for(nitems, nthreads, [&](int i) {
+        int g = item_group[i];
+        int n = offsets[g + 1] - offsets[g];
+        Partial r = search_prefix(tasks + offsets[g], n, dma_engines[g],
+                                  item_prefix + plen * i, plen);
+        fill_stats(r, n, out + i);
+        out[i].mean = (double)r.sum / (double)factorial(n - plen);
+    });
     return 0;
 }
 

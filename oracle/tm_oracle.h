@@ -58,6 +58,16 @@ int orc_exhaustive_batch(const orc_task* tasks, const int32_t* offsets, int G,
                          const int32_t* dma_engines, int nthreads,
                          orc_stats* out);
 
+/* Bounded samples for timing: item i enumerates, lexicographically, every
+ * order of group item_group[i] that starts with the `plen` tasks
+ * item_prefix[plen*i .. plen*i+plen) (distinct, in range).  out[i] holds
+ * that subtree's best / worst / sum (ranks are global lexicographic ranks;
+ * mean is sum / (n - plen)!).  Items run on `nthreads` host threads. */
+int orc_exhaustive_prefixes(const orc_task* tasks, const int32_t* offsets,
+                            const int32_t* dma_engines, const int32_t* item_group,
+                            const int32_t* item_prefix, int plen, int nitems,
+                            int nthreads, orc_stats* out);
+
 /* Batch Reordering heuristic (Sec. 5.1, Algorithm 1) under the readings
  * H1-H5 documented in tm_oracle.cpp.  n in [1, 16].  Writes the order and
  * its simulated makespan. */

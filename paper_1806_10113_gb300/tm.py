@@ -1,0 +1,280 @@
+"""ctypes binding of libtm.so (declared in include/tm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the model runs in the library's CUDA
+kernels.  There is no fallback; if libtm.so is missing or a call fails, the
+call raises.
+
+Host-pointer calls take array-likes (tasks as int32 [T, 3]: HtD, K, DtH in
+ns) and return numpy arrays.  ``*_dev`` calls take CUDA tensors (anything
+with ``data_ptr()``; PyTorch is the intended provider) and an optional
+stream (a ``torch.cuda.Stream``, a raw handle, or None for the current
+PyTorch stream if torch is loaded, else the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtm.so")
+
+TM_MAX_TASKS = 16
+TM_MAX_EXHAUSTIVE = 12
+
+STATS_DTYPE = np.dtype([
+    ("best", "<i4"), ("worst", "<i4"), ("sum", "<i8"), ("mean", "<f8"),
+    ("best_rank", "<u8"), ("worst_rank", "<u8"),
+    ("best_order", "u1", (16,)), ("worst_order", "u1", (16,)),
+], align=True)
+assert STATS_DTYPE.itemsize == 72
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TMError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class _Task(ctypes.Structure):
+    _fields_ = [("htd", ctypes.c_int32), ("k", ctypes.c_int32), ("dth", ctypes.c_int32)]
+
+
+class _Device(ctypes.Structure):
+    _fields_ = [("dma_engines", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_SIGS = {
+    "tm_predict": [_vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_exhaustive": [_vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_heuristic": [_vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_predict_batch": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_exhaustive_batch": [_vp, _vp, ctypes.c_int, _vp, _vp],
+    "tm_heuristic_batch": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_predict_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "tm_heuristic_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "tm_plan_create": [_vp, ctypes.c_int, ctypes.POINTER(_vp)],
+    "tm_plan_destroy": [_vp],
+    "tm_plan_launches": [_vp],
+    "tm_plan_set_timing": [_vp, _vp, _vp],
+    "tm_exhaustive_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tm_strerror": [ctypes.c_int],
+    "tm_version": [],
+}
+_RESTYPE = {"tm_plan_destroy": None, "tm_strerror": ctypes.c_char_p,
+            "tm_version": ctypes.c_char_p}
+
+
+def lib():
+    """Loads libtm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1806_10113_gb300.build`")
+            h = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                f = getattr(h, name)
+                f.argtypes = args
+                f.restype = _RESTYPE.get(name, ctypes.c_int)
+            _lib = h
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().tm_strerror(int(code)).decode()
+
+
+def version() -> str:
+    return lib().tm_version().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise TMError(rc, where)
+
+
+# ---- marshalling helpers ------------------------------------------------------
+
+def _tasks(tasks) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 3))
+    return a
+
+
+def _devs(dma, G: int) -> np.ndarray:
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(dma, dtype=np.int32), (G,)))
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def stats_to_dicts(stats: np.ndarray, sizes) -> list:
+    out = []
+    for s, n in zip(stats, sizes):
+        n = int(n)
+        out.append({
+            "best": int(s["best"]), "worst": int(s["worst"]), "sum": int(s["sum"]),
+            "mean": float(s["mean"]), "best_rank": int(s["best_rank"]),
+            "worst_rank": int(s["worst_rank"]),
+            "best_order": [int(x) for x in s["best_order"][:n]],
+            "worst_order": [int(x) for x in s["worst_order"][:n]],
+        })
+    return out
+
+
+# ---- single group, host pointers ---------------------------------------------
+
+def tm_predict(tasks, order, dma_engines: int) -> int:
+    t = _tasks(tasks)
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    out = np.zeros(1, dtype=np.int32)
+    _check(lib().tm_predict(_p(t), t.shape[0], _p(o), _p(dev), _p(out)), "tm_predict")
+    return int(out[0])
+
+
+def tm_exhaustive(tasks, dma_engines: int) -> dict:
+    t = _tasks(tasks)
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    st = np.zeros(1, dtype=STATS_DTYPE)
+    mean = ctypes.c_double(0.0)
+    _check(lib().tm_exhaustive(_p(t), t.shape[0], _p(dev), _p(st), ctypes.byref(mean)),
+           "tm_exhaustive")
+    d = stats_to_dicts(st, [t.shape[0]])[0]
+    assert d["mean"] == mean.value
+    return d
+
+
+def tm_heuristic(tasks, dma_engines: int):
+    t = _tasks(tasks)
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    order = np.zeros(max(t.shape[0], 1), dtype=np.int32)
+    ms = np.zeros(1, dtype=np.int32)
+    _check(lib().tm_heuristic(_p(t), t.shape[0], _p(dev), _p(order), _p(ms)), "tm_heuristic")
+    return [int(x) for x in order[:t.shape[0]]], int(ms[0])
+
+
+# ---- ragged batches, host pointers --------------------------------------------
+
+def tm_predict_batch(tasks, offsets, orders, dma) -> np.ndarray:
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(-1))
+    dev = _devs(dma, G)
+    out = np.zeros(max(G, 1), dtype=np.int32)
+    _check(lib().tm_predict_batch(_p(t), _p(off), G, _p(o), _p(dev), _p(out)),
+           "tm_predict_batch")
+    return out[:G]
+
+
+def tm_exhaustive_batch(tasks, offsets, dma) -> np.ndarray:
+    """Returns a structured array of STATS_DTYPE, one row per group."""
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    dev = _devs(dma, G)
+    st = np.zeros(max(G, 1), dtype=STATS_DTYPE)
+    _check(lib().tm_exhaustive_batch(_p(t), _p(off), G, _p(dev), _p(st)),
+           "tm_exhaustive_batch")
+    return st[:G]
+
+
+def tm_heuristic_batch(tasks, offsets, dma):
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    dev = _devs(dma, G)
+    orders = np.zeros(max(t.shape[0], 1), dtype=np.int32)
+    ms = np.zeros(max(G, 1), dtype=np.int32)
+    _check(lib().tm_heuristic_batch(_p(t), _p(off), G, _p(dev), _p(orders), _p(ms)),
+           "tm_heuristic_batch")
+    return orders[:t.shape[0]], ms[:G]
+
+
+# ---- ragged batches, device pointers, stream-ordered ---------------------------
+
+def tm_predict_batch_dev(d_tasks, d_offsets, G: int, d_orders, d_devs, d_makespans,
+                         d_status=None, stream=None):
+    _check(lib().tm_predict_batch_dev(_dptr(d_tasks), _dptr(d_offsets), int(G), _dptr(d_orders),
+                                      _dptr(d_devs), _dptr(d_makespans), _dptr(d_status),
+                                      _stream(stream)), "tm_predict_batch_dev")
+
+
+def tm_heuristic_batch_dev(d_tasks, d_offsets, G: int, d_devs, d_orders_out,
+                           d_makespans_out=None, d_status=None, stream=None):
+    _check(lib().tm_heuristic_batch_dev(_dptr(d_tasks), _dptr(d_offsets), int(G), _dptr(d_devs),
+                                        _dptr(d_orders_out), _dptr(d_makespans_out),
+                                        _dptr(d_status), _stream(stream)),
+           "tm_heuristic_batch_dev")
+
+
+class Plan:
+    """Owns a tm_plan (exhaustive search over a fixed set of group sizes)."""
+
+    def __init__(self, offsets):
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        self.G = off.shape[0] - 1
+        self.offsets = off
+        h = ctypes.c_void_p()
+        _check(lib().tm_plan_create(_p(off), self.G, ctypes.byref(h)), "tm_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def launches(self) -> int:
+        return int(lib().tm_plan_launches(self._h))
+
+    def set_timing(self, event_before=None, event_after=None):
+        """Records two CUDA events (e.g. torch.cuda.Event(enable_timing=True))
+        around the enumeration kernel of every later launch; None turns it off."""
+        h = lambda e: None if e is None else ctypes.c_void_p(int(getattr(e, "cuda_event", e)))
+        _check(lib().tm_plan_set_timing(self._h, h(event_before), h(event_after)),
+               "tm_plan_set_timing")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().tm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_exhaustive_batch_dev(plan: Plan, d_tasks, d_devs, d_stats, d_status=None, stream=None):
+    """d_stats: a device buffer of plan.G * 72 bytes (STATS_DTYPE rows)."""
+    _check(lib().tm_exhaustive_batch_dev(plan.handle, _dptr(d_tasks), _dptr(d_devs),
+                                         _dptr(d_stats), _dptr(d_status), _stream(stream)),
+           "tm_exhaustive_batch_dev")

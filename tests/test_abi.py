@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports every function tm.h declares.
+
+These run without a GPU: besides symbol checks they only exercise argument
+checks that the library performs on the host before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1806_10113_gb300 import build as tmbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tm():
+    tmbuild.build()
+    from paper_1806_10113_gb300 import tm as tmmod
+    return tmmod
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ["tm_predict", "tm_exhaustive", "tm_heuristic", "tm_predict_batch",
+              "tm_exhaustive_batch", "tm_heuristic_batch", "tm_predict_batch_dev",
+              "tm_heuristic_batch_dev", "tm_exhaustive_batch_dev", "tm_plan_create",
+              "tm_plan_destroy", "tm_strerror"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(tm):
+    h = ctypes.CDLL(tm.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(h, name), name
+
+
+def test_binding_names_match_header(tm):
+    for name in declared_functions():
+        if name.startswith("tm_plan_") or name in ("tm_strerror", "tm_version"):
+            continue
+        assert hasattr(tm, name), name
+
+
+def test_strerror_and_version(tm):
+    assert tm.strerror(0) == "ok"
+    assert "negative" in tm.strerror(-2)
+    assert tm.version().startswith("tm ")
+
+
+def test_tm_stats_layout_matches_numpy_dtype(tm):
+    assert tm.STATS_DTYPE.itemsize == 72
+    assert tm.STATS_DTYPE.fields["best_order"][1] == 40
+
+
+@pytest.mark.parametrize("bad,code", [
+    ([[1, -1, 0]], -2),                                  # negative duration
+    ([[2**30, 2**30, 0]], -3),                           # duration sum above INT32_MAX
+])
+def test_host_side_rejections(tm, bad, code):
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_predict(bad, [0], 2)
+    assert e.value.code == code
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_heuristic(bad, 2)
+    assert e.value.code == code
+
+
+def test_host_side_rejections_shape_and_model(tm):
+    t = [[1, 2, 3], [4, 5, 6]]
+    for call, code in [
+        (lambda: tm.tm_predict(t, [0, 0], 2), -1),          # not a permutation
+        (lambda: tm.tm_predict(t, [0, 1], 3), -1),          # bad DMA engine count
+        (lambda: tm.tm_exhaustive(np.ones((13, 3)), 2), -4),  # n > 12
+        (lambda: tm.tm_heuristic(np.ones((17, 3)), 2), -1),  # n > 16
+        (lambda: tm.tm_predict_batch(t, [0, 2, 2], [0, 1], 2), -1),  # empty group
+        (lambda: tm.tm_exhaustive_batch(t, [1, 2], 2), -1),  # offsets[0] != 0
+    ]:
+        with pytest.raises(tm.TMError) as e:
+            call()
+        assert e.value.code == code
+
+
+def test_plan_rejects_sizes_without_gpu(tm):
+    with pytest.raises(tm.TMError) as e:
+        tm.Plan([0, 13])
+    assert e.value.code == -4

@@ -1,0 +1,258 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Makespans, sums, best / worst values and ranks are integers and must match
+exactly; the mean is the same IEEE expression on both sides and must match
+bit for bit.  At full workload sizes (64 groups of 10 tasks, 12-task groups)
+the oracle cannot enumerate every order in seconds, so those tests check
+every reported order with the oracle, sample ranks, and run the full oracle
+on a few groups.
+"""
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10113_gb300 import build as tmbuild
+from paper_1806_10113_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tm():
+    tmbuild.build()
+    from paper_1806_10113_gb300 import tm as tmmod
+    return tmmod
+
+
+def lex_rank(order):
+    n, rank, rest = len(order), 0, sorted(order)
+    for i, e in enumerate(order):
+        c = rest.index(e)
+        rank += c * math.factorial(n - 1 - i)
+        rest.pop(c)
+    return rank
+
+
+def unrank(rank, n):
+    rest, out = list(range(n)), []
+    for i in range(n):
+        f = math.factorial(n - 1 - i)
+        out.append(rest.pop(rank // f))
+        rank %= f
+    return out
+
+
+def assert_stats_equal(gpu, orc, where=""):
+    for k in ("best", "worst", "sum", "best_rank", "worst_rank", "best_order", "worst_order"):
+        assert gpu[k] == orc[k], (where, k, gpu[k], orc[k])
+    assert gpu["mean"] == orc["mean"], (where, gpu["mean"], orc["mean"])
+
+
+# ---- predict ----------------------------------------------------------------
+
+def test_predict_paper_benchmarks_golden(tm):
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "bk_table3_orders.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    for bk, dma, order, ms in rows:
+        tasks = inputs.table2_tasks(inputs.TABLE3[bk], unit_ns=1_000_000)
+        assert tm.tm_predict(tasks, [int(x) for x in order.split(",")], int(dma)) == \
+            int(ms) * 1_000_000
+
+
+def test_predict_ragged_random_vs_oracle(tm):
+    rng = random.Random(3)
+    sizes = [rng.randint(1, 16) for _ in range(300)] + [1, 16, 16]
+    b = inputs.random_groups(3, sizes, hi=50_000_000)
+    orders = []
+    for g in range(b.G):
+        o = list(range(sizes[g]))
+        rng.shuffle(o)
+        orders += o
+    got = tm.tm_predict_batch(b.tasks, b.offsets, orders, b.dma)
+    for g in range(b.G):
+        o = orders[b.offsets[g]:b.offsets[g + 1]]
+        assert got[g] == oracle.predict(b.group(g), o, int(b.dma[g])), g
+
+
+# ---- exhaustive ---------------------------------------------------------------
+
+@pytest.mark.parametrize("dma", [1, 2])
+def test_exhaustive_every_size_up_to_8(tm, dma):
+    for n in range(1, 9):
+        for seed in range(4):
+            t = inputs.random_groups(100 * n + seed, [n], hi=3_000_000).tasks
+            assert_stats_equal(tm.tm_exhaustive(t, dma), oracle.exhaustive(t, dma), (n, seed))
+
+
+@pytest.mark.parametrize("dma", [1, 2])
+def test_exhaustive_ties_pick_first_rank(tm, dma):
+    """Small integer durations and identical tasks make many orders tie; the
+    first (lowest-rank) best and worst must still agree."""
+    cases = [inputs.random_small(s, n, 0, 3).tasks for s, n in
+             [(1, 5), (2, 6), (3, 7), (4, 8), (5, 9)]]
+    cases += [np.tile(np.asarray([[5, 7, 3]], dtype=np.int32), (n, 1)) for n in (5, 8)]
+    cases += [np.zeros((7, 3), dtype=np.int32)]
+    for i, t in enumerate(cases):
+        assert_stats_equal(tm.tm_exhaustive(t, dma), oracle.exhaustive(t, dma), i)
+
+
+def test_exhaustive_ragged_batch_vs_oracle(tm):
+    rng = random.Random(8)
+    sizes = [rng.randint(1, 9) for _ in range(60)]
+    b = inputs.random_groups(8, sizes, hi=4_000_000)
+    got = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), sizes)
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(got[g], ref[g], g)
+
+
+def test_exhaustive_small_case_six_tasks(tm):
+    """One group of 6 tasks, durations U[50k, 2M] ns, seed 0, both models."""
+    b = inputs.single_group_uniform(n=6, seed=0)
+    for dma in (2, 1):
+        assert_stats_equal(tm.tm_exhaustive(b.tasks, dma), oracle.exhaustive(b.tasks, dma))
+
+
+def test_exhaustive_ten_tasks_full_oracle(tm):
+    """Four groups of 10 tasks (DK and DT, both models), all 3,628,800 orders
+    on both sides."""
+    full = inputs.dk_dt_groups(groups=64, n=10, seed=1)
+    pick = [0, 32, 64, 96]
+    b = inputs.make_batch([full.group(g) for g in pick], full.dma[pick])
+    got = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), b.sizes())
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(got[g], ref[g], g)
+
+
+def check_reported_orders(tm, b, stats, samples=64, seed=0):
+    """Every reported order and a sample of ranks, checked with the oracle."""
+    rng = random.Random(seed)
+    for g in range(b.G):
+        t, n, dma, s = b.group(g), int(b.sizes()[g]), int(b.dma[g]), stats[g]
+        assert s["best_order"] == unrank(s["best_rank"], n)
+        assert s["worst_order"] == unrank(s["worst_rank"], n)
+        assert oracle.predict(t, s["best_order"], dma) == s["best"]
+        assert oracle.predict(t, s["worst_order"], dma) == s["worst"]
+        nf = math.factorial(n)
+        assert s["mean"] == float(s["sum"]) / float(nf)
+        assert s["best"] * nf <= s["sum"] <= s["worst"] * nf
+        for _ in range(samples):
+            r = rng.randrange(nf)
+            ms = oracle.predict(t, unrank(r, n), dma)
+            assert s["best"] <= ms <= s["worst"]
+            assert ms != s["best"] or r >= s["best_rank"]
+            assert ms != s["worst"] or r >= s["worst_rank"]
+
+
+def test_exhaustive_full_size_sixty_four_groups(tm):
+    """64 groups of 10 tasks (half DK, half DT) under both models, the bench
+    workload, with the bench's launch path (tm_exhaustive_batch)."""
+    b = inputs.dk_dt_groups(groups=64, n=10, seed=1)
+    stats = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), b.sizes())
+    check_reported_orders(tm, b, stats, samples=32)
+    # the paper's heuristic can never beat the exhaustive best
+    _, hms = tm.tm_heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert all(hms[g] >= stats[g]["best"] for g in range(b.G))
+
+
+def test_exhaustive_twelve_tasks_sampled(tm):
+    b = inputs.half_dk_half_dt(groups=2, n=12, seed=3, models=(2, 1))
+    stats = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), b.sizes())
+    check_reported_orders(tm, b, stats, samples=256)
+
+
+def test_exhaustive_duration_sum_at_int32_limit(tm):
+    """The largest admissible group: durations sum to exactly INT32_MAX."""
+    t = np.asarray([[300_000_000, 100_000_000, 200_000_000]] * 3 +
+                   [[1, 0, 0], [50_000_000, 0, 0]], dtype=np.int64)
+    t[-1, 1] += (2**31 - 1) - int(t.sum())
+    assert int(t.sum()) == 2**31 - 1
+    t = t.astype(np.int32)
+    for dma in (1, 2):
+        assert_stats_equal(tm.tm_exhaustive(t, dma), oracle.exhaustive(t, dma))
+    t2 = t.copy()
+    t2[0, 0] += 1
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_exhaustive(t2, 2)
+    assert e.value.code == -3
+
+
+def test_plan_reuse_gives_identical_results(tm):
+    b = inputs.random_groups(21, [5, 9, 7, 3, 8], hi=6_000_000)
+    first = tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma)
+    second = tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma)
+    assert first.tobytes() == second.tobytes()
+
+
+# ---- heuristic -------------------------------------------------------------------
+
+@pytest.mark.parametrize("dma", [1, 2])
+def test_heuristic_orders_match_oracle(tm, dma):
+    rng = random.Random(40 + dma)
+    sizes = [rng.randint(1, 16) for _ in range(400)] + list(range(1, 17))
+    his = [rng.choice([5, 1000, 5_000_000]) for _ in sizes]
+    groups = []
+    for g, (n, hi) in enumerate(zip(sizes, his)):
+        r = inputs.group_stream(777 + dma, g)
+        groups.append([inputs.uniform_task(r, (0, hi), (0, hi), (0, hi)) for _ in range(n)])
+    b = inputs.make_batch(groups, [dma] * len(groups))
+    orders, ms = tm.tm_heuristic_batch(b.tasks, b.offsets, b.dma)
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert (orders == ref_orders).all()
+    assert (ms.astype(np.int64) == ref_ms).all()
+
+
+def test_heuristic_worked_example(tm):
+    t3 = inputs.table2_tasks(["T0", "T7", "T5"], 1_000_000)
+    assert tm.tm_heuristic(t3, 2) == ([0, 2, 1], 18_000_000)
+    assert tm.tm_heuristic(t3, 1) == ([0, 2, 1], 19_000_000)
+
+
+# ---- device-pointer entry points ----------------------------------------------------
+
+def test_dev_entry_points_and_status(tm):
+    import torch
+    dev = torch.device("cuda")
+    b = inputs.random_groups(55, [6, 4, 9, 2, 7], hi=5_000_000)
+    tasks = b.tasks.copy()
+    tasks[b.offsets[1], 1] = -5                         # group 1: negative duration
+    dma = b.dma.copy()
+    dma[3] = 3                                          # group 3: bad model
+    d_tasks = torch.from_numpy(tasks).to(dev)
+    d_off = torch.from_numpy(b.offsets).to(dev)
+    d_dma = torch.from_numpy(dma).to(dev)
+    G = b.G
+    plan = tm.Plan(b.offsets)
+    d_stats = torch.zeros(G * 72, dtype=torch.uint8, device=dev)
+    d_status = torch.full((G,), 99, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        tm.tm_exhaustive_batch_dev(plan, d_tasks, d_dma, d_stats, d_status)
+        torch.cuda.synchronize()
+        st = d_stats.cpu().numpy().view(tm.STATS_DTYPE)
+        status = d_status.cpu().numpy()
+        assert list(status) == [0, -2, 0, -1, 0]
+        got = tm.stats_to_dicts(st, b.sizes())
+        for g in (0, 2, 4):
+            assert_stats_equal(got[g], oracle.exhaustive(b.group(g), int(b.dma[g])), g)
+    d_orders = torch.zeros(b.tasks.shape[0], dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
+    tm.tm_heuristic_batch_dev(d_tasks, d_off, G, d_dma, d_orders, d_ms, d_status)
+    torch.cuda.synchronize()
+    assert list(d_status.cpu().numpy()) == [0, -2, 0, -1, 0]
+    for g in (0, 2, 4):
+        o, ms = oracle.heuristic(b.group(g), int(b.dma[g]))
+        assert list(d_orders.cpu().numpy()[b.offsets[g]:b.offsets[g + 1]]) == o
+        assert int(d_ms[g]) == ms
+    ident = torch.from_numpy(np.concatenate([np.arange(n) for n in b.sizes()]).astype(np.int32))
+    ident[0] = 1                                        # group 0: not a permutation
+    tm.tm_predict_batch_dev(d_tasks, d_off, G, ident.to(dev), d_dma, d_ms, d_status)
+    torch.cuda.synchronize()
+    assert list(d_status.cpu().numpy()) == [-1, -2, 0, -1, 0]
+    assert int(d_ms[2]) == oracle.predict(b.group(2), list(range(9)), int(b.dma[2]))
+    plan.close()

@@ -327,3 +327,21 @@ def test_heuristic_beats_mean_on_paper_benchmarks():
         for dma in (1, 2):
             _, ms = oracle.heuristic(t, dma)
             assert ms <= oracle.exhaustive(t, dma)["mean"], (bk, dma)
+
+
+def test_prefix_samples_partition_the_exhaustive_search():
+    """Subtrees under every one- and two-task prefix combine to the full
+    search (same best / worst ranks, same sum)."""
+    b = inputs.random_groups(9, [6, 5], hi=1000)
+    for g in range(b.G):
+        n = int(b.sizes()[g])
+        full = oracle.exhaustive(b.group(g), int(b.dma[g]))
+        for plen in (1, 2):
+            prefixes = [p for p in itertools.permutations(range(n), plen)]
+            parts = oracle.exhaustive_prefixes(b.tasks, b.offsets, b.dma, [g] * len(prefixes),
+                                               prefixes)
+            assert sum(p["sum"] for p in parts) == full["sum"]
+            best = min(parts, key=lambda p: (p["best"], p["best_rank"]))
+            worst = min(parts, key=lambda p: (-p["worst"], p["worst_rank"]))
+            assert (best["best"], best["best_rank"]) == (full["best"], full["best_rank"])
+            assert (worst["worst"], worst["worst_rank"]) == (full["worst"], full["worst_rank"])
