@@ -63,7 +63,9 @@ typedef enum tm_status {
     TM_ETOOBIG = -4,    /* exhaustive search asked for n > 12 */
     TM_ECUDA = -5,      /* a CUDA runtime call failed */
     TM_ETIMEOUT = -6,   /* a bounded device-side wait expired */
-    TM_ENOMEM = -7      /* device or host allocation failed */
+    TM_ENOMEM = -7,     /* device or host allocation failed */
+    TM_ECAPACITY = -8   /* batch larger than tm_exhaustive_batch_noalloc's
+                           fixed working memory */
 } tm_status;
 
 /* One task (Sec. 4.1): durations of its three stages in ns.  A null stage is
@@ -172,6 +174,36 @@ int tm_plan_launches(const tm_plan* plan);
  * enumeration kernel.  NULL, NULL turns it off.  The plan does not own the
  * events; the caller keeps them alive while the hook is set. */
 int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
+
+/* ---- exhaustive search without any allocation ---------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: a caller whose GPU memory is all
+ * reserved by another allocator (for example a framework's caching pool),
+ * or one that cannot afford cudaMalloc / cudaFree (cudaFree waits for the
+ * whole device) where it runs.  tm_plan_create allocates; this call does
+ * not.  It computes the same results as tm_exhaustive_batch_dev, bit for
+ * bit, with its working memory in one fixed device array inside libtm.so
+ * (a few tens of KB, held by every GPU that loads the library until the
+ * process exits) instead of a plan.
+ *   d_tasks, d_devs, d_stats, d_status: device pointers as in
+ *     tm_exhaustive_batch_dev (d_status may be NULL); h_offsets: HOST array
+ *     of G + 1 offsets.
+ *   Limits: G <= TM_NOALLOC_MAX_GROUPS and offsets[G] <= TM_NOALLOC_MAX_TASKS,
+ *     else TM_ECAPACITY; n <= 12 per group, else TM_ETOOBIG.
+ *   It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ *     call on a device (with that device current) looks up the array's
+ *     device address once; make it before starting any stream capture.
+ *   Every call uses the same array, which keeps the previous call's
+ *     contents; each call resets what must start from a known value.  Calls
+ *     whose work can overlap on the GPU race on the array: serialise them.
+ * Stream-ordered: returns after enqueuing its kernels. */
+#define TM_NOALLOC_MAX_GROUPS 64
+#define TM_NOALLOC_MAX_TASKS 768
+
+int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t* h_offsets,
+                                int G, const tm_device* d_devs, tm_stats* d_stats,
+                                int32_t* d_status /* may be NULL */, void* stream);
 
 /* ---- misc ---------------------------------------------------------------- */
 

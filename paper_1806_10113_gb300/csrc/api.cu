@@ -218,6 +218,7 @@ const char* tm_strerror(int code)
     case TM_ECUDA: return "CUDA runtime error";
     case TM_ETIMEOUT: return "device-side wait timed out";
     case TM_ENOMEM: return "out of memory";
+    case TM_ECAPACITY: return "batch exceeds the no-allocation entry point's fixed capacity";
     default: return "unknown tm status";
     }
 }

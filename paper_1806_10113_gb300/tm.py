@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_PKG, "libtm.so")
 
 TM_MAX_TASKS = 16
 TM_MAX_EXHAUSTIVE = 12
+TM_NOALLOC_MAX_GROUPS = 64
+TM_NOALLOC_MAX_TASKS = 768
 
 STATS_DTYPE = np.dtype([
     ("best", "<i4"), ("worst", "<i4"), ("sum", "<i8"), ("mean", "<f8"),
@@ -65,6 +67,7 @@ _SIGS = {
     "tm_plan_launches": [_vp],
     "tm_plan_set_timing": [_vp, _vp, _vp],
     "tm_exhaustive_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tm_exhaustive_batch_noalloc": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
@@ -278,3 +281,20 @@ def tm_exhaustive_batch_dev(plan: Plan, d_tasks, d_devs, d_stats, d_status=None,
     _check(lib().tm_exhaustive_batch_dev(plan.handle, _dptr(d_tasks), _dptr(d_devs),
                                          _dptr(d_stats), _dptr(d_status), _stream(stream)),
            "tm_exhaustive_batch_dev")
+
+
+def tm_exhaustive_batch_noalloc(d_tasks, offsets, d_devs, d_stats, d_status=None, stream=None):
+    """Exhaustive search with no allocation, for callers that cannot allocate
+    device memory (their GPU memory is owned by another allocator, or they
+    cannot pay for cudaMalloc / cudaFree where they run).
+
+    Same results as tm_exhaustive_batch_dev.  ``offsets`` is a HOST array;
+    the other buffers are device tensors.  The library's fixed working array
+    caps a batch at TM_NOALLOC_MAX_GROUPS groups and TM_NOALLOC_MAX_TASKS
+    tasks (TMError code -8 beyond that).  All calls share that array, so
+    calls that could overlap on the GPU must be serialised."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    _check(lib().tm_exhaustive_batch_noalloc(_dptr(d_tasks), _p(off), G, _dptr(d_devs),
+                                             _dptr(d_stats), _dptr(d_status), _stream(stream)),
+           "tm_exhaustive_batch_noalloc")
