@@ -183,14 +183,16 @@ int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
  * or one that cannot afford cudaMalloc / cudaFree (cudaFree waits for the
  * whole device) where it runs.  tm_plan_create allocates; this call does
  * not.  It computes the same results as tm_exhaustive_batch_dev, bit for
- * bit, with its working memory in one fixed device array inside libtm.so
- * (a few tens of KB, held by every GPU that loads the library until the
- * process exits) instead of a plan.
+ * bit, with its working memory in one fixed 1 MiB device array inside
+ * libtm.so (held by every GPU that loads the library until the process
+ * exits) instead of a plan.
  *   d_tasks, d_devs, d_stats, d_status: device pointers as in
  *     tm_exhaustive_batch_dev (d_status may be NULL); h_offsets: HOST array
  *     of G + 1 offsets.
- *   Limits: G <= TM_NOALLOC_MAX_GROUPS and offsets[G] <= TM_NOALLOC_MAX_TASKS,
- *     else TM_ECAPACITY; n <= 12 per group, else TM_ETOOBIG.
+ *   Limits: G <= TM_NOALLOC_MAX_GROUPS, offsets[G] <= TM_NOALLOC_MAX_TASKS
+ *     and sum over groups of C(n, 4) <= TM_NOALLOC_MAX_SUBSETS, else
+ *     TM_ECAPACITY (e.g. 64 groups of 8 tasks, or 9 groups of 12 fit);
+ *     n <= 12 per group, else TM_ETOOBIG.
  *   It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  *     call on a device (with that device current) looks up the array's
  *     device address once; make it before starting any stream capture.
@@ -200,6 +202,7 @@ int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
  * Stream-ordered: returns after enqueuing its kernels. */
 #define TM_NOALLOC_MAX_GROUPS 64
 #define TM_NOALLOC_MAX_TASKS 768
+#define TM_NOALLOC_MAX_SUBSETS 4800
 
 int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t* h_offsets,
                                 int G, const tm_device* d_devs, tm_stats* d_stats,

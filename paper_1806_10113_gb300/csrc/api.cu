@@ -145,60 +145,32 @@ int first_error(const int32_t* status, int G)
 
 void free_plan(Plan& p)
 {
-    cudaFree(p.d_offsets);
-    cudaFree(p.d_item_base);
-    cudaFree(p.d_info);
-    cudaFree(p.d_tbl);
-    cudaFree(p.d_acc);
-    p.d_offsets = nullptr;
-    p.d_item_base = nullptr;
+    if (p.d_gp) cudaFree(p.d_gp);   // the start of the plan's single block
+    p.d_gp = nullptr;
     p.d_info = nullptr;
     p.d_tbl = nullptr;
+    p.d_sub = nullptr;
     p.d_acc = nullptr;
 }
 
-int build_plan(const int32_t* h_offsets, int G, int levels, Plan& p)
+int build_plan(const int32_t* h_offsets, int G, int pdmax, Plan& p)
 {
-    if (!h_offsets || G < 0 || h_offsets[0] != 0) return TM_EINVAL;
-    if (levels < 5 || levels > 7) return TM_EINVAL;
-    std::vector<uint32_t> base(G + 1, 0);
-    uint64_t total = 0;
-    for (int g = 0; g < G; ++g) {
-        int n = h_offsets[g + 1] - h_offsets[g];
-        if (n < 1) return TM_EINVAL;
-        if (n > TM_MAX_EXHAUSTIVE) return TM_ETOOBIG;
-        base[g] = (uint32_t)total;
-        if (n >= 5) total += tmgpu::factorial_u64(n) / tmgpu::factorial_u64(std::min(n, levels));
-        if (total >= 0xFFFFFFFFull) return TM_ETOOBIG;
-    }
-    base[G] = (uint32_t)total;
+    if (!h_offsets || G < 0) return TM_EINVAL;
+    std::vector<tmgpu::GroupPlan> gp((size_t)G + 1);
+    int rc = tmgpu::plan_decompose(h_offsets, G, pdmax, gp.data(), &p);
+    if (rc != TM_OK) return rc;
     TM_CUDA(cudaGetDevice(&p.device));
-    p.G = G;
-    p.T = h_offsets[G];
-    p.levels = levels;
-    p.total_items = (uint32_t)total;
-    int resident = tmgpu::exhaustive_resident_threads(levels, p.device);
-    if (resident <= 0) resident = 152 * 1024;
-    uint64_t per = (total + resident - 1) / (uint64_t)resident;
-    p.items_per_thread = (uint32_t)std::max<uint64_t>(1, per);
-    p.threads = (uint32_t)((total + p.items_per_thread - 1) / p.items_per_thread);
-    p.launches = tmgpu::exhaustive_launch_count(p);
-
-    size_t Gb = (size_t)std::max(G, 1);
-    bool ok = cudaMalloc(&p.d_offsets, (Gb + 1) * sizeof(int32_t)) == cudaSuccess &&
-              cudaMalloc(&p.d_item_base, (Gb + 1) * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&p.d_info, Gb * sizeof(tmgpu::GroupInfo)) == cudaSuccess &&
-              cudaMalloc(&p.d_tbl, std::max(p.T, 1) * sizeof(int4)) == cudaSuccess &&
-              cudaMalloc(&p.d_acc, 3 * Gb * sizeof(unsigned long long)) == cudaSuccess;
-    if (!ok) { free_plan(p); return TM_ENOMEM; }
-    std::vector<unsigned long long> acc(3 * Gb);
-    for (size_t g = 0; g < Gb; ++g) { acc[3 * g] = ~0ull; acc[3 * g + 1] = 0; acc[3 * g + 2] = 0; }
-    ok = cudaMemcpy(p.d_offsets, h_offsets, (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice) ==
-             cudaSuccess &&
-         cudaMemcpy(p.d_item_base, base.data(), (G + 1) * sizeof(uint32_t),
-                    cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
-                    cudaMemcpyHostToDevice) == cudaSuccess;
+    tmgpu::exhaustive_partition(p, p.device);
+    size_t bytes = tmgpu::plan_carve(p, nullptr);
+    void* base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) return TM_ENOMEM;
+    tmgpu::plan_carve(p, static_cast<unsigned char*>(base));
+    std::vector<unsigned long long> acc(3 * (size_t)std::max(G, 1));
+    for (size_t g = 0; 3 * g < acc.size(); ++g) acc[3 * g] = ~0ull;
+    bool ok = cudaMemcpy(p.d_gp, gp.data(), gp.size() * sizeof(tmgpu::GroupPlan),
+                         cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) { free_plan(p); return TM_ECUDA; }
     return TM_OK;
 }
@@ -230,7 +202,7 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
     if (!plan_out) return TM_EINVAL;
     std::unique_ptr<tm_plan> plan(new (std::nothrow) tm_plan());
     if (!plan) return TM_ENOMEM;
-    int rc = build_plan(h_offsets, G, 5, plan->p);
+    int rc = build_plan(h_offsets, G, 4, plan->p);
     if (rc != TM_OK) return rc;
     *plan_out = plan.release();
     return TM_OK;

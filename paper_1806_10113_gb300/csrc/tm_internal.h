@@ -9,39 +9,7 @@
 
 namespace tmgpu {
 
-// Per-group facts derived once per launch by the prep kernel.
-struct GroupInfo {
-    int32_t off;     // index of the group's first task
-    int32_t n;       // number of tasks
-    int32_t dinit;   // time the DtH stream becomes free before the first
-                     // task: 0 with two DMA engines; with one engine the
-                     // single transfer queue carries every HtD first, so it
-                     // is the sum of HtD (Sec. 3.2, Fig. 2)
-    int32_t hs;      // sum of HtD of the group
-    int32_t status;  // 0 or a tm_status code
-    int32_t pad0, pad1, pad2;
-};
-
-// Exhaustive-search plan (see tm_plan_create in tm.h).
-struct Plan {
-    int device = 0;
-    int G = 0;
-    int T = 0;                  // total tasks
-    int levels = 5;             // orders enumerated per work item: levels!
-    uint32_t total_items = 0;   // work items over all groups
-    uint32_t items_per_thread = 1;
-    uint32_t threads = 0;
-    int launches = 0;
-    int32_t* d_offsets = nullptr;         // [G + 1]
-    uint32_t* d_item_base = nullptr;      // [G + 1] first work item of each group
-    GroupInfo* d_info = nullptr;          // [G]
-    int4* d_tbl = nullptr;                // [T] {htd, k, dth, 0}
-    unsigned long long* d_acc = nullptr;  // [3 G] min key, max key, sum
-    cudaEvent_t ev_before = nullptr;      // optional timing hook
-    cudaEvent_t ev_after = nullptr;
-};
-
-// 0! .. 16!
+// 0! .. 20!
 __host__ __device__ inline uint64_t factorial_u64(int n)
 {
     uint64_t f = 1;
@@ -49,12 +17,149 @@ __host__ __device__ inline uint64_t factorial_u64(int n)
     return f;
 }
 
+// Number of 4-task subsets of n tasks.
+__host__ __device__ inline uint32_t choose4(int n)
+{
+    return n < 4 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) * (n - 3) / 24);
+}
+
+// Per-group facts derived on the device by the prep kernel.
+struct GroupInfo {
+    int32_t off;      // index of the group's first task
+    int32_t n;        // number of tasks
+    int32_t dinit;    // time the DtH stream becomes free before the first
+                      // task: 0 with two DMA engines; with one engine the
+                      // single transfer queue carries every HtD first, so it
+                      // is the sum of HtD (Sec. 3.2, Fig. 2)
+    int32_t hs;       // sum of HtD of the group
+    int32_t status;   // 0 or a tm_status code
+    uint32_t sum32;   // 1 if 24 makespans of this group always fit in 32 bits
+    int32_t pad0, pad1;
+};
+
+// Per-group work layout computed on the host from the group sizes alone.
+// Entry G holds the totals.
+struct GroupPlan {
+    uint64_t cost_base;   // first order (leaf) of the group among all groups
+                          // with n >= 4, in work-item order
+    uint32_t item_base;   // first work item
+    uint32_t unit_base;   // first thread of the prep / suffix-table kernel
+    uint32_t sub_base;    // first suffix-table entry
+    int32_t off;          // first task
+};
+
+// The last four positions of an order hold a 4-task set S.  Because the
+// model's recurrence is max-plus linear in the engine times (h, k, d), the
+// makespan of prefix pi followed by an order sigma of S is
+//     max(d_pi + alpha, k_pi + beta[sigma], gamma[sigma])
+// where h entering S is fixed (the HtD sum of the other tasks) and folded
+// into gamma.  One entry per (group, S); sigma in lexicographic order of S.
+struct SuffixTab {
+    int32_t beta[24];    // longest path from the K-engine time to the end
+    int32_t gamma[24];   // longest path from the HtD-engine time, plus that time
+    int32_t alpha;       // sum of DtH over S (the DtH-engine path)
+    uint32_t mask;       // bit e set if task e is in S
+    int32_t pad0, pad1;
+};
+static_assert(sizeof(SuffixTab) == 208, "suffix table layout");
+
+// Exhaustive-search plan (see tm_plan_create in tm.h).
+struct Plan {
+    int device = 0;
+    int G = 0;
+    int T = 0;                    // total tasks
+    int pdmax = 4;                // prefix positions walked depth-first per item
+    uint32_t total_items = 0;     // work items over all groups
+    uint64_t total_leaves = 0;    // orders of all groups with n >= 4
+    uint32_t total_units = 0;     // prep / suffix-table threads
+    uint32_t total_subs = 0;      // suffix-table entries
+    uint32_t threads = 0;         // enumeration threads
+    uint64_t leaves_per_thread = 0;
+    int launches = 0;
+    GroupPlan* d_gp = nullptr;            // [G + 1]
+    GroupInfo* d_info = nullptr;          // [G]
+    int4* d_tbl = nullptr;                // [T] {htd, k, dth, 0}
+    SuffixTab* d_sub = nullptr;           // [total_subs]
+    unsigned long long* d_acc = nullptr;  // [3 G] min key, max key, sum
+    cudaEvent_t ev_before = nullptr;      // optional timing hook
+    cudaEvent_t ev_after = nullptr;
+};
+
+// Work item of a group with n >= 4 tasks: a 4-subset S (the last four
+// positions) and a HEAD, the first f positions of the prefix; the thread
+// walks the remaining pd prefix positions depth-first.  P = n - 4.
+__host__ __device__ inline int plan_pd(int n, int pdmax) { return n - 4 < pdmax ? n - 4 : pdmax; }
+
+// Fills gp[0..G] from host offsets; allocates nothing.  Returns TM_OK,
+// TM_EINVAL (bad offsets) or TM_ETOOBIG (n > 12 or too many items).
+inline int plan_decompose(const int32_t* offsets, int G, int pdmax, GroupPlan* gp,
+                          Plan* totals)
+{
+    if (!offsets || G < 0 || offsets[0] != 0 || pdmax < 2 || pdmax > 5) return TM_EINVAL;
+    uint64_t cost = 0, items = 0, units = 0, subs = 0;
+    for (int g = 0; g < G; ++g) {
+        int n = offsets[g + 1] - offsets[g];
+        if (n < 1) return TM_EINVAL;
+        if (n > TM_MAX_EXHAUSTIVE) return TM_ETOOBIG;
+        gp[g].cost_base = cost;
+        gp[g].item_base = (uint32_t)items;
+        gp[g].unit_base = (uint32_t)units;
+        gp[g].sub_base = (uint32_t)subs;
+        gp[g].off = offsets[g];
+        uint32_t c4 = choose4(n);
+        units += c4 > 0 ? c4 : 1;
+        subs += c4;
+        if (n >= 4) {
+            int P = n - 4, pd = plan_pd(n, pdmax);
+            uint64_t heads = factorial_u64(P) / factorial_u64(pd);
+            items += (uint64_t)c4 * heads;
+            cost += factorial_u64(n);
+        }
+        if (items >= 0xFFFFFFFFull || units >= 0xFFFFFFFFull) return TM_ETOOBIG;
+    }
+    gp[G].cost_base = cost;
+    gp[G].item_base = (uint32_t)items;
+    gp[G].unit_base = (uint32_t)units;
+    gp[G].sub_base = (uint32_t)subs;
+    gp[G].off = offsets[G];
+    totals->G = G;
+    totals->T = offsets[G];
+    totals->pdmax = pdmax;
+    totals->total_items = (uint32_t)items;
+    totals->total_leaves = cost;
+    totals->total_units = (uint32_t)units;
+    totals->total_subs = (uint32_t)subs;
+    return TM_OK;
+}
+
+// Lays the plan's device arrays out in one block starting at `base` (256-byte
+// aligned pieces) and returns the block's size; with base == nullptr it only
+// measures.
+inline size_t plan_carve(Plan& p, unsigned char* base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* at = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return at;
+    };
+    const size_t G1 = (size_t)(p.G > 0 ? p.G : 1), T1 = (size_t)(p.T > 0 ? p.T : 1);
+    const size_t S1 = (size_t)(p.total_subs > 0 ? p.total_subs : 1);
+    p.d_gp = reinterpret_cast<GroupPlan*>(take((G1 + 1) * sizeof(GroupPlan)));
+    p.d_info = reinterpret_cast<GroupInfo*>(take(G1 * sizeof(GroupInfo)));
+    p.d_tbl = reinterpret_cast<int4*>(take(T1 * sizeof(int4)));
+    p.d_sub = reinterpret_cast<SuffixTab*>(take(S1 * sizeof(SuffixTab)));
+    p.d_acc = reinterpret_cast<unsigned long long*>(take(3 * G1 * sizeof(unsigned long long)));
+    return off;
+}
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_exhaustive(const Plan& plan, const tm_task* d_tasks,
                               const tm_device* d_devs, tm_stats* d_stats,
                               int32_t* d_status, cudaStream_t stream);
 int exhaustive_launch_count(const Plan& plan);
-int exhaustive_resident_threads(int levels, int device);
+// Sets plan.threads and plan.leaves_per_thread for the given device.
+void exhaustive_partition(Plan& plan, int device);
 
 cudaError_t launch_predict(const tm_task* d_tasks, const int32_t* d_offsets,
                            int G, const int32_t* d_orders,

@@ -25,6 +25,7 @@ TM_MAX_TASKS = 16
 TM_MAX_EXHAUSTIVE = 12
 TM_NOALLOC_MAX_GROUPS = 64
 TM_NOALLOC_MAX_TASKS = 768
+TM_NOALLOC_MAX_SUBSETS = 4800
 
 STATS_DTYPE = np.dtype([
     ("best", "<i4"), ("worst", "<i4"), ("sum", "<i8"), ("mean", "<f8"),
@@ -289,9 +290,9 @@ def tm_exhaustive_batch_noalloc(d_tasks, offsets, d_devs, d_stats, d_status=None
     cannot pay for cudaMalloc / cudaFree where they run).
 
     Same results as tm_exhaustive_batch_dev.  ``offsets`` is a HOST array;
-    the other buffers are device tensors.  The library's fixed working array
-    caps a batch at TM_NOALLOC_MAX_GROUPS groups and TM_NOALLOC_MAX_TASKS
-    tasks (TMError code -8 beyond that).  All calls share that array, so
+    the other buffers are device tensors.  The library's fixed 1 MiB working
+    array caps a batch at TM_NOALLOC_MAX_GROUPS groups, TM_NOALLOC_MAX_TASKS
+    tasks and TM_NOALLOC_MAX_SUBSETS 4-task subsets (TMError code -8 beyond).  All calls share that array, so
     calls that could overlap on the GPU must be serialised."""
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
     G = off.shape[0] - 1
