@@ -42,11 +42,30 @@ GROUPS, N_TASKS, SEED = 64, 10, 1
 WORKLOAD = ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
             "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
             "exhaustive 10! orders + heuristic per group")
-# Integer operations per evaluated order that the method needs with prefix
-# sharing: 5 per step of the recurrence (3 adds, 2 maxes) times
-# sum_{m<n} 1/m! ~ e tree nodes per leaf, plus 4 for the reduction
-# (min, max, 64-bit add).
-ALG_OPS_PER_ORDER = 5 * math.e + 4
+# Integer operations per evaluated order, as the plain method counts them:
+# 5 per recurrence step (3 adds, 2 maxes) times ~e tree nodes per order with
+# prefix sharing, plus 4 for the reduction.
+SURVEY_OPS_PER_ORDER = 5 * math.e + 4
+
+
+def method_ops_per_order(n: int) -> float:
+    """Integer operations per order that the implemented method needs.
+
+    The last four positions hold a set S; the makespan is
+    max(d + alpha_S, k + beta_sigma, gamma_sigma), so each order costs one
+    add and two maxes, plus one min and one add for the reductions (5).  Per
+    prefix of the other P = n - 4 tasks: d + alpha, the prefix maximum
+    (1 add, 2 maxes) and the 64-bit sum (2): 6, shared by 24 orders.  The
+    prefixes are walked depth-first at 5 operations per tree node.  The
+    suffix tables cost 24 orders x 2 chains x 4 steps x 5 per subset, shared
+    by P! x 24 orders."""
+    P = n - 4
+    nodes = sum(math.factorial(P) // math.factorial(P - i) for i in range(1, P + 1))
+    per_prefix = 6 + 5 * nodes / math.factorial(P)
+    return 5 + per_prefix / 24 + 960 / (math.factorial(P) * 24)
+
+
+ALG_OPS_PER_ORDER = method_ops_per_order(N_TASKS)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # Issue-limited int32 peak: 4 schedulers x 32 lanes per SM per clock.
@@ -289,13 +308,19 @@ def run_tm(args):
     d_status = torch.zeros(G, dtype=torch.int32, device=dev)
     d_orders = torch.zeros(T, dtype=torch.int32, device=dev)
     d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
-    plan = tm.Plan(b.offsets)
-    launches_per_step = plan.launches() + 1
+    from paper_1806_10113_gb300 import autotune
+    if args.tuning:
+        pd, fuse, bps = (int(x) for x in args.tuning.split(","))
+        tuning = {"pdmax": pd, "fuse_finalize": fuse, "blocks_per_sm": bps}
+    else:
+        tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
+    tm.tm_set_default_tuning(**tuning)          # also for the host-pointer (e2e) calls
+    plan = tm.Plan(b.offsets, **tuning)
+    launches_per_step = plan.launches()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step():
-        tm.tm_exhaustive_batch_dev(plan, d_tasks, d_dma, d_stats, d_status, stream)
-        tm.tm_heuristic_batch_dev(d_tasks, d_offsets, G, d_dma, d_orders, d_ms, d_status, stream)
+        tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status, stream)
 
     for _ in range(args.warmup):
         step()
@@ -345,17 +370,16 @@ def run_tm(args):
     h_dma = torch.from_numpy(b.dma).pin_memory().numpy()
     e2e_steps = max(3, min(K, 50))
     for _ in range(2):
-        tm.tm_exhaustive_batch(h_tasks, h_offsets, h_dma)
-        tm.tm_heuristic_batch(h_tasks, h_offsets, h_dma)
+        tm.tm_schedule_batch(h_tasks, h_offsets, h_dma)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        st = tm.tm_exhaustive_batch(h_tasks, h_offsets, h_dma)
-        ho, hms = tm.tm_heuristic_batch(h_tasks, h_offsets, h_dma)
+        st, ho, hms = tm.tm_schedule_batch(h_tasks, h_offsets, h_dma)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s, dev)
-    h2d = (2 * h_tasks.nbytes + 2 * h_dma.nbytes + h_offsets.nbytes)
-    d2h = st.nbytes + 4 * G + ho.nbytes + hms.nbytes + 4 * G
+    # per call: tasks and device models in; stats, status, orders, makespans out
+    h2d = h_tasks.nbytes + h_dma.nbytes
+    d2h = st.nbytes + 4 * G + ho.nbytes + hms.nbytes
 
     ws_total = ws
     result = None
@@ -363,6 +387,7 @@ def run_tm(args):
         enum_avg_s = statistics.mean(enum_ms) / 1000.0
         alg_ops = ALG_OPS_PER_ORDER * n_orders
         achieved = alg_ops / enum_avg_s / 1e12
+        survey_achieved = SURVEY_OPS_PER_ORDER * n_orders / enum_avg_s / 1e12
         traffic = profiled_traffic()
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_total, "steps": K,
@@ -370,6 +395,7 @@ def run_tm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "groups": G, "orders_per_step": n_orders,
+                       "tuning": tuning,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws_total}, no collective on the data path"},
             "groups_per_s": G * K * ws_total / total_s,
@@ -383,6 +409,9 @@ def run_tm(args):
                          "kernel": "enum_kernel (exhaustive enumeration)",
                          "kernel_ms": 1000 * enum_avg_s,
                          "ops_per_order": round(ALG_OPS_PER_ORDER, 3),
+                         "ops_basis": "max-plus suffix decomposition (see method_ops_per_order)",
+                         "survey_ops_per_order": round(SURVEY_OPS_PER_ORDER, 3),
+                         "survey_frac": survey_achieved / INT32_PEAK_TOPS,
                          "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
             "clocks": clocks,
             "wall_s_timed": wall,
@@ -404,6 +433,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["tm", "reference"], default="tm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="pdmax,fuse_finalize,blocks_per_sm (skips the autotuner)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

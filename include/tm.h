@@ -156,6 +156,30 @@ int tm_heuristic_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
 typedef struct tm_plan tm_plan;
 
 int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
+
+/* Tuning knobs of an exhaustive-search plan (an autotuner picks them; 0
+ * means "the library's default").  None changes any result.
+ *   pdmax          prefix positions each work item walks depth-first, 3..5
+ *                  (a work item holds pdmax! x 24 orders; default 4)
+ *   fuse_finalize  1: each group is finalized by the last enumeration
+ *                  thread to finish it (one launch fewer); 2: a separate
+ *                  finalize kernel; 0: default (2)
+ *   blocks_per_sm  resident enumeration blocks per SM used to size the
+ *                  work split, 1..occupancy limit; 0: the occupancy limit */
+typedef struct tm_tuning {
+    int32_t pdmax;
+    int32_t fuse_finalize;
+    int32_t blocks_per_sm;
+} tm_tuning;
+
+int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tuning,
+                         tm_plan** plan_out);
+
+/* Process-wide tuning used by tm_plan_create and by the plans that the
+ * host-pointer exhaustive calls build internally (NULL restores the
+ * library's defaults).  Plans created earlier keep their tuning.  Returns
+ * TM_EINVAL for out-of-range knobs. */
+int tm_set_default_tuning(const tm_tuning* tuning);
 void tm_plan_destroy(tm_plan* plan);
 
 /* Runs the exhaustive search of every group of the plan.  d_tasks must use
@@ -165,7 +189,23 @@ int tm_exhaustive_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
                             const tm_device* d_devs, tm_stats* d_stats,
                             int32_t* d_status /* may be NULL */, void* stream);
 
-/* Number of kernel launches one tm_exhaustive_batch_dev call enqueues. */
+/* The whole scheduling pass of the paper's method for every group of the
+ * plan: the exhaustive search (d_stats) and the reordering heuristic
+ * (d_orders_out in the task layout; d_makespans_out may be NULL), in two
+ * kernel launches.  Same results as tm_exhaustive_batch_dev followed by
+ * tm_heuristic_batch_dev.  d_status reports the per-group input checks. */
+int tm_schedule_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
+                          const tm_device* d_devs, tm_stats* d_stats,
+                          int32_t* d_orders_out, int32_t* d_makespans_out,
+                          int32_t* d_status /* may be NULL */, void* stream);
+
+/* Host-pointer form of tm_schedule_batch_dev (synchronous).  n <= 12. */
+int tm_schedule_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                      const tm_device* devs, tm_stats* stats,
+                      int32_t* orders_out, int32_t* makespans_out /* may be NULL */);
+
+/* Number of kernel launches one tm_exhaustive_batch_dev call enqueues
+ * (tm_schedule_batch_dev enqueues the same number). */
 int tm_plan_launches(const tm_plan* plan);
 
 /* Optional timing hook: cudaEvent_t handles (passed as void*, created by the

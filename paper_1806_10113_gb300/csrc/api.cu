@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "tm_internal.h"
@@ -86,6 +87,7 @@ struct Context {
     DevBuf tasks, offsets, devs, orders, out, stats, status;
     tm_plan* plan = nullptr;
     std::vector<int32_t> plan_offsets;
+    unsigned plan_epoch = 0;
     void release()
     {
         if (plan) tm_plan_destroy(plan);
@@ -104,6 +106,10 @@ struct Context {
 };
 
 thread_local std::unique_ptr<Context> t_ctx;
+
+std::mutex g_tune_mu;
+tm_tuning g_default_tuning{0, 0, 0};
+unsigned g_tuning_epoch = 0;   // bumped on every change; cached plans compare it
 
 int context(Context** out)
 {
@@ -151,26 +157,72 @@ void free_plan(Plan& p)
     p.d_tbl = nullptr;
     p.d_sub = nullptr;
     p.d_acc = nullptr;
+    p.d_unit_group = nullptr;
+    p.d_target = nullptr;
+    p.d_done = nullptr;
 }
 
-int build_plan(const int32_t* h_offsets, int G, int pdmax, Plan& p)
+// Host-side tables of the fused finalize: the group of every prep unit, and
+// per group the number of enumeration threads whose item range touches it
+// (thread t covers the items that start in orders [t W, (t + 1) W)).
+void fused_tables(const Plan& p, const std::vector<tmgpu::GroupPlan>& gp,
+                  std::vector<uint32_t>& unit_group, std::vector<uint32_t>& target)
 {
+    unit_group.assign(std::max<uint32_t>(p.total_units, 1), 0);
+    for (int g = 0; g < p.G; ++g)
+        for (uint32_t u = gp[g].unit_base; u < gp[g + 1].unit_base; ++u) unit_group[u] = g;
+    target.assign(std::max(p.G, 1), 0);
+    const uint64_t W = p.leaves_per_thread, total = gp[p.G].cost_base;
+    int g = 0;
+    for (uint64_t t = 0; t < p.threads; ++t) {
+        const uint64_t x0 = t * W;
+        if (x0 >= total) break;
+        const uint32_t i0 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, x0);
+        const uint32_t i1 =
+            tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, std::min(x0 + W, total));
+        if (i0 >= i1) continue;
+        while (gp[g + 1].item_base <= i0) ++g;        // the group holding item i0
+        for (int h = g; h < p.G && gp[h].item_base < i1; ++h)
+            if (gp[h + 1].item_base > gp[h].item_base) ++target[h];
+    }
+}
+
+int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
+{
+    const int pdmax = tune.pdmax == 0 ? 4 : tune.pdmax;
+    const bool fused = tune.fuse_finalize == 1;
+    if (pdmax < 3 || pdmax > 5 || tune.fuse_finalize < 0 || tune.fuse_finalize > 2 ||
+        tune.blocks_per_sm < 0)
+        return TM_EINVAL;
     if (!h_offsets || G < 0) return TM_EINVAL;
     std::vector<tmgpu::GroupPlan> gp((size_t)G + 1);
     int rc = tmgpu::plan_decompose(h_offsets, G, pdmax, gp.data(), &p);
     if (rc != TM_OK) return rc;
     TM_CUDA(cudaGetDevice(&p.device));
-    tmgpu::exhaustive_partition(p, p.device);
-    size_t bytes = tmgpu::plan_carve(p, nullptr);
+    tmgpu::exhaustive_partition(p, p.device, tune.blocks_per_sm);
+    std::vector<uint32_t> unit_group, target;
+    fused_tables(p, gp, unit_group, target);
+    const size_t main_bytes = tmgpu::plan_carve(p, nullptr);
+    const size_t fused_bytes = tmgpu::plan_carve_fused(p, nullptr);
     void* base = nullptr;
-    if (cudaMalloc(&base, bytes) != cudaSuccess) return TM_ENOMEM;
+    if (cudaMalloc(&base, main_bytes + fused_bytes) != cudaSuccess) return TM_ENOMEM;
     tmgpu::plan_carve(p, static_cast<unsigned char*>(base));
-    std::vector<unsigned long long> acc(3 * (size_t)std::max(G, 1));
-    for (size_t g = 0; 3 * g < acc.size(); ++g) acc[3 * g] = ~0ull;
+    tmgpu::plan_carve_fused(p, static_cast<unsigned char*>(base) + main_bytes);
+    if (!fused) p.d_target = p.d_done = nullptr;   // separate finalize kernel
+    p.launches = tmgpu::exhaustive_launch_count(p);
+    std::vector<unsigned long long> acc(tmgpu::kAccStride * (size_t)std::max(G, 1), 0ull);
+    for (size_t g = 0; g * tmgpu::kAccStride < acc.size(); ++g) acc[g * tmgpu::kAccStride] = ~0ull;
     bool ok = cudaMemcpy(p.d_gp, gp.data(), gp.size() * sizeof(tmgpu::GroupPlan),
                          cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
-                         cudaMemcpyHostToDevice) == cudaSuccess;
+                         cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(p.d_unit_group, unit_group.data(), unit_group.size() * sizeof(uint32_t),
+                         cudaMemcpyHostToDevice) == cudaSuccess &&
+              (!fused ||
+               (cudaMemcpy(p.d_target, target.data(), target.size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice) == cudaSuccess &&
+                cudaMemset(p.d_done, 0, tmgpu::kDoneStride * target.size() * sizeof(uint32_t)) ==
+                    cudaSuccess));
     if (!ok) { free_plan(p); return TM_ECUDA; }
     return TM_OK;
 }
@@ -197,14 +249,40 @@ const char* tm_strerror(int code)
 
 const char* tm_version(void) { return "tm 0.1 sm_103a"; }
 
-int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
+int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tuning,
+                         tm_plan** plan_out)
 {
     if (!plan_out) return TM_EINVAL;
+    tm_tuning tune{0, 0, 0};
+    if (tuning) tune = *tuning;
     std::unique_ptr<tm_plan> plan(new (std::nothrow) tm_plan());
     if (!plan) return TM_ENOMEM;
-    int rc = build_plan(h_offsets, G, 4, plan->p);
+    int rc = build_plan(h_offsets, G, tune, plan->p);
     if (rc != TM_OK) return rc;
     *plan_out = plan.release();
+    return TM_OK;
+}
+
+int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
+{
+    tm_tuning tune;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune = g_default_tuning;
+    }
+    return tm_plan_create_tuned(h_offsets, G, &tune, plan_out);
+}
+
+int tm_set_default_tuning(const tm_tuning* tuning)
+{
+    tm_tuning t{0, 0, 0};
+    if (tuning) t = *tuning;
+    if ((t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
+        t.fuse_finalize > 2 || t.blocks_per_sm < 0)
+        return TM_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_default_tuning = t;
+    ++g_tuning_epoch;
     return TM_OK;
 }
 
@@ -232,6 +310,17 @@ int tm_exhaustive_batch_dev(const tm_plan* plan, const tm_task* d_tasks, const t
     if (plan->p.G > 0 && (!d_tasks || !d_devs || !d_stats)) return TM_EINVAL;
     cudaError_t e = tmgpu::launch_exhaustive(plan->p, d_tasks, d_devs, d_stats, d_status,
                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_schedule_batch_dev(const tm_plan* plan, const tm_task* d_tasks, const tm_device* d_devs,
+                          tm_stats* d_stats, int32_t* d_orders_out, int32_t* d_makespans_out,
+                          int32_t* d_status, void* stream)
+{
+    if (!plan) return TM_EINVAL;
+    if (plan->p.G > 0 && (!d_tasks || !d_devs || !d_stats || !d_orders_out)) return TM_EINVAL;
+    cudaError_t e = tmgpu::launch_exhaustive(plan->p, d_tasks, d_devs, d_stats, d_status,
+                                             (cudaStream_t)stream, d_orders_out, d_makespans_out);
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
@@ -297,8 +386,14 @@ int tm_predict(const tm_task* tasks, int n, const int32_t* order, const tm_devic
     return tm_predict_batch(tasks, offsets, 1, order, dev, makespan);
 }
 
-int tm_exhaustive_batch(const tm_task* tasks, const int32_t* offsets, int G,
-                        const tm_device* devs, tm_stats* stats)
+}  // extern "C"
+
+namespace {
+
+// Host-pointer exhaustive search, with the heuristic too when orders_out is
+// given.  The plan is cached per thread for repeated group sizes.
+int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const tm_device* devs,
+                    tm_stats* stats, int32_t* orders_out, int32_t* makespans_out)
 {
     int rc = check_batch(tasks, offsets, G, devs, TM_MAX_EXHAUSTIVE);
     if (rc != TM_OK) return rc;
@@ -307,32 +402,71 @@ int tm_exhaustive_batch(const tm_task* tasks, const int32_t* offsets, int G,
     Context* c = nullptr;
     if ((rc = context(&c)) != TM_OK) return rc;
     std::vector<int32_t> offs(offsets, offsets + G + 1);
-    if (!c->plan || c->plan_offsets != offs) {
+    unsigned epoch;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        epoch = g_tuning_epoch;
+    }
+    if (!c->plan || c->plan_offsets != offs || c->plan_epoch != epoch) {
         if (c->plan) tm_plan_destroy(c->plan);
         c->plan = nullptr;
         c->plan_offsets.clear();
         if ((rc = tm_plan_create(offsets, G, &c->plan)) != TM_OK) return rc;
         c->plan_offsets = offs;
+        c->plan_epoch = epoch;
     }
-    int T = offsets[G];
+    const int T = offsets[G];
     cudaStream_t s = c->stream;
     if ((rc = copy_in(c->tasks, tasks, T * sizeof(tm_task), s)) != TM_OK) return rc;
     if ((rc = copy_in(c->devs, devs, G * sizeof(tm_device), s)) != TM_OK) return rc;
-    if (!c->stats.ensure(G * sizeof(tm_stats)) || !c->status.ensure(G * sizeof(int32_t)))
+    if (!c->stats.ensure(G * sizeof(tm_stats)) || !c->status.ensure(G * sizeof(int32_t)) ||
+        !c->orders.ensure(T * sizeof(int32_t)) || !c->out.ensure(G * sizeof(int32_t)))
         return TM_ENOMEM;
-    rc = tm_exhaustive_batch_dev(c->plan, c->tasks.as<tm_task>(), c->devs.as<tm_device>(),
-                                 c->stats.as<tm_stats>(), c->status.as<int32_t>(), s);
+    if (orders_out)
+        rc = tm_schedule_batch_dev(c->plan, c->tasks.as<tm_task>(), c->devs.as<tm_device>(),
+                                   c->stats.as<tm_stats>(), c->orders.as<int32_t>(),
+                                   c->out.as<int32_t>(), c->status.as<int32_t>(), s);
+    else
+        rc = tm_exhaustive_batch_dev(c->plan, c->tasks.as<tm_task>(), c->devs.as<tm_device>(),
+                                     c->stats.as<tm_stats>(), c->status.as<int32_t>(), s);
     if (rc != TM_OK) return rc;
     std::vector<tm_stats> out(G);
-    std::vector<int32_t> status(G);
+    std::vector<int32_t> status(G), orders(orders_out ? T : 0), ms(orders_out ? G : 0);
     TM_CUDA(cudaMemcpyAsync(out.data(), c->stats.p, G * sizeof(tm_stats), cudaMemcpyDeviceToHost,
                             s));
     TM_CUDA(cudaMemcpyAsync(status.data(), c->status.p, G * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, s));
+    if (orders_out) {
+        TM_CUDA(cudaMemcpyAsync(orders.data(), c->orders.p, T * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+        TM_CUDA(cudaMemcpyAsync(ms.data(), c->out.p, G * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+    }
     TM_CUDA(cudaStreamSynchronize(s));
     if ((rc = first_error(status.data(), G)) != TM_OK) return rc;
     std::memcpy(stats, out.data(), G * sizeof(tm_stats));
+    if (orders_out) {
+        std::memcpy(orders_out, orders.data(), T * sizeof(int32_t));
+        if (makespans_out) std::memcpy(makespans_out, ms.data(), G * sizeof(int32_t));
+    }
     return TM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tm_exhaustive_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                        const tm_device* devs, tm_stats* stats)
+{
+    return exhaustive_host(tasks, offsets, G, devs, stats, nullptr, nullptr);
+}
+
+int tm_schedule_batch(const tm_task* tasks, const int32_t* offsets, int G, const tm_device* devs,
+                      tm_stats* stats, int32_t* orders_out, int32_t* makespans_out)
+{
+    if (G > 0 && !orders_out) return TM_EINVAL;
+    return exhaustive_host(tasks, offsets, G, devs, stats, orders_out, makespans_out);
 }
 
 int tm_exhaustive(const tm_task* tasks, int n, const tm_device* dev, tm_stats* stats,

@@ -34,6 +34,7 @@
 // finalize kernel writes tm_stats and handles n <= 3.
 #include <algorithm>
 
+#include "heuristic.cuh"
 #include "tm_device.cuh"
 
 namespace tmgpu {
@@ -59,26 +60,6 @@ constexpr Subsets make_subsets()
     return s;
 }
 __constant__ Subsets c_subsets = make_subsets();
-
-// The 24 orders of four slots in lexicographic order, slot q of order j in
-// bits 2q..2q+1.
-struct Perm4 {
-    uint8_t p[24];
-};
-constexpr Perm4 make_perm4()
-{
-    Perm4 r{};
-    int i = 0;
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b)
-            for (int c = 0; c < 4; ++c) {
-                if (b == a || c == a || c == b) continue;
-                int d = 6 - a - b - c;
-                r.p[i++] = (uint8_t)(a | (b << 2) | (c << 4) | (d << 6));
-            }
-    return r;
-}
-__constant__ Perm4 c_perm4 = make_perm4();
 
 __constant__ uint32_t c_fact[13] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 40320u,
                                     362880u, 3628800u, 39916800u, 479001600u};
@@ -113,74 +94,261 @@ __device__ __forceinline__ int search_group(int G, uint64_t x, Key key)
     return lo;
 }
 
+// ---- per-group results ------------------------------------------------------
+
+// Statistics of a group of n <= 3 tasks (at most 6 orders), by one warp:
+// lane r evaluates the order of rank r.
+__device__ __forceinline__ void small_group_stats(const int4* __restrict__ t, int n,
+                                                  int32_t dinit, int lane, tm_stats* out)
+{
+    const uint32_t nf = (uint32_t)factorial_u64(n);
+    const bool live = (uint32_t)lane < nf;
+    const int32_t ms = live ? makespan_of_rank(t, n, dinit, lane, nullptr) : 0;
+    const int32_t best = __reduce_min_sync(kFull, live ? ms : INT32_MAX);
+    const int32_t worst = __reduce_max_sync(kFull, live ? ms : -1);
+    const uint32_t brank = __ffs(__ballot_sync(kFull, live && ms == best)) - 1;
+    const uint32_t wrank = __ffs(__ballot_sync(kFull, live && ms == worst)) - 1;
+    unsigned long long sum = live ? (unsigned long long)ms : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (lane != 0) return;
+    tm_stats st;
+    st.best = best;
+    st.worst = worst;
+    st.sum = (int64_t)sum;
+    st.mean = (double)(int64_t)sum / (double)nf;
+    st.best_rank = brank;
+    st.worst_rank = wrank;
+    for (int i = 0; i < 16; ++i) st.best_order[i] = st.worst_order[i] = 0xFF;
+    makespan_of_rank(t, n, dinit, brank, st.best_order);
+    makespan_of_rank(t, n, dinit, wrank, st.worst_order);
+    *out = st;
+}
+
+// The same by one full warp: lanes 0 and 1 unrank and check the best and
+// the worst order in parallel.  Every lane passes the same g.
+__device__ __noinline__ void finalize_group_warp(int g, const GroupInfo& gi,
+                                                 const int4* __restrict__ tbl,
+                                                 unsigned long long* __restrict__ acc,
+                                                 tm_stats* __restrict__ stats,
+                                                 int32_t* __restrict__ status)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long* A = acc + (size_t)kAccStride * g;
+    unsigned long long mk = 0, xk = 0, sum = 0;
+    if (lane == 0) {
+        mk = __ldcg(A);
+        xk = __ldcg(A + 1);
+        sum = __ldcg(A + 2);
+        A[0] = ~0ull;
+        A[1] = 0;
+        A[2] = 0;
+    }
+    mk = __shfl_sync(kFull, mk, 0);
+    xk = __shfl_sync(kFull, xk, 0);
+    const int n = gi.n;
+    const int32_t best = (int32_t)(mk >> 32), worst = (int32_t)(xk >> 32);
+    const uint32_t brank = (uint32_t)mk, wrank = kFull - (uint32_t)xk;
+    const uint64_t nf = factorial_u64(n);
+    uint8_t order[16];
+    for (int i = 0; i < 16; ++i) order[i] = 0xFF;
+    bool good = brank < nf && wrank < nf;
+    if (lane < 2 && good)
+        good = makespan_of_rank(tbl + gi.off, n, gi.dinit, lane == 0 ? brank : wrank, order) ==
+               (lane == 0 ? best : worst);
+    const bool ok = __all_sync(kFull, good);
+    uint32_t packed[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t w = (uint32_t)order[4 * q] | ((uint32_t)order[4 * q + 1] << 8) |
+                           ((uint32_t)order[4 * q + 2] << 16) | ((uint32_t)order[4 * q + 3] << 24);
+        packed[q] = __shfl_sync(kFull, w, 1);   // the worst order, from lane 1
+    }
+    if (lane != 0) return;
+    if (!ok) {  // the reduction disagrees with a re-evaluation: never expected
+        if (status) status[g] = TM_ECUDA;
+        return;
+    }
+    tm_stats st;
+    st.best = best;
+    st.worst = worst;
+    st.sum = (int64_t)sum;
+    st.mean = (double)(int64_t)sum / (double)nf;
+    st.best_rank = brank;
+    st.worst_rank = wrank;
+    for (int i = 0; i < 16; ++i) {
+        st.best_order[i] = order[i];
+        st.worst_order[i] = (uint8_t)(packed[i / 4] >> (8 * (i % 4)));
+    }
+    stats[g] = st;
+    if (status) status[g] = 0;
+}
+
+// Turns a group's three reduction words into tm_stats (one thread) and
+// resets them for the next launch.  The reported orders are re-evaluated;
+// a mismatch (never expected) is reported as TM_ECUDA.
+__device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const int4* __restrict__ tbl,
+                               unsigned long long* __restrict__ acc, tm_stats* __restrict__ stats,
+                               int32_t* __restrict__ status)
+{
+    unsigned long long* A = acc + (size_t)kAccStride * g;
+    const unsigned long long mk = __ldcg(A), xk = __ldcg(A + 1), sum = __ldcg(A + 2);
+    A[0] = ~0ull;
+    A[1] = 0;
+    A[2] = 0;
+    const int n = gi.n;
+    const int4* t = tbl + gi.off;
+    tm_stats st;
+    st.best = (int32_t)(mk >> 32);
+    st.worst = (int32_t)(xk >> 32);
+    st.best_rank = (uint32_t)mk;
+    st.worst_rank = kFull - (uint32_t)xk;
+    st.sum = (int64_t)sum;
+    st.mean = (double)(int64_t)sum / (double)factorial_u64(n);
+    for (int i = 0; i < 16; ++i) st.best_order[i] = st.worst_order[i] = 0xFF;
+    const uint64_t nf = factorial_u64(n);
+    bool ok = st.best_rank < nf && st.worst_rank < nf;
+    ok = ok && makespan_of_rank(t, n, gi.dinit, (uint32_t)st.best_rank, st.best_order) == st.best;
+    ok = ok && makespan_of_rank(t, n, gi.dinit, (uint32_t)st.worst_rank, st.worst_order) ==
+                   st.worst;
+    if (!ok) {
+        if (status) status[g] = TM_ECUDA;
+        return;
+    }
+    stats[g] = st;
+    if (status) status[g] = 0;
+}
+
 // ---- prep: validation, padded task table, suffix tables -------------------
 
-// One thread per (unit, order of S): a group with n >= 4 tasks has C(n, 4)
-// units (its 4-subsets in colexicographic order), smaller groups one unit.
-// Thread (unit 0, order 0) of each group also validates it and writes its
-// GroupInfo and padded task table.
-__global__ void prep_kernel(const tm_task* __restrict__ tasks, const tm_device* __restrict__ devs,
-                            const GroupPlan* __restrict__ gp, int G, uint32_t total_units,
-                            GroupInfo* __restrict__ info, int4* __restrict__ tbl,
-                            SuffixTab* __restrict__ sub)
+// One warp per unit: a group with n >= 4 tasks has C(n, 4) units (its
+// 4-subsets in colexicographic order), smaller groups one unit.  Lane i
+// holds task i; lane j < 24 tabulates order j of S.  The warp of a group's
+// first unit also validates the group and writes its GroupInfo and padded
+// task table.
+struct PrepArgs {
+    const tm_task* tasks;
+    const tm_device* devs;
+    const GroupPlan* gp;
+    const uint32_t* unit_group;   // may be null: binary search instead
+    int G;
+    uint32_t total_units;
+    GroupInfo* info;
+    int4* tbl;
+    SuffixTab* sub;
+    tm_stats* stats;
+    int32_t* status;
+    int32_t* orders;              // heuristic outputs; null: no heuristic
+    int32_t* makespans;
+};
+
+__global__ void prep_kernel(PrepArgs a)
 {
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t u = (uint32_t)(tid / 24), j = (uint32_t)(tid % 24);
-    if (u >= total_units) return;
-    int g = search_group(G, u, [&](int i) { return (uint64_t)gp[i].unit_base; });
+    const uint32_t u = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const tm_task* __restrict__ tasks = a.tasks;
+    const GroupPlan* __restrict__ gp = a.gp;
+    const int G = a.G;
+    if (u >= a.total_units) {
+        // the heuristic (Algorithm 1) of group u - total_units, in the same launch
+        const uint32_t hg = u - a.total_units;
+        if (a.orders && hg < (uint32_t)G) {
+            const int off = gp[hg].off;
+            heur::heuristic_group(tasks, off, gp[hg + 1].off - off, a.devs[hg].dma_engines,
+                                  (int)hg, lane, a.orders, a.makespans, nullptr);
+        }
+        return;
+    }
+    const int g = a.unit_group ? (int)a.unit_group[u]
+                               : search_group(G, u, [&](int i) { return (uint64_t)gp[i].unit_base; });
+    GroupInfo* __restrict__ info = a.info;
+    int4* __restrict__ tbl = a.tbl;
+    SuffixTab* __restrict__ sub = a.sub;
     const int off = gp[g].off;
     const int n = gp[g + 1].off - off;
     const uint32_t s = u - gp[g].unit_base;
-    int32_t hs = 0, dinit = 0;
-    int status = check_group(tasks + off, n, devs[g].dma_engines, TM_MAX_EXHAUSTIVE, &hs, &dinit);
-    if (s == 0 && j == 0) {
-        int64_t total = 0;
-        for (int i = 0; status == 0 && i < n; ++i) {
-            tm_task t = tasks[off + i];
-            total += (int64_t)t.htd + t.k + t.dth;
-            tbl[off + i] = make_int4(t.htd, t.k, t.dth, 0);
+    const bool mine = lane < n;
+    tm_task t = mine ? tasks[off + lane] : tm_task{0, 0, 0};
+    const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
+    unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+    // with no negative duration and tot <= INT32_MAX the HtD sum fits
+    const int32_t hs = (int32_t)__reduce_add_sync(kFull, mine ? (uint32_t)t.htd : 0u);
+    const int dma = a.devs[g].dma_engines;
+    int status = 0;
+    if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
+    else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
+    else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
+    if (s == 0) {
+        if (status == 0 && mine) tbl[off + lane] = make_int4(t.htd, t.k, t.dth, 0);
+        if (lane == 0) {
+            GroupInfo gi;
+            gi.off = off;
+            gi.n = n;
+            gi.hs = hs;
+            gi.dinit = dma == 1 ? hs : 0;
+            gi.status = status;
+            gi.sum32 = tot * 24u < (1ull << 32) ? 1u : 0u;
+            gi.pad0 = gi.pad1 = 0;
+            info[g] = gi;
+            if (status != 0 && a.status) a.status[g] = status;
         }
-        GroupInfo gi;
-        gi.off = off;
-        gi.n = n;
-        gi.dinit = dinit;
-        gi.hs = hs;
-        gi.status = status;
-        gi.sum32 = (uint64_t)total * 24u < (1ull << 32) ? 1u : 0u;
-        gi.pad0 = gi.pad1 = 0;
-        info[g] = gi;
+        if (status == 0 && n <= 3) {       // at most 6 orders: finish here
+            __syncwarp();
+            small_group_stats(tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
+            if (lane == 0 && a.status) a.status[g] = 0;
+        }
     }
     if (status != 0 || n < 4) return;
 
-    // the set S, ascending, and the order j of its four tasks
+    // the set S, ascending, broadcast from the lanes holding its tasks
     const uint32_t mask = c_subsets.m[s];
-    tm_task t4[4];
-    int64_t hS = hs, alpha = 0;
+    int e[4];
     for (int q = 0, m = (int)mask; q < 4; ++q) {
-        int e = __ffs(m) - 1;
+        e[q] = __ffs(m) - 1;
         m &= m - 1;
-        t4[q] = tasks[off + e];
-        hS -= t4[q].htd;
-        alpha += t4[q].dth;
     }
-    // beta: the makespan when only the K-engine time (= 0) enters S;
-    // gamma: when only the HtD-engine time (= hS) enters S.  A very negative
-    // start removes the other engines from the max-plus paths.
-    const int64_t NEG = -(int64_t(1) << 40);
-    const uint32_t p = c_perm4.p[j];
-    int64_t bh = NEG, bk = 0, bd = NEG, gh = hS, gk = NEG, gd = NEG;
+    int32_t H[4], K[4], D[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int x = (p >> (2 * q)) & 3;
-        const tm_task t = x == 0 ? t4[0] : x == 1 ? t4[1] : x == 2 ? t4[2] : t4[3];
-        bh += t.htd; bk = max(bk, bh) + t.k; bd = max(bd, bk) + t.dth;
-        gh += t.htd; gk = max(gk, gh) + t.k; gd = max(gd, gk) + t.dth;
+        H[q] = __shfl_sync(kFull, t.htd, e[q]);
+        K[q] = __shfl_sync(kFull, t.k, e[q]);
+        D[q] = __shfl_sync(kFull, t.dth, e[q]);
     }
     SuffixTab* out = sub + gp[g].sub_base + s;
-    out->beta[j] = (int32_t)bd;
-    out->gamma[j] = (int32_t)gd;
-    if (j == 0) {
-        out->alpha = (int32_t)alpha;
+    if (lane < 24) {
+        // order `lane` of S in lexicographic order: Lehmer digits 6, 2, 1
+        const int d0 = lane / 6, d1 = (lane % 6) / 2, d2 = lane % 2;
+        int slots = 0x3210, order[4];
+        const int dg[3] = {d0, d1, d2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int c = dg[q];
+            order[q] = (slots >> (4 * c)) & 0xF;
+            const int low = slots & ((1 << (4 * c)) - 1);
+            slots = low | ((slots >> (4 * c + 4)) << (4 * c));
+        }
+        order[3] = slots & 0xF;
+        // beta: the makespan when only the K-engine time (= 0) enters S;
+        // gamma: when only the HtD-engine time (= hs - sum of S's HtD)
+        // enters S.  A very negative start removes the other engines.
+        const int64_t NEG = -(int64_t(1) << 40);
+        int64_t hS = (int64_t)hs - H[0] - H[1] - H[2] - H[3];
+        int64_t bh = NEG, bk = 0, bd = NEG, gh = hS, gk = NEG, gd = NEG;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = order[q];
+            const int64_t h = x == 0 ? H[0] : x == 1 ? H[1] : x == 2 ? H[2] : H[3];
+            const int64_t k = x == 0 ? K[0] : x == 1 ? K[1] : x == 2 ? K[2] : K[3];
+            const int64_t d = x == 0 ? D[0] : x == 1 ? D[1] : x == 2 ? D[2] : D[3];
+            bh += h; bk = max(bk, bh) + k; bd = max(bd, bk) + d;
+            gh += h; gk = max(gk, gh) + k; gd = max(gd, gk) + d;
+        }
+        out->beta[lane] = (int32_t)bd;
+        out->gamma[lane] = (int32_t)gd;
+    } else if (lane == 24) {
+        out->alpha = D[0] + D[1] + D[2] + D[3];
         out->mask = mask;
         out->pad0 = out->pad1 = 0;
     }
@@ -223,18 +391,55 @@ __device__ __forceinline__ unsigned long long worst_key(const Acc& a)
     return ((unsigned long long)(uint32_t)a.worst << 32) | (kFull - a.worst_rank);
 }
 
-__device__ __forceinline__ void flush(Acc& a, unsigned long long* acc, int g)
+// Where the enumeration threads report.  With done != null each group is
+// finalized by its last finishing thread.
+struct Sink {
+    unsigned long long* acc;
+    const GroupInfo* info;
+    const int4* tbl;
+    tm_stats* stats;
+    int32_t* status;
+    const uint32_t* target;
+    uint32_t* done;
+};
+
+__device__ __forceinline__ void flush(const Acc& a, unsigned long long* acc, int g)
 {
     if (a.worst < 0) return;
-    atomicMin(&acc[3 * g + 0], best_key(a));
-    atomicMax(&acc[3 * g + 1], worst_key(a));
-    atomicAdd(&acc[3 * g + 2], a.sum);
+    unsigned long long* A = acc + (size_t)kAccStride * g;
+    atomicMin(&A[0], best_key(a));
+    atomicMax(&A[1], worst_key(a));
+    atomicAdd(&A[2], a.sum);
+}
+
+// Reports `threads` finished contributors to group g.  Returns true if this
+// call was the last one: the caller then finalizes the group.
+__device__ __forceinline__ bool finished(const Sink& k, int g, uint32_t threads)
+{
+    if (!k.done) return false;
+    __threadfence();
+    uint32_t* done = k.done + (size_t)kDoneStride * g;
+    const uint32_t before = atomicAdd(done, threads);
+    if (before + threads != k.target[g]) return false;
+    __threadfence();
+    *done = 0;
+    return true;
+}
+
+// finished() by one thread, which finalizes alone if it was the last.
+__device__ __forceinline__ void finished_single(const Sink& k, int g)
+{
+    if (finished(k, g, 1)) {
+        const GroupInfo gi = k.info[g];
+        if (gi.status == 0) finalize_group(g, gi, k.tbl, k.acc, k.stats, k.status);
+    }
 }
 
 // End-of-thread flush: when the whole warp is present and on one group, the
 // warp reduces first and one lane issues the three atomics.
-__device__ __forceinline__ void flush_final(Acc& a, unsigned long long* acc, int g)
+__device__ __forceinline__ void flush_final(Acc& a, const Sink& k, int g)
 {
+    unsigned long long* acc = k.acc;
     const unsigned live = __activemask();
     if (live == kFull && __all_sync(kFull, g == __shfl_sync(kFull, g, 0))) {
         int32_t best = __reduce_min_sync(kFull, a.best);
@@ -244,14 +449,21 @@ __device__ __forceinline__ void flush_final(Acc& a, unsigned long long* acc, int
         unsigned long long sum = a.sum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-        if ((threadIdx.x & 31) == 0 && worst >= 0) {
+        bool last = false;
+        if ((threadIdx.x & 31) == 0) {
             Acc r = a;
             r.best = best; r.best_rank = brank; r.worst = worst; r.worst_rank = wrank;
             r.sum = sum;
             flush(r, acc, g);
+            last = finished(k, g, 32);
+        }
+        if (__shfl_sync(kFull, last, 0)) {     // the whole warp finalizes
+            const GroupInfo gi = k.info[g];
+            if (gi.status == 0) finalize_group_warp(g, gi, k.tbl, k.acc, k.stats, k.status);
         }
     } else {
         flush(a, acc, g);
+        finished_single(k, g);
     }
 }
 
@@ -389,6 +601,28 @@ __device__ __forceinline__ Eng run_head(uint32_t hd, int f, int P, int32_t dinit
     return st;
 }
 
+// Rank of the item's first order (its head, the other prefix tasks
+// ascending, then S's first order): no order of the item ranks lower.
+__device__ __noinline__ uint32_t item_first_rank(uint32_t hd, uint64_t rem, int f, int pd, int n)
+{
+    const int P = n - 4;
+    uint32_t digits = 0;
+    for (int j = f - 1; j >= 0; --j) {
+        const uint32_t r = (uint32_t)(P - j);
+        const uint32_t q = hd / r;
+        digits |= (hd - q * r) << (4 * j);
+        hd = q;
+    }
+    uint32_t placed = 0;
+    for (int j = 0; j < f; ++j) {
+        const int c = (digits >> (4 * j)) & 0xF;
+        placed |= (uint32_t)nib_get(rem, c) << (4 * j);
+        rem = nib_remove(rem, c);
+    }
+    for (int q = 0; q < pd; ++q) placed |= (uint32_t)nib_get(rem, q) << (4 * (f + q));
+    return prefix_rank(placed, n, P);
+}
+
 // Rank of the first order of the current item reaching v: the prefix walked
 // `at`-th (its tail is the at-th order, lexicographically, of the pd tasks in
 // `rem`), completed by the first order of S reaching v.
@@ -412,32 +646,18 @@ __device__ __noinline__ uint32_t item_rank(uint32_t at, int32_t v, uint32_t hd, 
     return prefix_rank(placed, n, f + pd) + (uint32_t)first_completion(st.k, st.d, v, tab);
 }
 
-// First work item whose first order is at or after global order index x.
-template <int PDMAX>
-__device__ __forceinline__ uint32_t first_item(const GroupPlan* __restrict__ gp, int G,
-                                               uint64_t x)
-{
-    if (x >= gp[G].cost_base) return gp[G].item_base;
-    int g = search_group(G, x, [&](int i) { return gp[i].cost_base; });
-    int n = gp[g + 1].off - gp[g].off;
-    uint64_t lpi = 24ull * factorial_u64(plan_pd(n, PDMAX));
-    uint64_t q = (x - gp[g].cost_base + lpi - 1) / lpi;
-    uint64_t i = gp[g].item_base + q;
-    return (uint32_t)min(i, (uint64_t)gp[g + 1].item_base);
-}
-
 template <int PDMAX>
 __global__ void __launch_bounds__(kEnumBlock, 4)
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
-            uint64_t per_thread, unsigned long long* __restrict__ acc)
+            uint64_t per_thread, Sink sink)
 {
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t x0 = t * per_thread;
     const uint64_t total = gp[G].cost_base;
     if (x0 >= total) return;
-    uint32_t i = first_item<PDMAX>(gp, G, x0);
-    const uint32_t end = first_item<PDMAX>(gp, G, min(x0 + per_thread, total));
+    uint32_t i = plan_first_item(gp, G, PDMAX, x0);
+    const uint32_t end = plan_first_item(gp, G, PDMAX, min(x0 + per_thread, total));
     if (i >= end) return;
     int g = search_group(G, i, [&](int j) { return (uint64_t)gp[j].item_base; });
 
@@ -451,9 +671,15 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
     uint64_t sc = 0;   // S's complement, ascending nibbles
     int pd = 0, f = 0, P = 0;
     bool load_group = true;
+    bool touched = false;   // this thread has visited an item of group g
     for (; i < end; ++i) {
         while (load_group || i >= gend) {
-            if (!load_group) { flush(a, acc, g); a.reset(); ++g; }
+            if (!load_group) {
+                if (touched) { flush(a, sink.acc, g); finished_single(sink, g); }
+                a.reset();
+                touched = false;
+                ++g;
+            }
             load_group = false;
             gi = info[g];
             gbase = gp[g].item_base;
@@ -465,6 +691,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
             heads = (uint32_t)(factorial_u64(P) / factorial_u64(pd));
             cur = kFull;
         }
+        touched = true;
         if (gi.status != 0) continue;
         const uint32_t local = i - gbase;
         const uint32_t s = local / heads;
@@ -502,98 +729,48 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
         if (gi.sum32) walk_prefixes<PDMAX, true>(pd, st, rem, gt, S, a);
         else walk_prefixes<PDMAX, false>(pd, st, rem, gt, S, a);
         // Settle the item against the running best / worst: every lane of a
-        // warp gets here together, so this rank work does not diverge.
-        if (a.imin <= a.best) {
+        // warp gets here together, so this rank work does not diverge.  A
+        // tie can only lower the rank if the item's first order ranks below
+        // the running one; a strict improvement always counts.
+        const bool tie_b = a.imin == a.best, tie_w = a.imax == a.worst;
+        uint32_t low = 0;
+        if (tie_b || tie_w) low = item_first_rank(hd, sc, f, pd, gi.n);
+        if (a.imin < a.best || (tie_b && low < a.best_rank)) {
             uint32_t r = item_rank(a.imin_at, a.imin, hd, sc, f, pd, gi.n, gi.dinit, gt, tab);
             if (a.imin < a.best || r < a.best_rank) { a.best = a.imin; a.best_rank = r; }
         }
-        if (a.imax >= a.worst) {
+        if (a.imax > a.worst || (tie_w && low < a.worst_rank)) {
             uint32_t r = item_rank(a.imax_at, a.imax, hd, sc, f, pd, gi.n, gi.dinit, gt, tab);
             if (a.imax > a.worst || r < a.worst_rank) { a.worst = a.imax; a.worst_rank = r; }
         }
     }
-    flush_final(a, acc, g);
+    flush_final(a, sink, g);
 }
 
 // ---- finalize ---------------------------------------------------------------
 
+// Separate finalize (when the plan has no completion counters): one warp
+// per group of n >= 4 tasks; the prep kernel handled the others.
 __global__ void finalize_kernel(const GroupInfo* __restrict__ info, const int4* __restrict__ tbl,
                                 int G, unsigned long long* __restrict__ acc,
                                 tm_stats* __restrict__ stats, int32_t* __restrict__ status)
 {
-    int g = (int)((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
+    const int g = (int)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (g >= G) return;
-    GroupInfo gi = info[g];
-    unsigned long long* A = acc + 3 * g;
-    if (gi.status != 0) {
-        if (lane == 0) {
-            if (status) status[g] = gi.status;
-            A[0] = ~0ull; A[1] = 0; A[2] = 0;
-        }
-        return;
-    }
-    const int4* t = tbl + gi.off;
-    const int n = gi.n;
-    int32_t best, worst;
-    uint32_t best_rank, worst_rank;
-    unsigned long long sum;
-    bool ok = true;
-    if (n <= 3) {
-        uint32_t nf = (uint32_t)factorial_u64(n);
-        bool live = (uint32_t)lane < nf;
-        int32_t ms = live ? makespan_of_rank(t, n, gi.dinit, lane, nullptr) : 0;
-        best = __reduce_min_sync(kFull, live ? ms : INT32_MAX);
-        worst = __reduce_max_sync(kFull, live ? ms : -1);
-        best_rank = __ffs(__ballot_sync(kFull, live && ms == best)) - 1;
-        worst_rank = __ffs(__ballot_sync(kFull, live && ms == worst)) - 1;
-        sum = live ? (unsigned long long)ms : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    } else {
-        unsigned long long mk = A[0], xk = A[1];
-        sum = A[2];
-        best = (int32_t)(mk >> 32);
-        worst = (int32_t)(xk >> 32);
-        best_rank = (uint32_t)mk;
-        worst_rank = kFull - (uint32_t)xk;
-        const uint64_t nf = factorial_u64(n);
-        ok = best_rank < nf && worst_rank < nf;
-        __syncwarp();
-        if (lane == 0) { A[0] = ~0ull; A[1] = 0; A[2] = 0; }
-    }
-    if (lane != 0) return;
-    tm_stats st;
-    st.best = best;
-    st.worst = worst;
-    st.sum = (int64_t)sum;
-    st.mean = (double)(int64_t)sum / (double)factorial_u64(n);
-    st.best_rank = best_rank;
-    st.worst_rank = worst_rank;
-    for (int i = 0; i < 16; ++i) st.best_order[i] = st.worst_order[i] = 0xFF;
-    // self-check: the reported orders must reproduce the reported values
-    if (ok) {
-        ok = makespan_of_rank(t, n, gi.dinit, best_rank, st.best_order) == best &&
-             makespan_of_rank(t, n, gi.dinit, worst_rank, st.worst_order) == worst;
-    }
-    if (!ok) {  // the reduction disagrees with a re-evaluation: never expected
-        if (status) status[g] = TM_ECUDA;
-        return;
-    }
-    stats[g] = st;
-    if (status) status[g] = 0;
+    const GroupInfo gi = info[g];
+    if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, tbl, acc, stats, status);
 }
 
 template <int PDMAX>
-cudaError_t launch_enum(const Plan& p, cudaStream_t stream)
+cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
 {
     uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
     enum_kernel<PDMAX><<<blocks, kEnumBlock, 0, stream>>>(p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G,
-                                                           p.leaves_per_thread, p.d_acc);
+                                                           p.leaves_per_thread, sink);
     return cudaGetLastError();
 }
 
-int resident_threads(int pdmax, int device)
+int resident_threads(int pdmax, int device, int blocks_per_sm)
 {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -605,14 +782,15 @@ int resident_threads(int pdmax, int device)
     default: break;
     }
     if (e != cudaSuccess || sms <= 0 || per_sm <= 0) return 152 * 512;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
     return sms * per_sm * kEnumBlock;
 }
 
 }  // namespace
 
-void exhaustive_partition(Plan& p, int device)
+void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
 {
-    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, device),
+    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, device, blocks_per_sm),
                                           std::max<uint64_t>(p.total_items, 1));
     p.leaves_per_thread = std::max<uint64_t>(1, (p.total_leaves + threads - 1) / threads);
     p.threads = (uint32_t)((p.total_leaves + p.leaves_per_thread - 1) / p.leaves_per_thread);
@@ -621,33 +799,51 @@ void exhaustive_partition(Plan& p, int device)
 
 int exhaustive_launch_count(const Plan& p)
 {
-    return p.total_items > 0 ? 3 : 2;
+    if (p.G == 0) return 0;
+    return 1 + (p.total_items > 0 ? 1 : 0) + (p.d_done ? 0 : 1);
 }
 
 cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_device* d_devs,
-                              tm_stats* d_stats, int32_t* d_status, cudaStream_t stream)
+                              tm_stats* d_stats, int32_t* d_status, cudaStream_t stream,
+                              int32_t* d_orders, int32_t* d_makespans)
 {
     if (p.G == 0) return cudaSuccess;
-    const uint64_t prep_threads = (uint64_t)p.total_units * 24;
-    prep_kernel<<<(unsigned)((prep_threads + 191) / 192), 192, 0, stream>>>(
-        d_tasks, d_devs, p.d_gp, p.G, p.total_units, p.d_info, p.d_tbl, p.d_sub);
+    PrepArgs pa;
+    pa.tasks = d_tasks;
+    pa.devs = d_devs;
+    pa.gp = p.d_gp;
+    pa.unit_group = p.d_unit_group;
+    pa.G = p.G;
+    pa.total_units = p.total_units;
+    pa.info = p.d_info;
+    pa.tbl = p.d_tbl;
+    pa.sub = p.d_sub;
+    pa.stats = d_stats;
+    pa.status = d_status;
+    pa.orders = d_orders;
+    pa.makespans = d_makespans;
+    const uint64_t prep_threads = ((uint64_t)p.total_units + (d_orders ? p.G : 0)) * 32;
+    prep_kernel<<<(unsigned)((prep_threads + 255) / 256), 256, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
+        Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done};
         if (p.ev_before && (e = cudaEventRecord(p.ev_before, stream)) != cudaSuccess) return e;
         switch (p.pdmax) {
-        case 3: e = launch_enum<3>(p, stream); break;
-        case 4: e = launch_enum<4>(p, stream); break;
-        case 5: e = launch_enum<5>(p, stream); break;
+        case 3: e = launch_enum<3>(p, sink, stream); break;
+        case 4: e = launch_enum<4>(p, sink, stream); break;
+        case 5: e = launch_enum<5>(p, sink, stream); break;
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
         if (p.ev_after && (e = cudaEventRecord(p.ev_after, stream)) != cudaSuccess) return e;
+        if (!p.d_done) {
+            finalize_kernel<<<(p.G * 32 + 255) / 256, 256, 0, stream>>>(p.d_info, p.d_tbl, p.G,
+                                                                        p.d_acc, d_stats, d_status);
+            e = cudaGetLastError();
+        }
     }
-    uint64_t threads = (uint64_t)p.G * 32;
-    finalize_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
-        p.d_info, p.d_tbl, p.G, p.d_acc, d_stats, d_status);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace tmgpu

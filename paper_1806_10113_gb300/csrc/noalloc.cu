@@ -48,8 +48,8 @@ struct InitArgs {
 __global__ void noalloc_init_kernel(InitArgs a, GroupPlan* gp, unsigned long long* acc)
 {
     for (int i = threadIdx.x; i <= a.G; i += blockDim.x) gp[i] = a.gp[i];
-    for (int i = threadIdx.x; i < 3 * a.G; i += blockDim.x)
-        acc[i] = (i % 3 == 0) ? ~0ull : 0ull;
+    for (int i = threadIdx.x; i < kAccStride * a.G; i += blockDim.x)
+        acc[i] = (i % kAccStride == 0) ? ~0ull : 0ull;
 }
 
 std::mutex g_mu;

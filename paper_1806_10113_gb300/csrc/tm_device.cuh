@@ -78,6 +78,31 @@ __device__ __forceinline__ uint64_t nib_remove(uint64_t list, int c)
     return low | high;
 }
 
+// Division of a 32-bit numerator by k! (1 <= k <= 12) as one 64 x 64-bit
+// multiply-high by ceil(2^64 / k!) (division by invariant integers using
+// multiplication, Granlund and Montgomery, PLDI 1994): for r < 2^32 and a
+// divisor d < 2^32 the error term stays below 2^-32 < 1/d, so the quotient
+// is exact.
+struct FactRecip {
+    unsigned long long m[13];
+};
+constexpr FactRecip make_fact_recip()
+{
+    FactRecip r{};
+    unsigned long long f = 1;
+    for (int k = 0; k <= 12; ++k) {
+        if (k > 1) f *= (unsigned long long)k;
+        r.m[k] = f == 1 ? 0ull : (~0ull) / f + 1ull;   // k! = 1 handled apart
+    }
+    return r;
+}
+__constant__ FactRecip c_fact_recip = make_fact_recip();
+
+__device__ __forceinline__ uint32_t div_fact(uint32_t r, int k)
+{
+    return k <= 1 ? r : (uint32_t)__umul64hi((unsigned long long)r, c_fact_recip.m[k]);
+}
+
 // Makespan of the order with lexicographic rank `rank` (n <= 12, rank < n!),
 // generic and slow; writes the order to order_out if not NULL.  A rank out
 // of range is clamped digit by digit, so table reads stay inside the group.
@@ -86,11 +111,10 @@ __device__ inline int32_t makespan_of_rank(const int4* tbl, int n, int32_t dinit
 {
     uint64_t list = nib_identity(n);
     Eng s{0, 0, dinit};
-    uint32_t f = (uint32_t)factorial_u64(n - 1);
     for (int i = 0; i < n; ++i) {
-        uint32_t c = min(rank / f, (uint32_t)(n - 1 - i));
-        rank -= c * f;
-        if (i < n - 1) f /= (uint32_t)(n - 1 - i);
+        const int k = n - 1 - i;
+        const uint32_t c = min(div_fact(rank, k), (uint32_t)k);
+        rank -= c * (uint32_t)factorial_u64(k);
         int e = nib_get(list, (int)c);
         list = nib_remove(list, (int)c);
         if (order_out) order_out[i] = (uint8_t)e;

@@ -23,6 +23,12 @@ __host__ __device__ inline uint32_t choose4(int n)
     return n < 4 ? 0u : (uint32_t)(n * (n - 1) * (n - 2) * (n - 3) / 24);
 }
 
+// Each group's three reduction words (min key, max key, sum) and its
+// completion counter sit on their own 128-byte line, so that the atomics of
+// different groups do not queue at the same L2 slice.
+constexpr int kAccStride = 16;    // unsigned long long per group
+constexpr int kDoneStride = 32;   // uint32_t per group
+
 // Per-group facts derived on the device by the prep kernel.
 struct GroupInfo {
     int32_t off;      // index of the group's first task
@@ -80,7 +86,14 @@ struct Plan {
     GroupInfo* d_info = nullptr;          // [G]
     int4* d_tbl = nullptr;                // [T] {htd, k, dth, 0}
     SuffixTab* d_sub = nullptr;           // [total_subs]
-    unsigned long long* d_acc = nullptr;  // [3 G] min key, max key, sum
+    unsigned long long* d_acc = nullptr;  // [kAccStride G] min key, max key, sum
+    // Fused finalize: each group is finalized by the last enumeration thread
+    // to finish with it.  d_target[g] counts the threads whose item range
+    // touches group g; d_done[g] counts those that finished.  Without these
+    // (nullptr) a separate finalize kernel runs.
+    uint32_t* d_unit_group = nullptr;     // [total_units] group of each prep unit
+    uint32_t* d_target = nullptr;         // [G]
+    uint32_t* d_done = nullptr;           // [kDoneStride G]
     cudaEvent_t ev_before = nullptr;      // optional timing hook
     cudaEvent_t ev_after = nullptr;
 };
@@ -149,17 +162,58 @@ inline size_t plan_carve(Plan& p, unsigned char* base)
     p.d_info = reinterpret_cast<GroupInfo*>(take(G1 * sizeof(GroupInfo)));
     p.d_tbl = reinterpret_cast<int4*>(take(T1 * sizeof(int4)));
     p.d_sub = reinterpret_cast<SuffixTab*>(take(S1 * sizeof(SuffixTab)));
-    p.d_acc = reinterpret_cast<unsigned long long*>(take(3 * G1 * sizeof(unsigned long long)));
+    p.d_acc = reinterpret_cast<unsigned long long*>(
+        take(kAccStride * G1 * sizeof(unsigned long long)));
     return off;
 }
 
-// Launchers (return cudaError_t of the launch).
+// Device arrays of the fused-finalize plan, laid out after plan_carve's
+// block (same conventions).
+inline size_t plan_carve_fused(Plan& p, unsigned char* base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* at = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return at;
+    };
+    const size_t G1 = (size_t)(p.G > 0 ? p.G : 1);
+    const size_t U1 = (size_t)(p.total_units > 0 ? p.total_units : 1);
+    p.d_unit_group = reinterpret_cast<uint32_t*>(take(U1 * sizeof(uint32_t)));
+    p.d_target = reinterpret_cast<uint32_t*>(take(G1 * sizeof(uint32_t)));
+    p.d_done = reinterpret_cast<uint32_t*>(take(kDoneStride * G1 * sizeof(uint32_t)));
+    return off;
+}
+
+// First work item whose first order is at or after global order index x
+// (host and device).  pdmax as in the plan.
+__host__ __device__ inline uint32_t plan_first_item(const GroupPlan* gp, int G, int pdmax,
+                                                    uint64_t x)
+{
+    if (x >= gp[G].cost_base) return gp[G].item_base;
+    int lo = 0, hi = G;                       // largest g with cost_base <= x
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (gp[mid].cost_base <= x) lo = mid; else hi = mid;
+    }
+    const int n = gp[lo + 1].off - gp[lo].off;
+    const uint64_t lpi = 24ull * factorial_u64(plan_pd(n, pdmax));
+    const uint64_t q = (x - gp[lo].cost_base + lpi - 1) / lpi;
+    const uint64_t i = gp[lo].item_base + q;
+    return (uint32_t)(i < gp[lo + 1].item_base ? i : gp[lo + 1].item_base);
+}
+
+// Launchers (return cudaError_t of the launch).  With d_orders non-null the
+// heuristic for every group runs in the same launches (orders in the task
+// layout, makespans optional).
 cudaError_t launch_exhaustive(const Plan& plan, const tm_task* d_tasks,
                               const tm_device* d_devs, tm_stats* d_stats,
-                              int32_t* d_status, cudaStream_t stream);
+                              int32_t* d_status, cudaStream_t stream,
+                              int32_t* d_orders = nullptr, int32_t* d_makespans = nullptr);
 int exhaustive_launch_count(const Plan& plan);
-// Sets plan.threads and plan.leaves_per_thread for the given device.
-void exhaustive_partition(Plan& plan, int device);
+// Sets plan.threads and plan.leaves_per_thread for the given device;
+// blocks_per_sm 0 = occupancy limit.
+void exhaustive_partition(Plan& plan, int device, int blocks_per_sm = 0);
 
 cudaError_t launch_predict(const tm_task* d_tasks, const int32_t* d_offsets,
                            int G, const int32_t* d_orders,

@@ -64,11 +64,15 @@ _SIGS = {
     "tm_predict_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "tm_heuristic_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "tm_plan_create": [_vp, ctypes.c_int, ctypes.POINTER(_vp)],
+    "tm_plan_create_tuned": [_vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)],
+    "tm_set_default_tuning": [_vp],
     "tm_plan_destroy": [_vp],
     "tm_plan_launches": [_vp],
     "tm_plan_set_timing": [_vp, _vp, _vp],
     "tm_exhaustive_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tm_exhaustive_batch_noalloc": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tm_schedule_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "tm_schedule_batch": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
@@ -223,6 +227,22 @@ def tm_heuristic_batch(tasks, offsets, dma):
     return orders[:t.shape[0]], ms[:G]
 
 
+def tm_schedule_batch(tasks, offsets, dma):
+    """Exhaustive search and heuristic of every group in one call.
+
+    Returns (stats structured array, heuristic orders, heuristic makespans)."""
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    dev = _devs(dma, G)
+    st = np.zeros(max(G, 1), dtype=STATS_DTYPE)
+    orders = np.zeros(max(t.shape[0], 1), dtype=np.int32)
+    ms = np.zeros(max(G, 1), dtype=np.int32)
+    _check(lib().tm_schedule_batch(_p(t), _p(off), G, _p(dev), _p(st), _p(orders), _p(ms)),
+           "tm_schedule_batch")
+    return st[:G], orders[:t.shape[0]], ms[:G]
+
+
 # ---- ragged batches, device pointers, stream-ordered ---------------------------
 
 def tm_predict_batch_dev(d_tasks, d_offsets, G: int, d_orders, d_devs, d_makespans,
@@ -240,15 +260,29 @@ def tm_heuristic_batch_dev(d_tasks, d_offsets, G: int, d_devs, d_orders_out,
            "tm_heuristic_batch_dev")
 
 
+class Tuning(ctypes.Structure):
+    """tm_tuning: pdmax (3..5), fuse_finalize (1 fused, 2 separate), blocks_per_sm; 0 = default."""
+    _fields_ = [("pdmax", ctypes.c_int32), ("fuse_finalize", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+def tm_set_default_tuning(pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0):
+    """Tuning for plans made by tm_plan_create and the host-pointer calls."""
+    t = Tuning(pdmax, fuse_finalize, blocks_per_sm)
+    _check(lib().tm_set_default_tuning(ctypes.byref(t)), "tm_set_default_tuning")
+
+
 class Plan:
     """Owns a tm_plan (exhaustive search over a fixed set of group sizes)."""
 
-    def __init__(self, offsets):
+    def __init__(self, offsets, pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0):
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
         self.G = off.shape[0] - 1
         self.offsets = off
+        self.tuning = Tuning(pdmax, fuse_finalize, blocks_per_sm)
         h = ctypes.c_void_p()
-        _check(lib().tm_plan_create(_p(off), self.G, ctypes.byref(h)), "tm_plan_create")
+        _check(lib().tm_plan_create_tuned(_p(off), self.G, ctypes.byref(self.tuning),
+                                          ctypes.byref(h)), "tm_plan_create_tuned")
         self._h = h
 
     @property
@@ -275,6 +309,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def tm_schedule_batch_dev(plan: Plan, d_tasks, d_devs, d_stats, d_orders_out,
+                          d_makespans_out=None, d_status=None, stream=None):
+    """Exhaustive search and heuristic of every group of the plan, two launches."""
+    _check(lib().tm_schedule_batch_dev(plan.handle, _dptr(d_tasks), _dptr(d_devs), _dptr(d_stats),
+                                       _dptr(d_orders_out), _dptr(d_makespans_out),
+                                       _dptr(d_status), _stream(stream)),
+           "tm_schedule_batch_dev")
 
 
 def tm_exhaustive_batch_dev(plan: Plan, d_tasks, d_devs, d_stats, d_status=None, stream=None):

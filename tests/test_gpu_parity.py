@@ -214,6 +214,87 @@ def test_heuristic_worked_example(tm):
     assert tm.tm_heuristic(t3, 1) == ([0, 2, 1], 19_000_000)
 
 
+# ---- the whole scheduling pass ----------------------------------------------------
+
+def test_schedule_batch_matches_oracle_on_ragged_groups(tm):
+    """Exhaustive search and heuristic in one call: groups of 1..10 tasks,
+    both device models, small and large durations."""
+    rng = random.Random(17)
+    sizes = [rng.randint(1, 10) for _ in range(40)] + [1, 2, 3, 4, 10]
+    b = inputs.random_groups(17, sizes, hi=3_000_000)
+    st, orders, ms = tm.tm_schedule_batch(b.tasks, b.offsets, b.dma)
+    got = tm.stats_to_dicts(st, b.sizes())
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(got[g], ref[g], g)
+    assert (orders == ref_orders).all() and (ms.astype(np.int64) == ref_ms).all()
+    # repeated calls reuse the cached plan and its completion counters
+    st2, orders2, ms2 = tm.tm_schedule_batch(b.tasks, b.offsets, b.dma)
+    assert st2.tobytes() == st.tobytes() and (orders2 == orders).all()
+
+
+def test_schedule_batch_dev_reports_invalid_groups(tm):
+    import torch
+    dev = torch.device("cuda")
+    b = inputs.random_groups(58, [7, 3, 9, 5, 2, 8], hi=5_000_000)
+    tasks = b.tasks.copy()
+    tasks[b.offsets[2] + 4, 0] = -1                     # group 2: negative duration
+    tasks[b.offsets[4], 2] = -7                         # group 4 (2 tasks): negative duration
+    plan = tm.Plan(b.offsets)
+    d_tasks = torch.from_numpy(tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(b.G * 72, dtype=torch.uint8, device=dev)
+    d_orders = torch.zeros(b.tasks.shape[0], dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(b.G, dtype=torch.int32, device=dev)
+    d_status = torch.full((b.G,), 99, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status)
+        torch.cuda.synchronize()
+        assert list(d_status.cpu().numpy()) == [0, 0, -2, 0, -2, 0]
+        got = tm.stats_to_dicts(d_stats.cpu().numpy().view(tm.STATS_DTYPE), b.sizes())
+        orders = d_orders.cpu().numpy()
+        for g in (0, 1, 3, 5):
+            assert_stats_equal(got[g], oracle.exhaustive(b.group(g), int(b.dma[g])), g)
+            o, m = oracle.heuristic(b.group(g), int(b.dma[g]))
+            assert list(orders[b.offsets[g]:b.offsets[g + 1]]) == o and int(d_ms[g]) == m
+    plan.close()
+
+
+@pytest.mark.parametrize("tuning", [dict(pdmax=3), dict(pdmax=5), dict(fuse_finalize=1),
+                                    dict(pdmax=5, fuse_finalize=1, blocks_per_sm=2),
+                                    dict(pdmax=3, blocks_per_sm=1)])
+def test_every_tuning_gives_identical_results(tm, tuning):
+    """Work split, prefix depth and finalize placement change no result."""
+    import torch
+    dev = torch.device("cuda")
+    rng = random.Random(23)
+    sizes = [rng.randint(1, 11) for _ in range(30)] + [4, 5, 9, 11]
+    b = inputs.random_groups(23, sizes, hi=rng.choice([50, 4_000_000]))
+    tie = inputs.random_groups(24, [9, 10, 8], lo=0, hi=3)        # many ties
+    b = inputs.make_batch([b.group(g) for g in range(b.G)] + [tie.group(g) for g in range(tie.G)],
+                          list(b.dma) + list(tie.dma))
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    outs = []
+    for tun in ({}, tuning):
+        plan = tm.Plan(b.offsets, **tun)
+        d_stats = torch.zeros(b.G * 72, dtype=torch.uint8, device=dev)
+        d_status = torch.full((b.G,), 9, dtype=torch.int32, device=dev)
+        for _ in range(2):
+            tm.tm_exhaustive_batch_dev(plan, d_tasks, d_dma, d_stats, d_status)
+        torch.cuda.synchronize()
+        assert (d_status.cpu().numpy() == 0).all()
+        outs.append(d_stats.cpu().numpy().tobytes())
+        plan.close()
+    assert outs[0] == outs[1]
+    got = tm.stats_to_dicts(np.frombuffer(outs[1], dtype=tm.STATS_DTYPE), b.sizes())
+    small = [g for g in range(b.G) if b.sizes()[g] <= 9]
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in small:
+        assert_stats_equal(got[g], ref[g], g)
+
+
 # ---- device-pointer entry points ----------------------------------------------------
 
 def test_dev_entry_points_and_status(tm):
