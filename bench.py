@@ -39,9 +39,15 @@ from paper_1806_10113_gb300 import inputs  # noqa: E402
 METRIC = "orderings evaluated/s (exact model, N=10/12); task groups scheduled/s at <=1% gap"
 UNIT = "orders/s"
 GROUPS, N_TASKS, SEED = 64, 10, 1
-WORKLOAD = ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
-            "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
-            "exhaustive 10! orders + heuristic per group")
+WORKLOADS = {
+    "dkdt64x10": ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
+                  "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
+                  "exhaustive 10! orders + heuristic per group"),
+    "ragged8192": ("8192 ragged groups, n~U{4..9}, each task dominant-kernel or dominant-transfer "
+                   "(p=1/2), durations log-uniform [1e4,1e7] ns, seed 2, DMA engines alternating "
+                   "2/1: exhaustive n! orders + heuristic per group"),
+}
+WORKLOAD = WORKLOADS["dkdt64x10"]
 # Integer operations per evaluated order, as the plain method counts them:
 # 5 per recurrence step (3 adds, 2 maxes) times ~e tree nodes per order with
 # prefix sharing, plus 4 for the reduction.
@@ -74,8 +80,16 @@ PROFILE = os.path.join(ROOT, "profiles", "exhaustive_enum_kernel_n10_g128.md")
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload(rank: int = 0):
+def workload(rank: int = 0, name: str = "dkdt64x10"):
+    if name == "ragged8192":
+        return inputs.ragged_mixed(groups=8192, seed=2 + 1000 * rank)
     return inputs.dk_dt_groups(groups=GROUPS, n=N_TASKS, seed=SEED + 1000 * rank)
+
+
+def ops_per_order(b) -> float:
+    """method_ops_per_order weighted by each group's orders (groups n >= 4)."""
+    w = [(math.factorial(int(n)), method_ops_per_order(int(n))) for n in b.sizes() if n >= 4]
+    return sum(a * o for a, o in w) / max(1, sum(a for a, _ in w))
 
 
 def orders_per_step(b) -> int:
@@ -298,7 +312,7 @@ def run_tm(args):
     dist = dist_init("nccl")
     stream = torch.cuda.current_stream()
 
-    b = workload(rank)
+    b = workload(rank, args.workload)
     G, T = b.G, int(b.tasks.shape[0])
     n_orders = orders_per_step(b)
     d_tasks = torch.from_numpy(b.tasks).to(dev)
@@ -310,17 +324,30 @@ def run_tm(args):
     d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
     from paper_1806_10113_gb300 import autotune
     if args.tuning:
-        pd, fuse, bps = (int(x) for x in args.tuning.split(","))
-        tuning = {"pdmax": pd, "fuse_finalize": fuse, "blocks_per_sm": bps}
+        vals = [int(x) for x in args.tuning.split(",")] + [0]
+        tuning = dict(zip(("pdmax", "fuse_finalize", "blocks_per_sm", "item_cost"), vals[:4]))
     else:
         tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
     tm.tm_set_default_tuning(**tuning)          # also for the host-pointer (e2e) calls
     plan = tm.Plan(b.offsets, **tuning)
     launches_per_step = plan.launches()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ek_capture = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in ek_capture:
+        e.record(stream)
 
     def step():
         tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status, stream)
+
+    if args.graph:
+        # one CUDA-graph launch per step; the enumeration's timing events are
+        # recorded inside the graph and swapped per step
+        plan.set_timing(*ek_capture)
+        plan.capture(d_tasks, d_dma, d_stats, d_orders, d_ms, d_status)
+        plan.set_timing(None, None)
+
+        def step():
+            plan.graph_launch(stream)
 
     for _ in range(args.warmup):
         step()
@@ -346,7 +373,10 @@ def run_tm(args):
     wall0 = time.perf_counter()
     for k in range(K):
         flush.zero_()                        # evict L2 between timed steps
-        plan.set_timing(*ek[k])
+        if args.graph:
+            plan.graph_set_timing(*ek[k])
+        else:
+            plan.set_timing(*ek[k])
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
@@ -385,7 +415,8 @@ def run_tm(args):
     result = None
     if rank == 0:
         enum_avg_s = statistics.mean(enum_ms) / 1000.0
-        alg_ops = ALG_OPS_PER_ORDER * n_orders
+        ops_order = ops_per_order(b)
+        alg_ops = ops_order * n_orders
         achieved = alg_ops / enum_avg_s / 1e12
         survey_achieved = SURVEY_OPS_PER_ORDER * n_orders / enum_avg_s / 1e12
         traffic = profiled_traffic()
@@ -394,8 +425,9 @@ def run_tm(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "groups": G, "orders_per_step": n_orders,
-                       "tuning": tuning,
+            "config": {"workload": WORKLOADS[args.workload], "groups": G,
+                       "orders_per_step": n_orders, "tuning": tuning,
+                       "launch": "cuda graph" if args.graph else "stream",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws_total}, no collective on the data path"},
             "groups_per_s": G * K * ws_total / total_s,
@@ -408,7 +440,7 @@ def run_tm(args):
                          "traffic": traffic,
                          "kernel": "enum_kernel (exhaustive enumeration)",
                          "kernel_ms": 1000 * enum_avg_s,
-                         "ops_per_order": round(ALG_OPS_PER_ORDER, 3),
+                         "ops_per_order": round(ops_order, 3),
                          "ops_basis": "max-plus suffix decomposition (see method_ops_per_order)",
                          "survey_ops_per_order": round(SURVEY_OPS_PER_ORDER, 3),
                          "survey_frac": survey_achieved / INT32_PEAK_TOPS,
@@ -433,6 +465,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["tm", "reference"], default="tm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dkdt64x10")
+    ap.add_argument("--graph", action="store_true", help="replay each step as one CUDA graph")
     ap.add_argument("--tuning", default="",
                     help="pdmax,fuse_finalize,blocks_per_sm (skips the autotuner)")
     args = ap.parse_args(argv)

@@ -165,11 +165,15 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  thread to finish it (one launch fewer); 2: a separate
  *                  finalize kernel; 0: default (2)
  *   blocks_per_sm  resident enumeration blocks per SM used to size the
- *                  work split, 1..occupancy limit; 0: the occupancy limit */
+ *                  work split, 1..occupancy limit; 0: the occupancy limit
+ *   item_cost      the work split gives each thread the same estimated cost,
+ *                  a work item costing its orders plus item_cost (fixed
+ *                  per-item work, in orders); 0: default 4096 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;
     int32_t blocks_per_sm;
+    int32_t item_cost;
 } tm_tuning;
 
 int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tuning,
@@ -203,6 +207,23 @@ int tm_schedule_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
 int tm_schedule_batch(const tm_task* tasks, const int32_t* offsets, int G,
                       const tm_device* devs, tm_stats* stats,
                       int32_t* orders_out, int32_t* makespans_out /* may be NULL */);
+
+/* CUDA graph of one scheduling pass.  tm_plan_capture records one
+ * tm_schedule_batch_dev pass over these fixed device buffers (d_makespans
+ * and d_status may be NULL) into a graph owned by the plan (replacing any
+ * earlier one; timing events set with tm_plan_set_timing are recorded too);
+ * tm_plan_graph_launch replays it on a stream: same results, one launch call
+ * per pass.  The buffers must stay valid while the graph is used.  Capture
+ * uses a private stream of the library; it allocates the graph. */
+int tm_plan_capture(tm_plan* plan, const tm_task* d_tasks, const tm_device* d_devs,
+                    tm_stats* d_stats, int32_t* d_orders_out, int32_t* d_makespans_out,
+                    int32_t* d_status);
+int tm_plan_graph_launch(const tm_plan* plan, void* stream);
+
+/* If the graph was captured with timing events set (tm_plan_set_timing),
+ * makes later replays record these events instead, around the enumeration
+ * kernel (no new capture).  TM_EINVAL if the graph has no timing nodes. */
+int tm_plan_graph_set_timing(tm_plan* plan, void* event_before, void* event_after);
 
 /* Number of kernel launches one tm_exhaustive_batch_dev call enqueues
  * (tm_schedule_batch_dev enqueues the same number). */

@@ -22,8 +22,9 @@ from . import tm
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 CANDIDATES = {
     "pdmax": (3, 4, 5),
-    "fuse_finalize": (1, 2),
-    "blocks_per_sm": (0, 3, 2),
+    "fuse_finalize": (2,),
+    "blocks_per_sm": (0, 3),
+    "item_cost": (1024, 4096, 16384),
 }
 _lock = threading.Lock()
 

@@ -14,6 +14,9 @@ using tmgpu::Plan;
 
 struct tm_plan {
     Plan p;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};   // timing records, if captured
 };
 
 namespace {
@@ -108,7 +111,7 @@ struct Context {
 thread_local std::unique_ptr<Context> t_ctx;
 
 std::mutex g_tune_mu;
-tm_tuning g_default_tuning{0, 0, 0};
+tm_tuning g_default_tuning{0, 0, 0, 0};
 unsigned g_tuning_epoch = 0;   // bumped on every change; cached plans compare it
 
 int context(Context** out)
@@ -157,29 +160,25 @@ void free_plan(Plan& p)
     p.d_tbl = nullptr;
     p.d_sub = nullptr;
     p.d_acc = nullptr;
-    p.d_unit_group = nullptr;
     p.d_target = nullptr;
     p.d_done = nullptr;
 }
 
-// Host-side tables of the fused finalize: the group of every prep unit, and
-// per group the number of enumeration threads whose item range touches it
-// (thread t covers the items that start in orders [t W, (t + 1) W)).
+// Host-side table of the fused finalize: per group the number of
+// enumeration threads whose item range touches it (thread t covers the items
+// whose cost range starts in [t W, (t + 1) W)).
 void fused_tables(const Plan& p, const std::vector<tmgpu::GroupPlan>& gp,
-                  std::vector<uint32_t>& unit_group, std::vector<uint32_t>& target)
+                  std::vector<uint32_t>& target)
 {
-    unit_group.assign(std::max<uint32_t>(p.total_units, 1), 0);
-    for (int g = 0; g < p.G; ++g)
-        for (uint32_t u = gp[g].unit_base; u < gp[g + 1].unit_base; ++u) unit_group[u] = g;
     target.assign(std::max(p.G, 1), 0);
     const uint64_t W = p.leaves_per_thread, total = gp[p.G].cost_base;
     int g = 0;
     for (uint64_t t = 0; t < p.threads; ++t) {
         const uint64_t x0 = t * W;
         if (x0 >= total) break;
-        const uint32_t i0 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, x0);
-        const uint32_t i1 =
-            tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, std::min(x0 + W, total));
+        const uint32_t i0 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, p.item_cost, x0);
+        const uint32_t i1 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, p.item_cost,
+                                                   std::min(x0 + W, total));
         if (i0 >= i1) continue;
         while (gp[g + 1].item_base <= i0) ++g;        // the group holding item i0
         for (int h = g; h < p.G && gp[h].item_base < i1; ++h)
@@ -191,17 +190,18 @@ int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
 {
     const int pdmax = tune.pdmax == 0 ? 4 : tune.pdmax;
     const bool fused = tune.fuse_finalize == 1;
+    const uint32_t item_cost = tune.item_cost == 0 ? 4096u : (uint32_t)tune.item_cost;
     if (pdmax < 3 || pdmax > 5 || tune.fuse_finalize < 0 || tune.fuse_finalize > 2 ||
-        tune.blocks_per_sm < 0)
+        tune.blocks_per_sm < 0 || tune.item_cost < 0 || tune.item_cost > (1 << 20))
         return TM_EINVAL;
     if (!h_offsets || G < 0) return TM_EINVAL;
     std::vector<tmgpu::GroupPlan> gp((size_t)G + 1);
-    int rc = tmgpu::plan_decompose(h_offsets, G, pdmax, gp.data(), &p);
+    int rc = tmgpu::plan_decompose(h_offsets, G, pdmax, item_cost, gp.data(), &p);
     if (rc != TM_OK) return rc;
     TM_CUDA(cudaGetDevice(&p.device));
     tmgpu::exhaustive_partition(p, p.device, tune.blocks_per_sm);
-    std::vector<uint32_t> unit_group, target;
-    fused_tables(p, gp, unit_group, target);
+    std::vector<uint32_t> target;
+    fused_tables(p, gp, target);
     const size_t main_bytes = tmgpu::plan_carve(p, nullptr);
     const size_t fused_bytes = tmgpu::plan_carve_fused(p, nullptr);
     void* base = nullptr;
@@ -215,8 +215,6 @@ int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
     bool ok = cudaMemcpy(p.d_gp, gp.data(), gp.size() * sizeof(tmgpu::GroupPlan),
                          cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
-                         cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(p.d_unit_group, unit_group.data(), unit_group.size() * sizeof(uint32_t),
                          cudaMemcpyHostToDevice) == cudaSuccess &&
               (!fused ||
                (cudaMemcpy(p.d_target, target.data(), target.size() * sizeof(uint32_t),
@@ -253,7 +251,7 @@ int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tunin
                          tm_plan** plan_out)
 {
     if (!plan_out) return TM_EINVAL;
-    tm_tuning tune{0, 0, 0};
+    tm_tuning tune{0, 0, 0, 0};
     if (tuning) tune = *tuning;
     std::unique_ptr<tm_plan> plan(new (std::nothrow) tm_plan());
     if (!plan) return TM_ENOMEM;
@@ -275,10 +273,10 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
 
 int tm_set_default_tuning(const tm_tuning* tuning)
 {
-    tm_tuning t{0, 0, 0};
+    tm_tuning t{0, 0, 0, 0};
     if (tuning) t = *tuning;
     if ((t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
-        t.fuse_finalize > 2 || t.blocks_per_sm < 0)
+        t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 || t.item_cost > (1 << 20))
         return TM_EINVAL;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_default_tuning = t;
@@ -289,8 +287,76 @@ int tm_set_default_tuning(const tm_tuning* tuning)
 void tm_plan_destroy(tm_plan* plan)
 {
     if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
     free_plan(plan->p);
     delete plan;
+}
+
+int tm_plan_capture(tm_plan* plan, const tm_task* d_tasks, const tm_device* d_devs,
+                    tm_stats* d_stats, int32_t* d_orders_out, int32_t* d_makespans_out,
+                    int32_t* d_status)
+{
+    if (!plan) return TM_EINVAL;
+    if (plan->p.G > 0 && (!d_tasks || !d_devs || !d_stats || !d_orders_out)) return TM_EINVAL;
+    cudaStream_t s = nullptr;
+    TM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = tmgpu::launch_exhaustive(plan->p, d_tasks, d_devs, d_stats, d_status, s,
+                                                  d_orders_out, d_makespans_out);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return TM_ECUDA;
+    }
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    plan->graph = graph;
+    plan->exec = exec;
+    plan->ev_node[0] = plan->ev_node[1] = nullptr;
+    size_t count = 0;
+    if (plan->p.ev_before && cudaGraphGetNodes(graph, nullptr, &count) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(count);
+        if (cudaGraphGetNodes(graph, nodes.data(), &count) == cudaSuccess) {
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType type;
+                cudaEvent_t ev = nullptr;
+                if (cudaGraphNodeGetType(nd, &type) != cudaSuccess ||
+                    type != cudaGraphNodeTypeEventRecord ||
+                    cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess)
+                    continue;
+                if (ev == plan->p.ev_before) plan->ev_node[0] = nd;
+                if (ev == plan->p.ev_after) plan->ev_node[1] = nd;
+            }
+        }
+    }
+    return TM_OK;
+}
+
+int tm_plan_graph_set_timing(tm_plan* plan, void* event_before, void* event_after)
+{
+    if (!plan || !plan->exec || !plan->ev_node[0] || !plan->ev_node[1] || !event_before ||
+        !event_after)
+        return TM_EINVAL;
+    if (cudaGraphExecEventRecordNodeSetEvent(plan->exec, plan->ev_node[0],
+                                             (cudaEvent_t)event_before) != cudaSuccess ||
+        cudaGraphExecEventRecordNodeSetEvent(plan->exec, plan->ev_node[1],
+                                             (cudaEvent_t)event_after) != cudaSuccess)
+        return TM_ECUDA;
+    return TM_OK;
+}
+
+int tm_plan_graph_launch(const tm_plan* plan, void* stream)
+{
+    if (!plan || !plan->exec) return TM_EINVAL;
+    return cudaGraphLaunch(plan->exec, (cudaStream_t)stream) == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
 int tm_plan_launches(const tm_plan* plan) { return plan ? plan->p.launches : 0; }

@@ -221,18 +221,19 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 
 // ---- prep: validation, padded task table, suffix tables -------------------
 
-// One warp per unit: a group with n >= 4 tasks has C(n, 4) units (its
-// 4-subsets in colexicographic order), smaller groups one unit.  Lane i
-// holds task i; lane j < 24 tabulates order j of S.  The warp of a group's
-// first unit also validates the group and writes its GroupInfo and padded
-// task table.
+// One block per group (128 threads, or 512 when the batch has groups with
+// many 4-subsets).  Warp 0 loads and validates the group (lane i holds task
+// i) and writes its GroupInfo and padded task table (and finishes groups of
+// n <= 3 outright); then the block's threads stride over the (4-subset,
+// order) pairs of the group and tabulate alpha / beta / gamma.  When the
+// heuristic is requested, the last warp runs it for the group meanwhile.
+constexpr int kPrepMaxThreads = 512;
+
 struct PrepArgs {
     const tm_task* tasks;
     const tm_device* devs;
     const GroupPlan* gp;
-    const uint32_t* unit_group;   // may be null: binary search instead
     int G;
-    uint32_t total_units;
     GroupInfo* info;
     int4* tbl;
     SuffixTab* sub;
@@ -242,46 +243,40 @@ struct PrepArgs {
     int32_t* makespans;
 };
 
-__global__ void prep_kernel(PrepArgs a)
+__global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
 {
-    const uint32_t u = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    const tm_task* __restrict__ tasks = a.tasks;
+    const int kPrepThreads = blockDim.x;
+    const int g = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GroupPlan* __restrict__ gp = a.gp;
-    const int G = a.G;
-    if (u >= a.total_units) {
-        // the heuristic (Algorithm 1) of group u - total_units, in the same launch
-        const uint32_t hg = u - a.total_units;
-        if (a.orders && hg < (uint32_t)G) {
-            const int off = gp[hg].off;
-            heur::heuristic_group(tasks, off, gp[hg + 1].off - off, a.devs[hg].dma_engines,
-                                  (int)hg, lane, a.orders, a.makespans, nullptr);
-        }
-        return;
-    }
-    const int g = a.unit_group ? (int)a.unit_group[u]
-                               : search_group(G, u, [&](int i) { return (uint64_t)gp[i].unit_base; });
-    GroupInfo* __restrict__ info = a.info;
-    int4* __restrict__ tbl = a.tbl;
-    SuffixTab* __restrict__ sub = a.sub;
     const int off = gp[g].off;
     const int n = gp[g + 1].off - off;
-    const uint32_t s = u - gp[g].unit_base;
-    const bool mine = lane < n;
-    tm_task t = mine ? tasks[off + lane] : tm_task{0, 0, 0};
-    const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
-    unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
-    // with no negative duration and tot <= INT32_MAX the HtD sum fits
-    const int32_t hs = (int32_t)__reduce_add_sync(kFull, mine ? (uint32_t)t.htd : 0u);
     const int dma = a.devs[g].dma_engines;
-    int status = 0;
-    if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
-    else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
-    else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
-    if (s == 0) {
-        if (status == 0 && mine) tbl[off + lane] = make_int4(t.htd, t.k, t.dth, 0);
+    __shared__ int4 s_task[TM_MAX_EXHAUSTIVE];
+    __shared__ int s_status, s_hs;
+
+    const bool heur = a.orders != nullptr;
+    if (heur && warp == kPrepThreads / 32 - 1) {
+        heur::heuristic_group(a.tasks, off, n, dma, g, lane, a.orders, a.makespans, nullptr);
+        return;   // this warp takes no part in the barrier below
+    }
+    if (warp == 0) {
+        const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
+        tm_task t = mine ? a.tasks[off + lane] : tm_task{0, 0, 0};
+        const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
+        unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+        // with no negative duration and tot <= INT32_MAX the HtD sum fits
+        const int32_t hs = (int32_t)__reduce_add_sync(kFull, mine ? (uint32_t)t.htd : 0u);
+        int status = 0;
+        if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
+        else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
+        else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
+        if (mine) {
+            s_task[lane] = make_int4(t.htd, t.k, t.dth, 0);
+            if (status == 0) a.tbl[off + lane] = s_task[lane];
+        }
         if (lane == 0) {
             GroupInfo gi;
             gi.off = off;
@@ -291,37 +286,39 @@ __global__ void prep_kernel(PrepArgs a)
             gi.status = status;
             gi.sum32 = tot * 24u < (1ull << 32) ? 1u : 0u;
             gi.pad0 = gi.pad1 = 0;
-            info[g] = gi;
+            a.info[g] = gi;
             if (status != 0 && a.status) a.status[g] = status;
+            s_status = status;
+            s_hs = hs;
         }
         if (status == 0 && n <= 3) {       // at most 6 orders: finish here
             __syncwarp();
-            small_group_stats(tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
+            small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
             if (lane == 0 && a.status) a.status[g] = 0;
         }
     }
-    if (status != 0 || n < 4) return;
+    const int workers = heur ? kPrepThreads - 32 : kPrepThreads;
+    asm volatile("bar.sync 1, %0;" ::"r"(workers));   // the warps below only
+    if (s_status != 0 || n < 4) return;
 
-    // the set S, ascending, broadcast from the lanes holding its tasks
-    const uint32_t mask = c_subsets.m[s];
-    int e[4];
-    for (int q = 0, m = (int)mask; q < 4; ++q) {
-        e[q] = __ffs(m) - 1;
-        m &= m - 1;
-    }
-    int32_t H[4], K[4], D[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        H[q] = __shfl_sync(kFull, t.htd, e[q]);
-        K[q] = __shfl_sync(kFull, t.k, e[q]);
-        D[q] = __shfl_sync(kFull, t.dth, e[q]);
-    }
-    SuffixTab* out = sub + gp[g].sub_base + s;
-    if (lane < 24) {
-        // order `lane` of S in lexicographic order: Lehmer digits 6, 2, 1
-        const int d0 = lane / 6, d1 = (lane % 6) / 2, d2 = lane % 2;
+    // beta: the makespan when only the K-engine time (= 0) enters S;
+    // gamma: when only the HtD-engine time (= hs - sum of S's HtD) enters S.
+    // A very negative start removes the other engines from the max-plus paths.
+    const int64_t NEG = -(int64_t(1) << 40);
+    const int32_t hs = s_hs;
+    SuffixTab* out = a.sub + gp[g].sub_base;
+    const uint32_t pairs = choose4(n) * 24u;
+    for (uint32_t pj = tid; pj < pairs; pj += workers) {
+        const uint32_t s = pj / 24, j = pj - s * 24;
+        const uint32_t mask = c_subsets.m[s];
+        int4 t4[4];
+        for (int q = 0, m = (int)mask; q < 4; ++q) {
+            t4[q] = s_task[__ffs(m) - 1];
+            m &= m - 1;
+        }
+        // order j of S in lexicographic order: Lehmer digits 6, 2, 1
+        const int dg[3] = {(int)j / 6, ((int)j % 6) / 2, (int)j % 2};
         int slots = 0x3210, order[4];
-        const int dg[3] = {d0, d1, d2};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const int c = dg[q];
@@ -330,27 +327,22 @@ __global__ void prep_kernel(PrepArgs a)
             slots = low | ((slots >> (4 * c + 4)) << (4 * c));
         }
         order[3] = slots & 0xF;
-        // beta: the makespan when only the K-engine time (= 0) enters S;
-        // gamma: when only the HtD-engine time (= hs - sum of S's HtD)
-        // enters S.  A very negative start removes the other engines.
-        const int64_t NEG = -(int64_t(1) << 40);
-        int64_t hS = (int64_t)hs - H[0] - H[1] - H[2] - H[3];
+        int64_t hS = (int64_t)hs - t4[0].x - t4[1].x - t4[2].x - t4[3].x;
         int64_t bh = NEG, bk = 0, bd = NEG, gh = hS, gk = NEG, gd = NEG;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int x = order[q];
-            const int64_t h = x == 0 ? H[0] : x == 1 ? H[1] : x == 2 ? H[2] : H[3];
-            const int64_t k = x == 0 ? K[0] : x == 1 ? K[1] : x == 2 ? K[2] : K[3];
-            const int64_t d = x == 0 ? D[0] : x == 1 ? D[1] : x == 2 ? D[2] : D[3];
-            bh += h; bk = max(bk, bh) + k; bd = max(bd, bk) + d;
-            gh += h; gk = max(gk, gh) + k; gd = max(gd, gk) + d;
+            const int4 t = x == 0 ? t4[0] : x == 1 ? t4[1] : x == 2 ? t4[2] : t4[3];
+            bh += t.x; bk = max(bk, bh) + t.y; bd = max(bd, bk) + t.z;
+            gh += t.x; gk = max(gk, gh) + t.y; gd = max(gd, gk) + t.z;
         }
-        out->beta[lane] = (int32_t)bd;
-        out->gamma[lane] = (int32_t)gd;
-    } else if (lane == 24) {
-        out->alpha = D[0] + D[1] + D[2] + D[3];
-        out->mask = mask;
-        out->pad0 = out->pad1 = 0;
+        out[s].beta[j] = (int32_t)bd;
+        out[s].gamma[j] = (int32_t)gd;
+        if (j == 0) {
+            out[s].alpha = t4[0].z + t4[1].z + t4[2].z + t4[3].z;
+            out[s].mask = mask;
+            out[s].pad0 = out[s].pad1 = 0;
+        }
     }
 }
 
@@ -650,14 +642,14 @@ template <int PDMAX>
 __global__ void __launch_bounds__(kEnumBlock, 4)
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
-            uint64_t per_thread, Sink sink)
+            uint64_t per_thread, uint32_t item_cost, Sink sink)
 {
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t x0 = t * per_thread;
     const uint64_t total = gp[G].cost_base;
     if (x0 >= total) return;
-    uint32_t i = plan_first_item(gp, G, PDMAX, x0);
-    const uint32_t end = plan_first_item(gp, G, PDMAX, min(x0 + per_thread, total));
+    uint32_t i = plan_first_item(gp, G, PDMAX, item_cost, x0);
+    const uint32_t end = plan_first_item(gp, G, PDMAX, item_cost, min(x0 + per_thread, total));
     if (i >= end) return;
     int g = search_group(G, i, [&](int j) { return (uint64_t)gp[j].item_base; });
 
@@ -766,7 +758,8 @@ cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
 {
     uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
     enum_kernel<PDMAX><<<blocks, kEnumBlock, 0, stream>>>(p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G,
-                                                           p.leaves_per_thread, sink);
+                                                           p.leaves_per_thread, p.item_cost,
+                                                           sink);
     return cudaGetLastError();
 }
 
@@ -812,9 +805,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.tasks = d_tasks;
     pa.devs = d_devs;
     pa.gp = p.d_gp;
-    pa.unit_group = p.d_unit_group;
     pa.G = p.G;
-    pa.total_units = p.total_units;
     pa.info = p.d_info;
     pa.tbl = p.d_tbl;
     pa.sub = p.d_sub;
@@ -822,13 +813,21 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.status = d_status;
     pa.orders = d_orders;
     pa.makespans = d_makespans;
-    const uint64_t prep_threads = ((uint64_t)p.total_units + (d_orders ? p.G : 0)) * 32;
-    prep_kernel<<<(unsigned)((prep_threads + 255) / 256), 256, 0, stream>>>(pa);
+    // many (subset, order) pairs per group (n >= 9: >= 3,024): a bigger block
+    prep_kernel<<<p.G, p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
         Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done};
-        if (p.ev_before && (e = cudaEventRecord(p.ev_before, stream)) != cudaSuccess) return e;
+        // Under stream capture, an external record becomes an event-record
+        // node of the graph (a plain record would only order the capture).
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (p.ev_before && (e = cudaStreamIsCapturing(stream, &cap)) != cudaSuccess) return e;
+        const unsigned rec_flags =
+            cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (p.ev_before &&
+            (e = cudaEventRecordWithFlags(p.ev_before, stream, rec_flags)) != cudaSuccess)
+            return e;
         switch (p.pdmax) {
         case 3: e = launch_enum<3>(p, sink, stream); break;
         case 4: e = launch_enum<4>(p, sink, stream); break;
@@ -836,7 +835,9 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
-        if (p.ev_after && (e = cudaEventRecord(p.ev_after, stream)) != cudaSuccess) return e;
+        if (p.ev_after &&
+            (e = cudaEventRecordWithFlags(p.ev_after, stream, rec_flags)) != cudaSuccess)
+            return e;
         if (!p.d_done) {
             finalize_kernel<<<(p.G * 32 + 255) / 256, 256, 0, stream>>>(p.d_info, p.d_tbl, p.G,
                                                                         p.d_acc, d_stats, d_status);

@@ -81,7 +81,7 @@ extern "C" int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t
     InitArgs a;
     a.G = G;
     Plan p;
-    int rc = plan_decompose(h_offsets, G, kPdmax, a.gp, &p);
+    int rc = plan_decompose(h_offsets, G, kPdmax, 256u, a.gp, &p);
     if (rc != TM_OK) return rc;
     if (p.T > TM_NOALLOC_MAX_TASKS || p.total_subs > TM_NOALLOC_MAX_SUBSETS ||
         plan_carve(p, nullptr) > kScratchBytes)

@@ -46,8 +46,9 @@ struct GroupInfo {
 // Per-group work layout computed on the host from the group sizes alone.
 // Entry G holds the totals.
 struct GroupPlan {
-    uint64_t cost_base;   // first order (leaf) of the group among all groups
-                          // with n >= 4, in work-item order
+    uint64_t cost_base;   // first cost unit of the group: each work item of a
+                          // group with n >= 4 costs its orders plus a fixed
+                          // per-item overhead (the plan's item_cost)
     uint32_t item_base;   // first work item
     uint32_t unit_base;   // first thread of the prep / suffix-table kernel
     uint32_t sub_base;    // first suffix-table entry
@@ -76,7 +77,8 @@ struct Plan {
     int T = 0;                    // total tasks
     int pdmax = 4;                // prefix positions walked depth-first per item
     uint32_t total_items = 0;     // work items over all groups
-    uint64_t total_leaves = 0;    // orders of all groups with n >= 4
+    uint64_t total_leaves = 0;    // cost units of all work items (see GroupPlan)
+    uint32_t item_cost = 256;     // per-item overhead, in orders
     uint32_t total_units = 0;     // prep / suffix-table threads
     uint32_t total_subs = 0;      // suffix-table entries
     uint32_t threads = 0;         // enumeration threads
@@ -91,7 +93,6 @@ struct Plan {
     // to finish with it.  d_target[g] counts the threads whose item range
     // touches group g; d_done[g] counts those that finished.  Without these
     // (nullptr) a separate finalize kernel runs.
-    uint32_t* d_unit_group = nullptr;     // [total_units] group of each prep unit
     uint32_t* d_target = nullptr;         // [G]
     uint32_t* d_done = nullptr;           // [kDoneStride G]
     cudaEvent_t ev_before = nullptr;      // optional timing hook
@@ -105,8 +106,8 @@ __host__ __device__ inline int plan_pd(int n, int pdmax) { return n - 4 < pdmax 
 
 // Fills gp[0..G] from host offsets; allocates nothing.  Returns TM_OK,
 // TM_EINVAL (bad offsets) or TM_ETOOBIG (n > 12 or too many items).
-inline int plan_decompose(const int32_t* offsets, int G, int pdmax, GroupPlan* gp,
-                          Plan* totals)
+inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t item_cost,
+                          GroupPlan* gp, Plan* totals)
 {
     if (!offsets || G < 0 || offsets[0] != 0 || pdmax < 2 || pdmax > 5) return TM_EINVAL;
     uint64_t cost = 0, items = 0, units = 0, subs = 0;
@@ -126,7 +127,7 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, GroupPlan* g
             int P = n - 4, pd = plan_pd(n, pdmax);
             uint64_t heads = factorial_u64(P) / factorial_u64(pd);
             items += (uint64_t)c4 * heads;
-            cost += factorial_u64(n);
+            cost += (uint64_t)c4 * heads * (24ull * factorial_u64(pd) + item_cost);
         }
         if (items >= 0xFFFFFFFFull || units >= 0xFFFFFFFFull) return TM_ETOOBIG;
     }
@@ -138,6 +139,7 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, GroupPlan* g
     totals->G = G;
     totals->T = offsets[G];
     totals->pdmax = pdmax;
+    totals->item_cost = item_cost;
     totals->total_items = (uint32_t)items;
     totals->total_leaves = cost;
     totals->total_units = (uint32_t)units;
@@ -178,17 +180,15 @@ inline size_t plan_carve_fused(Plan& p, unsigned char* base)
         return at;
     };
     const size_t G1 = (size_t)(p.G > 0 ? p.G : 1);
-    const size_t U1 = (size_t)(p.total_units > 0 ? p.total_units : 1);
-    p.d_unit_group = reinterpret_cast<uint32_t*>(take(U1 * sizeof(uint32_t)));
     p.d_target = reinterpret_cast<uint32_t*>(take(G1 * sizeof(uint32_t)));
     p.d_done = reinterpret_cast<uint32_t*>(take(kDoneStride * G1 * sizeof(uint32_t)));
     return off;
 }
 
-// First work item whose first order is at or after global order index x
-// (host and device).  pdmax as in the plan.
+// First work item whose first cost unit is at or after x (host and device);
+// pdmax and item_cost as in the plan.
 __host__ __device__ inline uint32_t plan_first_item(const GroupPlan* gp, int G, int pdmax,
-                                                    uint64_t x)
+                                                    uint32_t item_cost, uint64_t x)
 {
     if (x >= gp[G].cost_base) return gp[G].item_base;
     int lo = 0, hi = G;                       // largest g with cost_base <= x
@@ -197,7 +197,7 @@ __host__ __device__ inline uint32_t plan_first_item(const GroupPlan* gp, int G, 
         if (gp[mid].cost_base <= x) lo = mid; else hi = mid;
     }
     const int n = gp[lo + 1].off - gp[lo].off;
-    const uint64_t lpi = 24ull * factorial_u64(plan_pd(n, pdmax));
+    const uint64_t lpi = 24ull * factorial_u64(plan_pd(n, pdmax)) + item_cost;
     const uint64_t q = (x - gp[lo].cost_base + lpi - 1) / lpi;
     const uint64_t i = gp[lo].item_base + q;
     return (uint32_t)(i < gp[lo + 1].item_base ? i : gp[lo + 1].item_base);

@@ -69,6 +69,9 @@ _SIGS = {
     "tm_plan_destroy": [_vp],
     "tm_plan_launches": [_vp],
     "tm_plan_set_timing": [_vp, _vp, _vp],
+    "tm_plan_capture": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "tm_plan_graph_launch": [_vp, _vp],
+    "tm_plan_graph_set_timing": [_vp, _vp, _vp],
     "tm_exhaustive_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tm_exhaustive_batch_noalloc": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "tm_schedule_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -261,25 +264,28 @@ def tm_heuristic_batch_dev(d_tasks, d_offsets, G: int, d_devs, d_orders_out,
 
 
 class Tuning(ctypes.Structure):
-    """tm_tuning: pdmax (3..5), fuse_finalize (1 fused, 2 separate), blocks_per_sm; 0 = default."""
+    """tm_tuning: pdmax (3..5), fuse_finalize (1 fused, 2 separate), blocks_per_sm,
+    item_cost; 0 = default."""
     _fields_ = [("pdmax", ctypes.c_int32), ("fuse_finalize", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("item_cost", ctypes.c_int32)]
 
 
-def tm_set_default_tuning(pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0):
+def tm_set_default_tuning(pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0,
+                          item_cost: int = 0):
     """Tuning for plans made by tm_plan_create and the host-pointer calls."""
-    t = Tuning(pdmax, fuse_finalize, blocks_per_sm)
+    t = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost)
     _check(lib().tm_set_default_tuning(ctypes.byref(t)), "tm_set_default_tuning")
 
 
 class Plan:
     """Owns a tm_plan (exhaustive search over a fixed set of group sizes)."""
 
-    def __init__(self, offsets, pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0):
+    def __init__(self, offsets, pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0,
+                 item_cost: int = 0):
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
         self.G = off.shape[0] - 1
         self.offsets = off
-        self.tuning = Tuning(pdmax, fuse_finalize, blocks_per_sm)
+        self.tuning = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost)
         h = ctypes.c_void_p()
         _check(lib().tm_plan_create_tuned(_p(off), self.G, ctypes.byref(self.tuning),
                                           ctypes.byref(h)), "tm_plan_create_tuned")
@@ -298,6 +304,23 @@ class Plan:
         h = lambda e: None if e is None else ctypes.c_void_p(int(getattr(e, "cuda_event", e)))
         _check(lib().tm_plan_set_timing(self._h, h(event_before), h(event_after)),
                "tm_plan_set_timing")
+
+    def capture(self, d_tasks, d_devs, d_stats, d_orders_out, d_makespans_out=None,
+                d_status=None):
+        """Records one tm_schedule_batch_dev pass over these buffers as a CUDA graph."""
+        _check(lib().tm_plan_capture(self._h, _dptr(d_tasks), _dptr(d_devs), _dptr(d_stats),
+                                     _dptr(d_orders_out), _dptr(d_makespans_out),
+                                     _dptr(d_status)), "tm_plan_capture")
+
+    def graph_launch(self, stream=None):
+        """Replays the captured pass on a stream."""
+        _check(lib().tm_plan_graph_launch(self._h, _stream(stream)), "tm_plan_graph_launch")
+
+    def graph_set_timing(self, event_before, event_after):
+        """Swaps the timing events recorded by the captured graph."""
+        h = lambda e: ctypes.c_void_p(int(getattr(e, "cuda_event", e)))
+        _check(lib().tm_plan_graph_set_timing(self._h, h(event_before), h(event_after)),
+               "tm_plan_graph_set_timing")
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

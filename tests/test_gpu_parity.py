@@ -263,7 +263,8 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
 
 @pytest.mark.parametrize("tuning", [dict(pdmax=3), dict(pdmax=5), dict(fuse_finalize=1),
                                     dict(pdmax=5, fuse_finalize=1, blocks_per_sm=2),
-                                    dict(pdmax=3, blocks_per_sm=1)])
+                                    dict(pdmax=3, blocks_per_sm=1), dict(item_cost=1),
+                                    dict(pdmax=4, item_cost=5000)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
@@ -293,6 +294,43 @@ def test_every_tuning_gives_identical_results(tm, tuning):
     ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
     for g in small:
         assert_stats_equal(got[g], ref[g], g)
+
+
+def test_cuda_graph_replay_matches_direct_call(tm):
+    import torch
+    dev = torch.device("cuda")
+    b = inputs.ragged_mixed(groups=300, seed=31)
+    plan = tm.Plan(b.offsets)
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    bufs = []
+    for _ in range(2):
+        bufs.append((torch.zeros(b.G * 72, dtype=torch.uint8, device=dev),
+                     torch.zeros(b.tasks.shape[0], dtype=torch.int32, device=dev),
+                     torch.zeros(b.G, dtype=torch.int32, device=dev),
+                     torch.full((b.G,), 9, dtype=torch.int32, device=dev)))
+    tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, *bufs[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(); e1.record()
+    plan.set_timing(e0, e1)
+    plan.capture(d_tasks, d_dma, *bufs[1])
+    plan.set_timing(None, None)
+    for _ in range(3):
+        plan.graph_launch()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(); f1.record()
+    plan.graph_set_timing(f0, f1)
+    plan.graph_launch()
+    torch.cuda.synchronize()
+    assert f0.elapsed_time(f1) > 0
+    for x, y in zip(bufs[0], bufs[1]):
+        assert torch.equal(x, y)
+    assert (bufs[1][3].cpu().numpy() == 0).all()
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    got = tm.stats_to_dicts(bufs[1][0].cpu().numpy().view(tm.STATS_DTYPE), b.sizes())
+    for g in range(0, b.G, 7):
+        assert_stats_equal(got[g], ref[g], g)
+    plan.close()
 
 
 # ---- device-pointer entry points ----------------------------------------------------
