@@ -51,7 +51,9 @@ MUTANTS = {
 def test_pins_catch_mutant(name, tmp_path):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    # every copy of the anchor is mutated (the full search and the prefix
+    # samples share the reduction rule)
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     mut = tmp_path / "tm_oracle.cpp"
     mut.write_text(src.replace(old, new))
     hdr = os.path.join(ROOT, "oracle", "tm_oracle.h")
