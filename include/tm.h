@@ -269,6 +269,105 @@ int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t* h_offsets
                                 int G, const tm_device* d_devs, tm_stats* d_stats,
                                 int32_t* d_status /* may be NULL */, void* stream);
 
+/* ---- learned order ranker and beam search --------------------------------- */
+
+/* The paper has no learned component and no search beyond its O(n^2)
+ * heuristic (Sec. 5.1); exhaustive search (above) stops at n = 12.  For
+ * groups up to TM_MAX_TASKS (16) the library also offers a beam search whose
+ * proposals come from a small learned ranker, the exact model (Sec. 4.1)
+ * judging every order it returns.
+ *
+ * THE RANKER.  A 4-layer perceptron, 32 -> 128 -> 128 -> 128 -> 1 with ReLU,
+ * scores "append task j next" from 32 features of task j, of the engine
+ * times (end of the last HtD, K and DtH, Sec. 4.1) after the placed prefix
+ * and of the tasks still unplaced, times scaled by n / (sum of the group's
+ * durations).  Weights and activations are bfloat16 with float32
+ * accumulation; the master parameters are float32, trained with Adam on the
+ * softmax cross-entropy of each state's candidates against the task that a
+ * reference order (normally the exhaustive best order) places there.
+ * Parameters: one float32 vector of TM_RANKER_PARAMS values, laid out
+ *   W1 [32 x 128] (row-major, input x output), b1 [128], W2 [128 x 128],
+ *   b2 [128], W3 [128 x 128], b3 [128], w4 [128], b4 [1].
+ * Feature rows are bfloat16 bit patterns (uint16_t), TM_RANKER_FEATURES per
+ * row.  A ranker lives on the device that was current at creation; calls
+ * with another device current return TM_EINVAL.  One ranker must not be
+ * used by two calls that can run at the same time (it owns the scratch of
+ * its training and beam calls, grown on demand with cudaMalloc). */
+#define TM_RANKER_FEATURES 32
+#define TM_RANKER_PARAMS 37377
+#define TM_BEAM_MAX_WIDTH 64
+
+typedef struct tm_ranker tm_ranker;
+
+/* Allocates a ranker with He-uniform weights drawn by SplitMix64 from
+ * `seed` (zero biases, zero Adam moments).  Synchronous. */
+int tm_ranker_create(uint64_t seed, tm_ranker** ranker_out);
+void tm_ranker_destroy(tm_ranker* ranker);
+
+/* Copies the TM_RANKER_PARAMS float32 parameters out / in (host arrays;
+ * synchronous: waits for the device).  set_params also resets the Adam
+ * moments and step count. */
+int tm_ranker_get_params(const tm_ranker* ranker, float* h_params);
+int tm_ranker_set_params(tm_ranker* ranker, const float* h_params);
+
+/* Training rows of a batch (host offsets): a group of n >= 2 tasks has
+ * n - 1 states (positions p = 0 .. n - 2) with n - p candidate rows each,
+ * n (n + 1) / 2 - 1 rows in all; n = 1 has none.  TM_EINVAL for bad
+ * offsets, TM_ECAPACITY when rows would pass INT32_MAX - 16. */
+int tm_ranker_rows_count(const int32_t* h_offsets, int G, int64_t* rows,
+                         int32_t* states);
+
+/* Builds the training rows of every group along its reference order:
+ * d_orders (task layout, as tm_predict_batch_dev) or, if d_orders is NULL,
+ * the best_order of d_stats[G] (from tm_exhaustive_batch_dev).  rows and
+ * states must be tm_ranker_rows_count's values for these offsets.
+ * Outputs: d_X [ceil16(rows) x 32] (rows past `rows` are zeroed),
+ * d_state_off [states + 1] (state s owns rows d_state_off[s] ..
+ * d_state_off[s + 1]), d_target [states] (the row of the placed task).
+ * Candidates of a state come in ascending task index.  A group that fails
+ * its input check, or whose order is not a permutation, gets zero rows and
+ * its code in d_status (may be NULL).  Stream-ordered. */
+int tm_ranker_rows_dev(tm_ranker* ranker, const tm_task* d_tasks,
+                       const int32_t* d_offsets, int G, const tm_device* d_devs,
+                       const int32_t* d_orders, const tm_stats* d_stats,
+                       int64_t rows, int32_t states, uint16_t* d_X,
+                       int32_t* d_state_off, int32_t* d_target,
+                       int32_t* d_status, void* stream);
+
+/* Scores rows: d_logits[rows] from d_X [rows x 32].  Stream-ordered. */
+int tm_ranker_forward_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
+                          float* d_logits, void* stream);
+
+/* Loss (mean over states of the softmax cross-entropy) and its gradient with
+ * respect to the parameters, kept in the ranker for tm_ranker_adam_dev and
+ * copied to d_grad [TM_RANKER_PARAMS] / d_loss [1] when those are not NULL.
+ * d_X must hold ceil16(rows) rows whose tail past `rows` is zero (as
+ * tm_ranker_rows_dev leaves it).  Stream-ordered. */
+int tm_ranker_grad_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
+                       const int32_t* d_state_off, const int32_t* d_target,
+                       int32_t states, float* d_grad, float* d_loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr
+ * on the gradient of the last tm_ranker_grad_dev.  Stream-ordered. */
+int tm_ranker_adam_dev(tm_ranker* ranker, float lr, void* stream);
+
+/* Beam search over orders for every group (1 <= n <= 16; h_offsets is the
+ * HOST copy of d_offsets).  Position by position, every live beam proposes
+ * each unplaced task, the ranker scores the proposals, and the beam_width
+ * (1 .. TM_BEAM_MAX_WIDTH) best by summed log-softmax score survive (ties:
+ * lower beam, then lower task index); each beam carries the exact int32
+ * engine times of its prefix.  The result is the finished beam with the
+ * smallest makespan if it beats the heuristic's order (tm_heuristic_batch_dev,
+ * run first), else the heuristic's order: never worse than the heuristic.
+ * Writes d_orders_out (task layout), d_makespans_out [G] (may be NULL),
+ * d_status [G] (may be NULL) and d_beam_won [G] (may be NULL; 1 where the
+ * beam's order was kept).  Stream-ordered. */
+int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
+                      const int32_t* d_offsets, const int32_t* h_offsets, int G,
+                      const tm_device* d_devs, int beam_width,
+                      int32_t* d_orders_out, int32_t* d_makespans_out,
+                      int32_t* d_status, int32_t* d_beam_won, void* stream);
+
 /* ---- misc ---------------------------------------------------------------- */
 
 const char* tm_strerror(int code);

@@ -1,0 +1,411 @@
+// beam.cu -- beam search over task orders with the learned ranker, for
+// groups beyond exhaustive reach (up to 16 tasks).  The paper has no
+// counterpart; its exact model judges every order: each beam carries the
+// exact int32 engine times of its prefix (the recurrence of tm_device.cuh),
+// so a finished beam's makespan is exact, and the result is the better of
+// the best finished beam and the paper's heuristic order (Algorithm 1).
+//
+// The same feature map also builds the ranker's training rows along given
+// orders (rows_kernel).
+//
+// Step i (the i-th position): every live beam b of group g proposes each of
+// its unused tasks; row ((g * B + b) * R + slot) of the feature matrix holds
+// the features of "append the slot-th unused task", R = nmax - i.  The
+// ranker scores the rows; a block per group turns scores into log-softmax
+// over each beam's candidates, adds the beam's log-probability, keeps the
+// best B candidates (bitonic sort in shared memory; ties: lower beam, then
+// lower slot) and applies them.
+#include <cuda_bf16.h>
+
+#include "rank_features.cuh"
+#include "ranker.h"
+#include "tm_device.cuh"
+
+namespace tmgpu {
+
+struct BeamState {
+    int32_t h, k, d;
+    uint32_t used;
+    unsigned long long order;   // task at position p in bits 4p .. 4p + 3
+    float logp;
+    int32_t alive;
+};
+static_assert(sizeof(BeamState) == 32, "beam state layout");
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSelectThreads = 512;
+constexpr int kMaxCand = 64 * 16;   // beam width <= 64, tasks <= 16
+
+__device__ __forceinline__ int slot_task(uint32_t used, int n, int slot)
+{
+    // the slot-th task not in `used`
+    uint32_t free_mask = ((n >= 32) ? kFull : ((1u << n) - 1u)) & ~used;
+    for (int s = 0; s < slot; ++s) free_mask &= free_mask - 1;
+    return __ffs(free_mask) - 1;
+}
+
+__global__ void beam_init_kernel(const int32_t* __restrict__ offsets,
+                                 const int32_t* __restrict__ status, const tm_task* __restrict__ tasks,
+                                 const tm_device* __restrict__ devs, int G, int B,
+                                 BeamState* __restrict__ st, float* __restrict__ scale)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G * B) return;
+    const int g = t / B, b = t - g * B;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    BeamState s;
+    s.h = s.k = s.d = 0;
+    s.used = 0;
+    s.order = 0;
+    s.logp = 0.0f;
+    s.alive = (b == 0 && status[g] == 0) ? 1 : 0;
+    if (b == 0) {
+        int64_t hs = 0, total = 0;
+        for (int i = 0; i < n && status[g] == 0; ++i) {
+            hs += tasks[off + i].htd;
+            total += (int64_t)tasks[off + i].htd + tasks[off + i].k + tasks[off + i].dth;
+        }
+        if (devs[g].dma_engines == 1) s.d = (int32_t)hs;   // one transfer queue
+        scale[g] = total > 0 ? (float)n / (float)total : 0.0f;
+    }
+    st[t] = s;
+}
+
+// Feature rows of step i.  One thread per (g, b, slot).
+__global__ void beam_features_kernel(const int32_t* __restrict__ offsets,
+                                     const tm_task* __restrict__ tasks,
+                                     const tm_device* __restrict__ devs,
+                                     const float* __restrict__ scale, const BeamState* __restrict__ st,
+                                     int G, int B, int R, int pos, __nv_bfloat16* __restrict__ X)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows = (int64_t)G * B * R;
+    if (row >= rows) return;
+    const int gb = (int)(row / R), slot = (int)(row - (int64_t)gb * R);
+    const int g = gb / B;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    const BeamState s = st[gb];
+    float f[kFeat];
+    if (s.alive && pos < n && slot < n - pos) {
+        const int j = slot_task(s.used, n, slot);
+        rank_features(tasks + off, n, s.used, s.h, s.k, s.d, devs[g].dma_engines, scale[g], j, f);
+    } else {
+        for (int q = 0; q < kFeat; ++q) f[q] = 0.0f;
+    }
+    __nv_bfloat16* x = X + row * kFeat;
+#pragma unroll
+    for (int q = 0; q < kFeat; ++q) x[q] = __float2bfloat16_rn(f[q]);
+}
+
+__device__ __forceinline__ uint32_t orderable(float v)
+{
+    uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kSelectThreads)
+beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
+                   const float* __restrict__ logits, const BeamState* __restrict__ cur,
+                   BeamState* __restrict__ nxt, int B, int R, int pos)
+{
+    const int g = blockIdx.x;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    const int tid = threadIdx.x;
+    if (pos >= n) {   // group already complete: carry the beams over
+        for (int b = tid; b < B; b += blockDim.x) nxt[(size_t)g * B + b] = cur[(size_t)g * B + b];
+        return;
+    }
+    __shared__ float lse[64];
+    __shared__ unsigned long long key[kMaxCand];
+    const int cands = n - pos;
+    int nk = 16;
+    while (nk < B * 16) nk <<= 1;   // keys sorted: a power of two >= B * 16
+    // log-sum-exp of each live beam's candidate logits
+    for (int b = tid; b < B; b += blockDim.x) {
+        const BeamState s = cur[(size_t)g * B + b];
+        float mx = -INFINITY, z = 0.0f;
+        if (s.alive) {
+            const float* lg = logits + ((size_t)g * B + b) * R;
+            for (int c = 0; c < cands; ++c) mx = fmaxf(mx, lg[c]);
+            for (int c = 0; c < cands; ++c) z += expf(lg[c] - mx);
+        }
+        lse[b] = s.alive ? mx + logf(z) : 0.0f;
+    }
+    __syncthreads();
+    for (int i = tid; i < nk; i += blockDim.x) {
+        const int b = i / 16, c = i % 16;
+        unsigned long long k = 0;
+        if (b < B && c < cands && cur[(size_t)g * B + b].alive) {
+            const float score = cur[(size_t)g * B + b].logp +
+                                (logits[((size_t)g * B + b) * R + c] - lse[b]);
+            k = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
+        }
+        key[i] = k;
+    }
+    __syncthreads();
+    // bitonic sort, descending
+    for (int kk = 2; kk <= nk; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < nk; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = key[i], c = key[ixj];
+                    const bool desc = (i & kk) == 0;
+                    if (desc ? (a < c) : (a > c)) { key[i] = c; key[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int b = tid; b < B; b += blockDim.x) {
+        BeamState s;
+        const unsigned long long k = key[b];
+        if (k == 0) {
+            s.alive = 0;
+            s.h = s.k = s.d = 0;
+            s.used = 0;
+            s.order = 0;
+            s.logp = 0.0f;
+        } else {
+            const int i = (int)(0xFFFFu - (uint32_t)(k & 0xFFFFu));
+            const int pb = i / 16, c = i % 16;
+            const BeamState p = cur[(size_t)g * B + pb];
+            const int j = slot_task(p.used, n, c);
+            const tm_task t = tasks[off + j];
+            const Eng e = step(Eng{p.h, p.k, p.d}, t.htd, t.k, t.dth);
+            s.h = e.h; s.k = e.k; s.d = e.d;
+            s.used = p.used | (1u << j);
+            s.order = p.order | ((unsigned long long)j << (4 * pos));
+            s.logp = p.logp + (logits[((size_t)g * B + pb) * R + c] - lse[pb]);
+            s.alive = 1;
+        }
+        nxt[(size_t)g * B + b] = s;
+    }
+}
+
+// Best finished beam vs the heuristic's order, which is already in `orders`
+// (and its makespan in heur_ms): a beam replaces it only when strictly
+// better.  beam_won[g] (optional) records which one was kept.
+__global__ void beam_finish_kernel(const int32_t* __restrict__ offsets,
+                                   const int32_t* __restrict__ status,
+                                   const BeamState* __restrict__ st, int G, int B,
+                                   const int32_t* __restrict__ heur_ms, int32_t* __restrict__ orders,
+                                   int32_t* __restrict__ ms, int32_t* __restrict__ beam_won)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G || status[g] != 0) return;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    int best = -1;
+    int32_t best_d = 0;
+    for (int b = 0; b < B; ++b) {
+        const BeamState s = st[(size_t)g * B + b];
+        if (s.alive && (best < 0 || s.d < best_d)) { best = b; best_d = s.d; }
+    }
+    const bool use_beam = best >= 0 && best_d < heur_ms[g];
+    if (use_beam) {
+        const unsigned long long order = st[(size_t)g * B + best].order;
+        for (int p = 0; p < n; ++p) orders[off + p] = (int32_t)((order >> (4 * p)) & 0xF);
+    }
+    if (ms) ms[g] = use_beam ? best_d : heur_ms[g];
+    if (beam_won) beam_won[g] = use_beam ? 1 : 0;
+}
+
+// ---- training rows ----------------------------------------------------------
+
+// Exclusive prefix sums over groups of the training rows (n (n + 1) / 2 - 1
+// for n >= 2) and states (n - 1).  One block of 1024 threads.
+__global__ void __launch_bounds__(1024)
+rows_scan_kernel(const int32_t* __restrict__ offsets, int G, int64_t* __restrict__ row_base,
+                 int32_t* __restrict__ state_base)
+{
+    __shared__ int64_t wr[32];
+    __shared__ int32_t ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t carry_r = 0;
+    int32_t carry_s = 0;
+    for (int base = 0; base < G; base += 1024) {
+        const int g = base + tid;
+        int n = g < G ? offsets[g + 1] - offsets[g] : 0;
+        n = n < 2 ? 0 : (n > 16 ? 16 : n);   // out-of-range groups get rows of n = 16
+        int64_t r = n ? (int64_t)n * (n + 1) / 2 - 1 : 0;
+        int32_t c = n ? n - 1 : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t rr = __shfl_up_sync(kFull, r, o);
+            const int32_t cc = __shfl_up_sync(kFull, c, o);
+            if (lane >= o) { r += rr; c += cc; }
+        }
+        if (lane == 31) { wr[warp] = r; ws[warp] = c; }
+        __syncthreads();
+        if (warp == 0) {
+            int64_t x = wr[lane];
+            int32_t y = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t xx = __shfl_up_sync(kFull, x, o);
+                const int32_t yy = __shfl_up_sync(kFull, y, o);
+                if (lane >= o) { x += xx; y += yy; }
+            }
+            wr[lane] = x;
+            ws[lane] = y;
+        }
+        __syncthreads();
+        const int64_t before_r = carry_r + (warp ? wr[warp - 1] : 0);
+        const int32_t before_s = carry_s + (warp ? ws[warp - 1] : 0);
+        if (g < G) {
+            const int nn = offsets[g + 1] - offsets[g];
+            const int nc = nn < 2 ? 0 : (nn > 16 ? 16 : nn);
+            row_base[g] = before_r + r - (nc ? (int64_t)nc * (nc + 1) / 2 - 1 : 0);
+            state_base[g] = before_s + c - (nc ? nc - 1 : 0);
+        }
+        carry_r += wr[31];
+        carry_s += ws[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        row_base[G] = carry_r;
+        state_base[G] = carry_s;
+    }
+}
+
+// Training rows along each group's given order (behaviour cloning): for
+// every position p < n - 1, one row per unused task (ascending task index),
+// the state's target being the row of the task the order places at p.
+// One warp per group.  Rows and states past M / S are never written; a
+// group that fails its input check or whose order is not a permutation gets
+// zero rows, targets on the first row of each state, and its status.
+__global__ void rows_kernel(const tm_task* __restrict__ tasks, const int32_t* __restrict__ offsets,
+                            int G, const tm_device* __restrict__ devs,
+                            const int32_t* __restrict__ orders, const tm_stats* __restrict__ stats,
+                            const int64_t* __restrict__ row_base,
+                            const int32_t* __restrict__ state_base, int64_t M, int64_t M_pad, int S,
+                            __nv_bfloat16* __restrict__ X, int32_t* __restrict__ state_off,
+                            int32_t* __restrict__ target, int32_t* __restrict__ status)
+{
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw == 0) {
+        // zero tail rows up to M_pad, close the state offsets
+        for (int64_t i = M * kFeat + lane; i < M_pad * kFeat; i += 32) X[i] = __float2bfloat16_rn(0.f);
+        if (lane == 0) state_off[S] = (int32_t)M;
+    }
+    if (gw >= G) return;
+    const int g = (int)gw;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    const int dma = devs[g].dma_engines;
+    int32_t hs = 0, dinit = 0;
+    int err = check_group(tasks + off, n, dma, 16, &hs, &dinit);
+    int my = -1;
+    if (err == 0) {
+        if (orders) my = lane < n ? orders[off + lane] : -1;
+        else my = lane < n ? (int)stats[g].best_order[lane] : -1;
+        const bool ok = lane >= n || (my >= 0 && my < n);
+        const uint32_t seen = __reduce_or_sync(kFull, (lane < n && ok) ? (1u << my) : 0u);
+        if (!__all_sync(kFull, ok) || seen != (n >= 32 ? kFull : (1u << n) - 1u)) err = TM_EINVAL;
+    }
+    if (lane == 0 && status) status[g] = err;
+    int64_t total = 0;
+    for (int i = 0; i < n && err == 0; ++i)
+        total += (int64_t)tasks[off + i].htd + tasks[off + i].k + tasks[off + i].dth;
+    const float scale = total > 0 ? (float)n / (float)total : 0.f;
+    const int64_t rb0 = row_base[g];
+    const int32_t sb0 = state_base[g];
+    Eng e{0, 0, dinit};
+    uint32_t used = 0;
+    int64_t rb = rb0;
+    const int nr = n < 2 ? 0 : (n > 16 ? 16 : n);   // the row layout of rows_scan_kernel
+    for (int p = 0; p + 1 < nr; ++p) {
+        const int cands = nr - p;
+        const int tj = err == 0 ? __shfl_sync(kFull, my, p) : 0;
+        const uint32_t free_mask = ((1u << nr) - 1u) & ~used;
+        if (lane < cands) {
+            float f[kFeat];
+            if (err == 0) {
+                const int j = slot_task(used, n, lane);
+                rank_features(tasks + off, n, used, e.h, e.k, e.d, dma, scale, j, f);
+            } else {
+                for (int q = 0; q < kFeat; ++q) f[q] = 0.f;
+            }
+            const int64_t row = rb + lane;
+            if (row < M) {
+                __nv_bfloat16* x = X + row * kFeat;
+#pragma unroll
+                for (int q = 0; q < kFeat; ++q) x[q] = __float2bfloat16_rn(f[q]);
+            }
+        }
+        const int32_t sidx = sb0 + p;
+        if (lane == 0 && sidx < S) {
+            state_off[sidx] = (int32_t)rb;
+            const int slot = err == 0 ? __popc(free_mask & ((1u << tj) - 1u)) : 0;
+            target[sidx] = (int32_t)(rb + slot);
+        }
+        if (err == 0) {
+            const tm_task t = tasks[off + tj];
+            e = step(e, t.htd, t.k, t.dth);
+            used |= 1u << tj;
+        }
+        rb += cands;
+    }
+}
+
+}  // namespace
+
+// Launchers used by the C ABI (learn_api.cu).
+size_t beam_state_bytes(int G, int B) { return (size_t)G * B * sizeof(BeamState); }
+
+cudaError_t beam_init(const int32_t* offsets, const int32_t* status, const tm_task* tasks,
+                      const tm_device* devs, int G, int B, void* st, float* scale, cudaStream_t s)
+{
+    const int threads = G * B;
+    beam_init_kernel<<<(threads + 255) / 256, 256, 0, s>>>(offsets, status, tasks, devs, G, B,
+                                                           static_cast<BeamState*>(st), scale);
+    return cudaGetLastError();
+}
+
+cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
+                          const float* scale, const void* st, int G, int B, int R, int pos,
+                          bf16_raw* X, cudaStream_t s)
+{
+    const int64_t rows = (int64_t)G * B * R;
+    beam_features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(
+        offsets, tasks, devs, scale, static_cast<const BeamState*>(st), G, B, R, pos,
+        reinterpret_cast<__nv_bfloat16*>(X));
+    return cudaGetLastError();
+}
+
+cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const float* logits,
+                        const void* cur, void* nxt, int G, int B, int R, int pos, cudaStream_t s)
+{
+    beam_select_kernel<<<G, kSelectThreads, 0, s>>>(offsets, tasks, logits,
+                                                    static_cast<const BeamState*>(cur),
+                                                    static_cast<BeamState*>(nxt), B, R, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const void* st, int G,
+                        int B, const int32_t* heur_ms, int32_t* orders, int32_t* ms,
+                        int32_t* beam_won, cudaStream_t s)
+{
+    beam_finish_kernel<<<(G + 127) / 128, 128, 0, s>>>(offsets, status,
+                                                       static_cast<const BeamState*>(st), G, B,
+                                                       heur_ms, orders, ms, beam_won);
+    return cudaGetLastError();
+}
+
+cudaError_t rank_rows(const tm_task* tasks, const int32_t* offsets, int G, const tm_device* devs,
+                      const int32_t* orders, const tm_stats* stats, int64_t* row_base,
+                      int32_t* state_base, int64_t M, int S, bf16_raw* X, int32_t* state_off,
+                      int32_t* target, int32_t* status, cudaStream_t s)
+{
+    rows_scan_kernel<<<1, 1024, 0, s>>>(offsets, G, row_base, state_base);
+    const int64_t M_pad = (M + 15) / 16 * 16;
+    const int64_t threads = (int64_t)(G > 0 ? G : 1) * 32;
+    rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        tasks, offsets, G, devs, orders, stats, row_base, state_base, M, M_pad, S,
+        reinterpret_cast<__nv_bfloat16*>(X), state_off, target, status);
+    return cudaGetLastError();
+}
+
+}  // namespace tmgpu

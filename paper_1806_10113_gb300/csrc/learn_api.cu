@@ -1,0 +1,324 @@
+// learn_api.cu -- the extern "C" entry points of the learned order ranker
+// and of the beam search that uses it (declared in include/tm.h).  The
+// paper has no learned component; these schedule groups beyond exhaustive
+// reach, every returned order being judged by the exact model.
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "ranker.h"
+#include "tm_internal.h"
+
+namespace tmgpu {
+// beam.cu
+size_t beam_state_bytes(int G, int B);
+cudaError_t beam_init(const int32_t* offsets, const int32_t* status, const tm_task* tasks,
+                      const tm_device* devs, int G, int B, void* st, float* scale, cudaStream_t s);
+cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
+                          const float* scale, const void* st, int G, int B, int R, int pos,
+                          bf16_raw* X, cudaStream_t s);
+cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const float* logits,
+                        const void* cur, void* nxt, int G, int B, int R, int pos, cudaStream_t s);
+cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const void* st, int G,
+                        int B, const int32_t* heur_ms, int32_t* orders, int32_t* ms,
+                        int32_t* beam_won, cudaStream_t s);
+cudaError_t rank_rows(const tm_task* tasks, const int32_t* offsets, int G, const tm_device* devs,
+                      const int32_t* orders, const tm_stats* stats, int64_t* row_base,
+                      int32_t* state_base, int64_t M, int S, bf16_raw* X, int32_t* state_off,
+                      int32_t* target, int32_t* status, cudaStream_t s);
+}  // namespace tmgpu
+
+namespace {
+
+// A device buffer that grows on demand (contents are not kept).
+struct Grow {
+    void* p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes)
+    {
+        if (bytes <= cap) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes, 256);
+        if (cudaMalloc(&p, want) != cudaSuccess) { p = nullptr; return false; }
+        cap = want;
+        return true;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+    void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
+};
+
+// Rows a group of n tasks contributes to the training rows (states p = 0 ..
+// n - 2 with n - p candidates each) and its number of states.
+inline int64_t group_rows(int n) { return n < 2 ? 0 : (int64_t)n * (n + 1) / 2 - 1; }
+inline int32_t group_states(int n) { return n < 2 ? 0 : n - 1; }
+
+// Rows of one beam step are processed in chunks of groups so that the
+// feature matrix stays below this many rows.
+constexpr int64_t kBeamRowsPerChunk = int64_t(1) << 22;
+
+}  // namespace
+
+struct tm_ranker {
+    int device = -1;
+    int sms = 0;
+    float* P = nullptr;       // float32 master parameters
+    tmgpu::bf16_raw* Wb = nullptr;   // bfloat16 weight copies
+    float* Mom = nullptr;
+    float* Vel = nullptr;
+    float* G = nullptr;       // gradient of the last tm_ranker_grad_dev
+    float* loss = nullptr;
+    int adam_step = 0;
+    Grow scan_rows, scan_states, logits, dlogit, act;          // training
+    Grow st[2], scale, bx, blog, hms, bstatus;                 // beam search
+    void release()
+    {
+        for (void* q : {(void*)P, (void*)Wb, (void*)Mom, (void*)Vel, (void*)G, (void*)loss})
+            if (q) cudaFree(q);
+        for (Grow* b : {&scan_rows, &scan_states, &logits, &dlogit, &act, &st[0], &st[1], &scale,
+                        &bx, &blog, &hms, &bstatus})
+            b->release();
+    }
+};
+
+namespace {
+
+int forward_blocks(const tm_ranker* r, int64_t M)
+{
+    const int64_t slabs = (M + 15) / 16;
+    const int64_t want = (slabs + 7) / 8;   // 8 warps per block, one slab per warp
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, r->sms));
+}
+
+int on_device(const tm_ranker* r)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+    return dev == r->device ? TM_OK : TM_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tm_ranker_create(uint64_t seed, tm_ranker** out)
+{
+    if (!out) return TM_EINVAL;
+    *out = nullptr;
+    tm_ranker* r = new (std::nothrow) tm_ranker;
+    if (!r) return TM_ENOMEM;
+    if (cudaGetDevice(&r->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess ||
+        tmgpu::ranker_configure() != cudaSuccess) {
+        delete r;
+        return TM_ECUDA;
+    }
+    const size_t pb = tmgpu::kRankParams * sizeof(float);
+    if (cudaMalloc(&r->P, pb) != cudaSuccess || cudaMalloc(&r->Mom, pb) != cudaSuccess ||
+        cudaMalloc(&r->Vel, pb) != cudaSuccess || cudaMalloc(&r->G, pb) != cudaSuccess ||
+        cudaMalloc(&r->loss, sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&r->Wb, tmgpu::kRankBf16 * sizeof(tmgpu::bf16_raw)) != cudaSuccess) {
+        r->release();
+        delete r;
+        return TM_ENOMEM;
+    }
+    cudaError_t e = cudaMemset(r->Mom, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(r->Vel, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(r->G, 0, pb);
+    if (e == cudaSuccess) e = tmgpu::ranker_init(r->P, r->Wb, seed, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        r->release();
+        delete r;
+        return TM_ECUDA;
+    }
+    *out = r;
+    return TM_OK;
+}
+
+void tm_ranker_destroy(tm_ranker* r)
+{
+    if (!r) return;
+    cudaDeviceSynchronize();
+    r->release();
+    delete r;
+}
+
+int tm_ranker_get_params(const tm_ranker* r, float* h_params)
+{
+    if (!r || !h_params) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TM_ECUDA;
+    return cudaMemcpy(h_params, r->P, tmgpu::kRankParams * sizeof(float),
+                      cudaMemcpyDeviceToHost) == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_set_params(tm_ranker* r, const float* h_params)
+{
+    if (!r || !h_params) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    const size_t pb = tmgpu::kRankParams * sizeof(float);
+    if (cudaDeviceSynchronize() != cudaSuccess) return TM_ECUDA;
+    cudaError_t e = cudaMemcpy(r->P, h_params, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(r->Mom, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(r->Vel, 0, pb);
+    if (e == cudaSuccess) e = tmgpu::ranker_refresh(r->P, r->Wb, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    r->adam_step = 0;
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_rows_count(const int32_t* h_offsets, int G, int64_t* rows, int32_t* states)
+{
+    if (G < 0 || !rows || !states || (G > 0 && !h_offsets)) return TM_EINVAL;
+    if (G > 0 && h_offsets[0] != 0) return TM_EINVAL;
+    int64_t m = 0, s = 0;
+    for (int g = 0; g < G; ++g) {
+        const int n = h_offsets[g + 1] - h_offsets[g];
+        if (n < 1 || n > TM_MAX_TASKS) return TM_EINVAL;
+        m += group_rows(n);
+        s += group_states(n);
+    }
+    if (m > INT32_MAX - 16 || s > INT32_MAX - 1) return TM_ECAPACITY;
+    *rows = m;
+    *states = (int32_t)s;
+    return TM_OK;
+}
+
+int tm_ranker_rows_dev(tm_ranker* r, const tm_task* d_tasks, const int32_t* d_offsets, int G,
+                       const tm_device* d_devs, const int32_t* d_orders, const tm_stats* d_stats,
+                       int64_t rows, int32_t states, uint16_t* d_X, int32_t* d_state_off,
+                       int32_t* d_target, int32_t* d_status, void* stream)
+{
+    if (!r || G < 0 || rows < 0 || states < 0 || rows > INT32_MAX - 16) return TM_EINVAL;
+    if (!d_X || !d_state_off || (states > 0 && !d_target)) return TM_EINVAL;
+    if (G > 0 && (!d_tasks || !d_offsets || !d_devs || (!d_orders && !d_stats))) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    if (!r->scan_rows.ensure((size_t)(G + 1) * sizeof(int64_t)) ||
+        !r->scan_states.ensure((size_t)(G + 1) * sizeof(int32_t)))
+        return TM_ENOMEM;
+    cudaError_t e = tmgpu::rank_rows(d_tasks, d_offsets, G, d_devs, d_orders, d_stats,
+                                     r->scan_rows.as<int64_t>(), r->scan_states.as<int32_t>(),
+                                     rows, states, d_X, d_state_off, d_target, d_status,
+                                     (cudaStream_t)stream);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_forward_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows, float* d_logits,
+                          void* stream)
+{
+    if (!r || rows < 0 || (rows > 0 && (!d_X || !d_logits))) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    if (rows == 0) return TM_OK;
+    cudaError_t e = tmgpu::ranker_forward(d_X, rows, r->Wb, r->P, d_logits, nullptr, 0,
+                                          forward_blocks(r, rows), (cudaStream_t)stream);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_grad_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows,
+                       const int32_t* d_state_off, const int32_t* d_target, int32_t states,
+                       float* d_grad, float* d_loss, void* stream)
+{
+    if (!r || rows <= 0 || states <= 0 || !d_X || !d_state_off || !d_target) return TM_EINVAL;
+    if (rows > INT32_MAX - 16) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    const int64_t M_pad = (rows + 15) / 16 * 16;
+    const size_t slab = (size_t)M_pad * tmgpu::kRankH * sizeof(tmgpu::bf16_raw);
+    if (!r->logits.ensure((size_t)M_pad * sizeof(float)) ||
+        !r->dlogit.ensure((size_t)M_pad * sizeof(float)) || !r->act.ensure(5 * slab))
+        return TM_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    // a1, a2, a3, dzA, dzB: rows past `rows` must read as zero
+    const size_t tail = (size_t)(M_pad - rows) * tmgpu::kRankH * sizeof(tmgpu::bf16_raw);
+    cudaError_t e = cudaSuccess;
+    if (tail)
+        e = cudaMemset2DAsync(static_cast<char*>(r->act.p) + (slab - tail), slab, 0, tail, 5, s);
+    tmgpu::bf16_raw* act = r->act.as<tmgpu::bf16_raw>();
+    if (e == cudaSuccess)
+        e = tmgpu::ranker_backward(d_X, rows, d_state_off, d_target, states, r->Wb, r->P,
+                                   r->logits.as<float>(), r->dlogit.as<float>(), act,
+                                   act + 3 * slab / sizeof(tmgpu::bf16_raw), r->G, r->loss,
+                                   2 * r->sms, s);
+    if (e == cudaSuccess && d_grad)
+        e = cudaMemcpyAsync(d_grad, r->G, tmgpu::kRankParams * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d_loss)
+        e = cudaMemcpyAsync(d_loss, r->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_adam_dev(tm_ranker* r, float lr, void* stream)
+{
+    if (!r || !(lr > 0.0f)) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    r->adam_step += 1;
+    cudaError_t e = tmgpu::ranker_adam(r->P, r->Mom, r->Vel, r->G, r->Wb, lr, r->adam_step,
+                                       (cudaStream_t)stream);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_beam_batch_dev(tm_ranker* r, const tm_task* d_tasks, const int32_t* d_offsets,
+                      const int32_t* h_offsets, int G, const tm_device* d_devs, int beam_width,
+                      int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
+                      int32_t* d_beam_won, void* stream)
+{
+    if (!r || G < 0 || beam_width < 1 || beam_width > TM_BEAM_MAX_WIDTH) return TM_EINVAL;
+    if (G == 0) return TM_OK;
+    if (!d_tasks || !d_offsets || !h_offsets || !d_devs || !d_orders_out) return TM_EINVAL;
+    if (h_offsets[0] != 0) return TM_EINVAL;
+    int nmax = 0;
+    for (int g = 0; g < G; ++g) {
+        const int n = h_offsets[g + 1] - h_offsets[g];
+        if (n < 1 || n > TM_MAX_TASKS) return TM_EINVAL;
+        nmax = std::max(nmax, n);
+    }
+    if (int rc = on_device(r)) return rc;
+    const int B = beam_width;
+    // groups per chunk: G_c * B * nmax rows at the first step
+    const int64_t per_group = (int64_t)B * nmax;
+    const int Gc = (int)std::max<int64_t>(1, std::min<int64_t>(G, kBeamRowsPerChunk / per_group));
+    if (!r->st[0].ensure(tmgpu::beam_state_bytes(Gc, B)) ||
+        !r->st[1].ensure(tmgpu::beam_state_bytes(Gc, B)) ||
+        !r->scale.ensure((size_t)Gc * sizeof(float)) ||
+        !r->bx.ensure((size_t)Gc * per_group * tmgpu::kRankF * sizeof(tmgpu::bf16_raw)) ||
+        !r->blog.ensure((size_t)Gc * per_group * sizeof(float)) ||
+        !r->hms.ensure((size_t)G * sizeof(int32_t)) ||
+        (!d_status && !r->bstatus.ensure((size_t)G * sizeof(int32_t))))
+        return TM_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* status = d_status ? d_status : r->bstatus.as<int32_t>();
+    int32_t* hms = r->hms.as<int32_t>();
+    // the paper's heuristic first: its order is the fallback (Algorithm 1)
+    cudaError_t e = tmgpu::launch_heuristic(d_tasks, d_offsets, G, d_devs, d_orders_out, hms,
+                                            status, s);
+    for (int g0 = 0; g0 < G && e == cudaSuccess; g0 += Gc) {
+        const int gc = std::min(Gc, G - g0);
+        int nm = 0;
+        for (int g = g0; g < g0 + gc; ++g) nm = std::max(nm, h_offsets[g + 1] - h_offsets[g]);
+        const int32_t* off = d_offsets + g0;
+        void* cur = r->st[0].p;
+        void* nxt = r->st[1].p;
+        e = tmgpu::beam_init(off, status + g0, d_tasks, d_devs + g0, gc, B, cur,
+                             r->scale.as<float>(), s);
+        for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
+            const int R = nm - pos;
+            const int64_t rows = (int64_t)gc * B * R;
+            e = tmgpu::beam_features(off, d_tasks, d_devs + g0, r->scale.as<float>(), cur, gc, B,
+                                     R, pos, r->bx.as<tmgpu::bf16_raw>(), s);
+            if (e == cudaSuccess)
+                e = tmgpu::ranker_forward(r->bx.as<tmgpu::bf16_raw>(), rows, r->Wb, r->P,
+                                          r->blog.as<float>(), nullptr, 0, forward_blocks(r, rows), s);
+            if (e == cudaSuccess)
+                e = tmgpu::beam_select(off, d_tasks, r->blog.as<float>(), cur, nxt, gc, B, R, pos, s);
+            std::swap(cur, nxt);
+        }
+        if (e == cudaSuccess)
+            e = tmgpu::beam_finish(off, status + g0, cur, gc, B, hms + g0, d_orders_out,
+                                   d_makespans_out ? d_makespans_out + g0 : nullptr,
+                                   d_beam_won ? d_beam_won + g0 : nullptr, s);
+    }
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+}  // extern "C"

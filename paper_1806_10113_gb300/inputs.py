@@ -212,3 +212,63 @@ TABLE3 = {
 
 def table2_tasks(names, unit_ns=1_000_000) -> np.ndarray:
     return np.asarray([[v * unit_ns for v in TABLE2_MS[x]] for x in names], dtype=np.int32)
+
+
+# ---- large training sets (vectorised) -----------------------------------------
+
+def _splitmix_at(keys: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """SplitMix64 output number idx (0-based) of the stream seeded with key:
+    the state after idx + 1 steps is key + (idx + 1) * golden, then mix13."""
+    with np.errstate(over="ignore"):
+        z = keys.astype(np.uint64) + (idx.astype(np.uint64) + np.uint64(1)) * np.uint64(GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _log_uniform_vec(u64: np.ndarray, lo: int, hi: int) -> np.ndarray:
+    u = (u64 >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    v = np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))
+    return np.clip(np.floor(v + 0.5), lo, hi).astype(np.int64)
+
+
+def training_groups(groups: int, nmin: int = 6, nmax: int = 10, seed: int = 5,
+                    lo: int = 10_000, hi: int = 10_000_000) -> Batch:
+    """Many ragged groups drawn like `ragged_mixed` (n ~ U{nmin..nmax}, each
+    task DK or DT with p = 1/2, log-uniform durations on [lo, hi] redrawn
+    until the class matches, two DMA engines on even groups, one on odd),
+    vectorised with numpy.  Group g reads its stream (key seed ^ g * golden)
+    at fixed positions: number 0 gives n (as floor(u * r / 2^64), bias below
+    2^-59), number 1 + i the class of task i (top bit), and numbers
+    64 + 4096 i + 3 a + c the c-th duration of attempt a of task i."""
+    g = np.arange(groups, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        keys = np.uint64(seed & M64) ^ (g * np.uint64(GOLDEN))
+    r = nmax - nmin + 1
+    u = _splitmix_at(keys, np.zeros(groups, dtype=np.uint64))
+    # floor(u * r / 2^64) from the top 32 bits (exact enough for r < 2^16)
+    n = nmin + (((u >> np.uint64(32)) * np.uint64(r)) >> np.uint64(32)).astype(np.int64)
+    offsets = np.zeros(groups + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(n)
+    T = int(offsets[-1])
+    gid = np.repeat(np.arange(groups), n)
+    tid = np.arange(T) - offsets[gid]
+    tkeys = keys[gid]
+    dk = (_splitmix_at(tkeys, (1 + tid).astype(np.uint64)) >> np.uint64(63)) == 1
+    out = np.zeros((T, 3), dtype=np.int64)
+    todo = np.arange(T)
+    a = 0
+    while todo.size:
+        if a >= 1365:
+            raise RuntimeError("class rejection did not settle")
+        base = (64 + 4096 * tid[todo] + 3 * a).astype(np.uint64)
+        vals = [_log_uniform_vec(_splitmix_at(tkeys[todo], base + np.uint64(c)), lo, hi)
+                for c in range(3)]
+        ok = ((vals[0] + vals[2]) <= vals[1]) == dk[todo]
+        for c in range(3):
+            out[todo[ok], c] = vals[c][ok]
+        todo = todo[~ok]
+        a += 1
+    dma = np.where(np.arange(groups) % 2 == 0, 2, 1).astype(np.int32)
+    return Batch(np.ascontiguousarray(out.astype(np.int32)), offsets.astype(np.int32), dma,
+                 f"train_g{groups}_n{nmin}-{nmax}_seed{seed}")

@@ -26,6 +26,9 @@ TM_MAX_EXHAUSTIVE = 12
 TM_NOALLOC_MAX_GROUPS = 64
 TM_NOALLOC_MAX_TASKS = 768
 TM_NOALLOC_MAX_SUBSETS = 4800
+TM_RANKER_FEATURES = 32
+TM_RANKER_PARAMS = 37377
+TM_BEAM_MAX_WIDTH = 64
 
 STATS_DTYPE = np.dtype([
     ("best", "<i4"), ("worst", "<i4"), ("sum", "<i8"), ("mean", "<f8"),
@@ -76,10 +79,23 @@ _SIGS = {
     "tm_exhaustive_batch_noalloc": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "tm_schedule_batch_dev": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tm_schedule_batch": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tm_ranker_create": [ctypes.c_uint64, ctypes.POINTER(_vp)],
+    "tm_ranker_destroy": [_vp],
+    "tm_ranker_get_params": [_vp, _vp],
+    "tm_ranker_set_params": [_vp, _vp],
+    "tm_ranker_rows_count": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int32)],
+    "tm_ranker_rows_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64,
+                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp],
+    "tm_ranker_forward_dev": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "tm_ranker_grad_dev": [_vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp],
+    "tm_ranker_adam_dev": [_vp, ctypes.c_float, _vp],
+    "tm_beam_batch_dev": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
+                          _vp, _vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
-_RESTYPE = {"tm_plan_destroy": None, "tm_strerror": ctypes.c_char_p,
+_RESTYPE = {"tm_plan_destroy": None, "tm_ranker_destroy": None, "tm_strerror": ctypes.c_char_p,
             "tm_version": ctypes.c_char_p}
 
 
@@ -365,3 +381,88 @@ def tm_exhaustive_batch_noalloc(d_tasks, offsets, d_devs, d_stats, d_status=None
     _check(lib().tm_exhaustive_batch_noalloc(_dptr(d_tasks), _p(off), G, _dptr(d_devs),
                                              _dptr(d_stats), _dptr(d_status), _stream(stream)),
            "tm_exhaustive_batch_noalloc")
+
+
+# ---- learned order ranker and beam search --------------------------------------
+
+def tm_ranker_rows_count(offsets):
+    """(rows, states) of the training rows of a batch with these host offsets."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    rows, states = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(lib().tm_ranker_rows_count(_p(off), off.shape[0] - 1, ctypes.byref(rows),
+                                      ctypes.byref(states)), "tm_ranker_rows_count")
+    return int(rows.value), int(states.value)
+
+
+class Ranker:
+    """Owns a tm_ranker: the learned order ranker (4-layer bfloat16 MLP) whose
+    proposals feed tm_beam_batch_dev.  Lives on the CUDA device current at
+    creation."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().tm_ranker_create(ctypes.c_uint64(seed & ((1 << 64) - 1)), ctypes.byref(h)),
+               "tm_ranker_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(TM_RANKER_PARAMS, dtype=np.float32)
+        _check(lib().tm_ranker_get_params(self._h, _p(out)), "tm_ranker_get_params")
+        return out
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if a.shape[0] != TM_RANKER_PARAMS:
+            raise ValueError(f"expected {TM_RANKER_PARAMS} parameters, got {a.shape[0]}")
+        _check(lib().tm_ranker_set_params(self._h, _p(a)), "tm_ranker_set_params")
+
+    def rows_dev(self, d_tasks, d_offsets, G: int, d_devs, rows: int, states: int, d_X,
+                 d_state_off, d_target, d_orders=None, d_stats=None, d_status=None,
+                 stream=None):
+        """Training rows along d_orders (or d_stats' best orders)."""
+        _check(lib().tm_ranker_rows_dev(self._h, _dptr(d_tasks), _dptr(d_offsets), int(G),
+                                        _dptr(d_devs), _dptr(d_orders), _dptr(d_stats),
+                                        int(rows), int(states), _dptr(d_X), _dptr(d_state_off),
+                                        _dptr(d_target), _dptr(d_status), _stream(stream)),
+               "tm_ranker_rows_dev")
+
+    def forward_dev(self, d_X, rows: int, d_logits, stream=None):
+        _check(lib().tm_ranker_forward_dev(self._h, _dptr(d_X), int(rows), _dptr(d_logits),
+                                           _stream(stream)), "tm_ranker_forward_dev")
+
+    def grad_dev(self, d_X, rows: int, d_state_off, d_target, states: int, d_grad=None,
+                 d_loss=None, stream=None):
+        _check(lib().tm_ranker_grad_dev(self._h, _dptr(d_X), int(rows), _dptr(d_state_off),
+                                        _dptr(d_target), int(states), _dptr(d_grad),
+                                        _dptr(d_loss), _stream(stream)), "tm_ranker_grad_dev")
+
+    def adam_dev(self, lr: float, stream=None):
+        _check(lib().tm_ranker_adam_dev(self._h, ctypes.c_float(lr), _stream(stream)),
+               "tm_ranker_adam_dev")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().tm_ranker_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_beam_batch_dev(ranker: Ranker, d_tasks, d_offsets, offsets, d_devs, beam_width: int,
+                      d_orders_out, d_makespans_out=None, d_status=None, d_beam_won=None,
+                      stream=None):
+    """Beam search of every group with the ranker's proposals; never worse than
+    the heuristic.  ``offsets`` is the HOST copy of d_offsets."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    _check(lib().tm_beam_batch_dev(ranker.handle, _dptr(d_tasks), _dptr(d_offsets), _p(off),
+                                   off.shape[0] - 1, _dptr(d_devs), int(beam_width),
+                                   _dptr(d_orders_out), _dptr(d_makespans_out), _dptr(d_status),
+                                   _dptr(d_beam_won), _stream(stream)), "tm_beam_batch_dev")

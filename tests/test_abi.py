@@ -47,7 +47,25 @@ def test_binding_names_match_header(tm):
     for name in declared_functions():
         if name.startswith("tm_plan_") or name in ("tm_strerror", "tm_version"):
             continue
+        if name.startswith("tm_ranker_") and not hasattr(tm, name):
+            # methods of tm.Ranker (create / destroy are its constructor / close)
+            method = name[len("tm_ranker_"):]
+            assert method in ("create", "destroy") or hasattr(tm.Ranker, method), name
+            continue
         assert hasattr(tm, name), name
+
+
+def test_ranker_rows_count(tm):
+    sizes = [1, 2, 3, 16, 7, 10]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    rows, states = tm.tm_ranker_rows_count(off)
+    assert rows == sum(n * (n + 1) // 2 - 1 for n in sizes if n >= 2)
+    assert states == sum(n - 1 for n in sizes)
+    assert tm.tm_ranker_rows_count([0]) == (0, 0)
+    for bad in ([0, 17], [1, 3], [0, 2, 2]):                # n > 16, offsets[0] != 0, n = 0
+        with pytest.raises(tm.TMError) as e:
+            tm.tm_ranker_rows_count(bad)
+        assert e.value.code == -1
 
 
 def test_strerror_and_version(tm):
