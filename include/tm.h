@@ -368,6 +368,89 @@ int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
                       int32_t* d_orders_out, int32_t* d_makespans_out,
                       int32_t* d_status, int32_t* d_beam_won, void* stream);
 
+/* ---- serving ---------------------------------------------------------------- */
+
+/* A scheduling server for task groups that arrive one at a time (the paper
+ * schedules each group as it is submitted to the device, Sec. 5.1; it has no
+ * serving system).  A host worker thread gathers every waiting group into a
+ * batch as soon as one of the server's lanes is free (continuous batching)
+ * and runs it on that lane's two CUDA streams: groups of n <= exact_max_n
+ * get the exhaustive optimum (first best order, as tm_exhaustive_batch_dev),
+ * larger ones the beam search with `ranker` (tm_beam_batch_dev) if
+ * beam_width > 0, else the heuristic (tm_heuristic_batch_dev).  A group's
+ * result does not depend on the other groups of its batch.
+ *
+ * Memory: each lane owns fixed device and pinned host memory sized by the
+ * config at creation; a batch takes at most lane_groups groups, lane_tasks
+ * tasks and lane_subsets 4-task subsets of exhaustively searched groups
+ * (C(n, 4) per group), and a group waits on the host until a lane has room
+ * (first come, first served).  Serving itself allocates nothing.
+ *
+ * Threads: submit / poll / replay may be called from any host thread; the
+ * server runs on the device current at creation.  Results are delivered
+ * once, to whichever poll (or the replay that submitted them) takes them. */
+typedef struct tm_server tm_server;
+
+typedef struct tm_server_config {
+    int32_t lanes;          /* batches in flight, 1..8 (0: 2) */
+    int32_t lane_groups;    /* groups per batch (0: 1024) */
+    int32_t lane_tasks;     /* tasks per batch, >= 16 (0: 16 x lane_groups) */
+    int32_t lane_subsets;   /* 4-task subsets per batch, >= 495 (0: 210 x lane_groups) */
+    int32_t exact_max_n;    /* 0..12: groups up to this size are solved exactly */
+    int32_t beam_width;     /* 0..64; 0: heuristic for the larger groups */
+    tm_tuning tuning;       /* exhaustive-search knobs (fuse_finalize must not be 1) */
+} tm_server_config;
+
+#define TM_METHOD_EXHAUSTIVE 0
+#define TM_METHOD_BEAM 1
+#define TM_METHOD_HEURISTIC 2
+
+/* One scheduled group.  96 bytes. */
+typedef struct tm_server_result {
+    uint64_t ticket;        /* as returned by tm_server_submit */
+    int32_t status;         /* TM_OK or the group's error code */
+    int32_t n;
+    int32_t makespan;       /* of `order`, by the model of Sec. 4.1 */
+    int32_t method;         /* TM_METHOD_*: which search produced `order` */
+    int64_t latency_ns;     /* submission (replay: scheduled arrival) to the
+                               result being on the host */
+    int32_t order[16];      /* task indices; entries past n are -1 */
+} tm_server_result;
+
+/* Creates a server and starts its worker thread.  ranker may be NULL when
+ * beam_width is 0; it must outlive the server and must not be trained while
+ * the server runs. */
+int tm_server_create(const tm_server_config* config, const tm_ranker* ranker,
+                     tm_server** server_out);
+
+/* Queues one group (host pointers, copied before returning).  Input errors
+ * (n outside 1..16, dma_engines, negative durations, sum above INT32_MAX)
+ * are returned at once and the group is not queued. */
+int tm_server_submit(tm_server* server, const tm_task* tasks, int n,
+                     const tm_device* dev, uint64_t* ticket_out);
+
+/* Takes up to max finished results, waiting up to wait_us microseconds for
+ * the first one; *count receives how many were written. */
+int tm_server_poll(tm_server* server, tm_server_result* out, int max, int wait_us,
+                   int* count);
+
+/* Open-loop load: submits group g of the batch (host arrays as in
+ * tm_heuristic_batch) at arrival_ns[g] (nondecreasing) after the call
+ * starts, from the calling thread, and returns when all G results are in
+ * out[g].  Latencies are counted from the scheduled arrival times. */
+int tm_server_replay(tm_server* server, const tm_task* tasks,
+                     const int32_t* offsets, int G, const tm_device* devs,
+                     const int64_t* arrival_ns, tm_server_result* out);
+
+/* Batches launched, groups completed, and the largest batch so far (any
+ * pointer may be NULL). */
+int tm_server_counters(const tm_server* server, int64_t* batches,
+                       int64_t* completed, int64_t* max_batch_groups);
+
+/* Finishes every queued group, stops the worker and frees the server.
+ * Results not yet polled are dropped. */
+void tm_server_destroy(tm_server* server);
+
 /* ---- misc ---------------------------------------------------------------- */
 
 const char* tm_strerror(int code);

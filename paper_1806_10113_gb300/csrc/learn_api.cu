@@ -6,8 +6,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "ranker.h"
-#include "tm_internal.h"
+#include "learn_internal.h"
 
 namespace tmgpu {
 // beam.cu
@@ -30,57 +29,12 @@ cudaError_t rank_rows(const tm_task* tasks, const int32_t* offsets, int G, const
 
 namespace {
 
-// A device buffer that grows on demand (contents are not kept).
-struct Grow {
-    void* p = nullptr;
-    size_t cap = 0;
-    bool ensure(size_t bytes)
-    {
-        if (bytes <= cap) return true;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        const size_t want = std::max<size_t>(bytes, 256);
-        if (cudaMalloc(&p, want) != cudaSuccess) { p = nullptr; return false; }
-        cap = want;
-        return true;
-    }
-    template <class T> T* as() const { return static_cast<T*>(p); }
-    void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
-};
-
 // Rows a group of n tasks contributes to the training rows (states p = 0 ..
 // n - 2 with n - p candidates each) and its number of states.
 inline int64_t group_rows(int n) { return n < 2 ? 0 : (int64_t)n * (n + 1) / 2 - 1; }
 inline int32_t group_states(int n) { return n < 2 ? 0 : n - 1; }
 
-// Rows of one beam step are processed in chunks of groups so that the
-// feature matrix stays below this many rows.
-constexpr int64_t kBeamRowsPerChunk = int64_t(1) << 22;
-
 }  // namespace
-
-struct tm_ranker {
-    int device = -1;
-    int sms = 0;
-    float* P = nullptr;       // float32 master parameters
-    tmgpu::bf16_raw* Wb = nullptr;   // bfloat16 weight copies
-    float* Mom = nullptr;
-    float* Vel = nullptr;
-    float* G = nullptr;       // gradient of the last tm_ranker_grad_dev
-    float* loss = nullptr;
-    int adam_step = 0;
-    Grow scan_rows, scan_states, logits, dlogit, act;          // training
-    Grow st[2], scale, bx, blog, hms, bstatus;                 // beam search
-    void release()
-    {
-        for (void* q : {(void*)P, (void*)Wb, (void*)Mom, (void*)Vel, (void*)G, (void*)loss})
-            if (q) cudaFree(q);
-        for (Grow* b : {&scan_rows, &scan_states, &logits, &dlogit, &act, &st[0], &st[1], &scale,
-                        &bx, &blog, &hms, &bstatus})
-            b->release();
-    }
-};
 
 namespace {
 
@@ -99,6 +53,65 @@ int on_device(const tm_ranker* r)
 }
 
 }  // namespace
+
+namespace tmgpu {
+
+bool BeamScratch::reserve(int G, int nmax, int B)
+{
+    const int64_t per_group = (int64_t)B * nmax;
+    const int Gc = (int)std::max<int64_t>(1, std::min<int64_t>(G, kBeamRowsPerChunk / per_group));
+    return st[0].ensure(beam_state_bytes(Gc, B)) && st[1].ensure(beam_state_bytes(Gc, B)) &&
+           scale.ensure((size_t)Gc * sizeof(float)) &&
+           bx.ensure((size_t)Gc * per_group * kRankF * sizeof(bf16_raw)) &&
+           blog.ensure((size_t)Gc * per_group * sizeof(float)) &&
+           hms.ensure((size_t)G * sizeof(int32_t)) && bstatus.ensure((size_t)G * sizeof(int32_t));
+}
+
+int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
+               const int32_t* d_offsets, const int32_t* h_offsets, int G, const tm_device* d_devs,
+               int B, int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
+               int32_t* d_beam_won, cudaStream_t s)
+{
+    if (G == 0) return TM_OK;
+    int nmax = 0;
+    for (int g = 0; g < G; ++g) nmax = std::max(nmax, h_offsets[g + 1] - h_offsets[g]);
+    // groups per chunk: G_c * B * nmax rows at the first step
+    const int64_t per_group = (int64_t)B * nmax;
+    const int Gc = (int)std::max<int64_t>(1, std::min<int64_t>(G, kBeamRowsPerChunk / per_group));
+    if (!sc.reserve(G, nmax, B)) return TM_ENOMEM;
+    int32_t* status = d_status ? d_status : sc.bstatus.as<int32_t>();
+    int32_t* hms = sc.hms.as<int32_t>();
+    // the paper's heuristic first: its order is the fallback (Algorithm 1)
+    cudaError_t e = launch_heuristic(d_tasks, d_offsets, G, d_devs, d_orders_out, hms, status, s);
+    for (int g0 = 0; g0 < G && e == cudaSuccess; g0 += Gc) {
+        const int gc = std::min(Gc, G - g0);
+        int nm = 0;
+        for (int g = g0; g < g0 + gc; ++g) nm = std::max(nm, h_offsets[g + 1] - h_offsets[g]);
+        const int32_t* off = d_offsets + g0;
+        void* cur = sc.st[0].p;
+        void* nxt = sc.st[1].p;
+        e = beam_init(off, status + g0, d_tasks, d_devs + g0, gc, B, cur, sc.scale.as<float>(), s);
+        for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
+            const int R = nm - pos;
+            const int64_t rows = (int64_t)gc * B * R;
+            e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R, pos,
+                              sc.bx.as<bf16_raw>(), s);
+            if (e == cudaSuccess)
+                e = ranker_forward(sc.bx.as<bf16_raw>(), rows, r->Wb, r->P, sc.blog.as<float>(),
+                                   nullptr, 0, forward_blocks(r, rows), s);
+            if (e == cudaSuccess)
+                e = beam_select(off, d_tasks, sc.blog.as<float>(), cur, nxt, gc, B, R, pos, s);
+            std::swap(cur, nxt);
+        }
+        if (e == cudaSuccess)
+            e = beam_finish(off, status + g0, cur, gc, B, hms + g0, d_orders_out,
+                            d_makespans_out ? d_makespans_out + g0 : nullptr,
+                            d_beam_won ? d_beam_won + g0 : nullptr, s);
+    }
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+}  // namespace tmgpu
 
 extern "C" {
 
@@ -267,58 +280,14 @@ int tm_beam_batch_dev(tm_ranker* r, const tm_task* d_tasks, const int32_t* d_off
     if (G == 0) return TM_OK;
     if (!d_tasks || !d_offsets || !h_offsets || !d_devs || !d_orders_out) return TM_EINVAL;
     if (h_offsets[0] != 0) return TM_EINVAL;
-    int nmax = 0;
     for (int g = 0; g < G; ++g) {
         const int n = h_offsets[g + 1] - h_offsets[g];
         if (n < 1 || n > TM_MAX_TASKS) return TM_EINVAL;
-        nmax = std::max(nmax, n);
     }
     if (int rc = on_device(r)) return rc;
-    const int B = beam_width;
-    // groups per chunk: G_c * B * nmax rows at the first step
-    const int64_t per_group = (int64_t)B * nmax;
-    const int Gc = (int)std::max<int64_t>(1, std::min<int64_t>(G, kBeamRowsPerChunk / per_group));
-    if (!r->st[0].ensure(tmgpu::beam_state_bytes(Gc, B)) ||
-        !r->st[1].ensure(tmgpu::beam_state_bytes(Gc, B)) ||
-        !r->scale.ensure((size_t)Gc * sizeof(float)) ||
-        !r->bx.ensure((size_t)Gc * per_group * tmgpu::kRankF * sizeof(tmgpu::bf16_raw)) ||
-        !r->blog.ensure((size_t)Gc * per_group * sizeof(float)) ||
-        !r->hms.ensure((size_t)G * sizeof(int32_t)) ||
-        (!d_status && !r->bstatus.ensure((size_t)G * sizeof(int32_t))))
-        return TM_ENOMEM;
-    cudaStream_t s = (cudaStream_t)stream;
-    int32_t* status = d_status ? d_status : r->bstatus.as<int32_t>();
-    int32_t* hms = r->hms.as<int32_t>();
-    // the paper's heuristic first: its order is the fallback (Algorithm 1)
-    cudaError_t e = tmgpu::launch_heuristic(d_tasks, d_offsets, G, d_devs, d_orders_out, hms,
-                                            status, s);
-    for (int g0 = 0; g0 < G && e == cudaSuccess; g0 += Gc) {
-        const int gc = std::min(Gc, G - g0);
-        int nm = 0;
-        for (int g = g0; g < g0 + gc; ++g) nm = std::max(nm, h_offsets[g + 1] - h_offsets[g]);
-        const int32_t* off = d_offsets + g0;
-        void* cur = r->st[0].p;
-        void* nxt = r->st[1].p;
-        e = tmgpu::beam_init(off, status + g0, d_tasks, d_devs + g0, gc, B, cur,
-                             r->scale.as<float>(), s);
-        for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
-            const int R = nm - pos;
-            const int64_t rows = (int64_t)gc * B * R;
-            e = tmgpu::beam_features(off, d_tasks, d_devs + g0, r->scale.as<float>(), cur, gc, B,
-                                     R, pos, r->bx.as<tmgpu::bf16_raw>(), s);
-            if (e == cudaSuccess)
-                e = tmgpu::ranker_forward(r->bx.as<tmgpu::bf16_raw>(), rows, r->Wb, r->P,
-                                          r->blog.as<float>(), nullptr, 0, forward_blocks(r, rows), s);
-            if (e == cudaSuccess)
-                e = tmgpu::beam_select(off, d_tasks, r->blog.as<float>(), cur, nxt, gc, B, R, pos, s);
-            std::swap(cur, nxt);
-        }
-        if (e == cudaSuccess)
-            e = tmgpu::beam_finish(off, status + g0, cur, gc, B, hms + g0, d_orders_out,
-                                   d_makespans_out ? d_makespans_out + g0 : nullptr,
-                                   d_beam_won ? d_beam_won + g0 : nullptr, s);
-    }
-    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+    return tmgpu::beam_batch(r, r->beam, d_tasks, d_offsets, h_offsets, G, d_devs, beam_width,
+                             d_orders_out, d_makespans_out, d_status, d_beam_won,
+                             (cudaStream_t)stream);
 }
 
 }  // extern "C"

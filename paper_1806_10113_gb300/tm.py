@@ -92,10 +92,17 @@ _SIGS = {
     "tm_ranker_adam_dev": [_vp, ctypes.c_float, _vp],
     "tm_beam_batch_dev": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
                           _vp, _vp],
+    "tm_server_create": [_vp, _vp, ctypes.POINTER(_vp)],
+    "tm_server_submit": [_vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_uint64)],
+    "tm_server_poll": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "tm_server_replay": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp],
+    "tm_server_counters": [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_int64)],
+    "tm_server_destroy": [_vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
-_RESTYPE = {"tm_plan_destroy": None, "tm_ranker_destroy": None, "tm_strerror": ctypes.c_char_p,
+_RESTYPE = {"tm_plan_destroy": None, "tm_ranker_destroy": None, "tm_server_destroy": None, "tm_strerror": ctypes.c_char_p,
             "tm_version": ctypes.c_char_p}
 
 
@@ -466,3 +473,84 @@ def tm_beam_batch_dev(ranker: Ranker, d_tasks, d_offsets, offsets, d_devs, beam_
                                    off.shape[0] - 1, _dptr(d_devs), int(beam_width),
                                    _dptr(d_orders_out), _dptr(d_makespans_out), _dptr(d_status),
                                    _dptr(d_beam_won), _stream(stream)), "tm_beam_batch_dev")
+
+
+# ---- serving -------------------------------------------------------------------
+
+TM_METHOD_EXHAUSTIVE, TM_METHOD_BEAM, TM_METHOD_HEURISTIC = 0, 1, 2
+
+RESULT_DTYPE = np.dtype([
+    ("ticket", "<u8"), ("status", "<i4"), ("n", "<i4"), ("makespan", "<i4"), ("method", "<i4"),
+    ("latency_ns", "<i8"), ("order", "<i4", (16,)),
+], align=True)
+assert RESULT_DTYPE.itemsize == 96
+
+
+class ServerConfig(ctypes.Structure):
+    """tm_server_config (0 = default for the sizes)."""
+    _fields_ = [("lanes", ctypes.c_int32), ("lane_groups", ctypes.c_int32),
+                ("lane_tasks", ctypes.c_int32), ("lane_subsets", ctypes.c_int32),
+                ("exact_max_n", ctypes.c_int32), ("beam_width", ctypes.c_int32),
+                ("tuning", Tuning)]
+
+
+class Server:
+    """Owns a tm_server: continuous batching of task groups that arrive one at
+    a time (exhaustive optimum up to exact_max_n tasks, beam search with
+    `ranker` or the heuristic above)."""
+
+    def __init__(self, exact_max_n: int = 12, beam_width: int = 0, ranker: Ranker = None,
+                 lanes: int = 0, lane_groups: int = 0, lane_tasks: int = 0,
+                 lane_subsets: int = 0, tuning: Tuning = None):
+        self.config = ServerConfig(lanes, lane_groups, lane_tasks, lane_subsets, exact_max_n,
+                                   beam_width, tuning if tuning is not None else Tuning())
+        self._ranker = ranker          # keeps the ranker alive while the server runs
+        h = ctypes.c_void_p()
+        _check(lib().tm_server_create(ctypes.byref(self.config),
+                                      ranker.handle if ranker is not None else None,
+                                      ctypes.byref(h)), "tm_server_create")
+        self._h = h
+
+    def submit(self, tasks, dma_engines: int) -> int:
+        t = _tasks(tasks)
+        dev = np.asarray([dma_engines], dtype=np.int32)
+        ticket = ctypes.c_uint64(0)
+        _check(lib().tm_server_submit(self._h, _p(t), t.shape[0], _p(dev), ctypes.byref(ticket)),
+               "tm_server_submit")
+        return int(ticket.value)
+
+    def poll(self, max_results: int = 1024, wait_us: int = 0) -> np.ndarray:
+        out = np.zeros(max(max_results, 1), dtype=RESULT_DTYPE)
+        k = ctypes.c_int(0)
+        _check(lib().tm_server_poll(self._h, _p(out), int(max_results), int(wait_us),
+                                    ctypes.byref(k)), "tm_server_poll")
+        return out[:k.value]
+
+    def replay(self, tasks, offsets, dma, arrival_ns) -> np.ndarray:
+        """Open-loop load from the calling thread; results in group order."""
+        t = _tasks(tasks)
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        G = off.shape[0] - 1
+        dev = _devs(dma, G)
+        arr = np.ascontiguousarray(np.asarray(arrival_ns, dtype=np.int64))
+        out = np.zeros(max(G, 1), dtype=RESULT_DTYPE)
+        _check(lib().tm_server_replay(self._h, _p(t), _p(off), G, _p(dev), _p(arr), _p(out)),
+               "tm_server_replay")
+        return out[:G]
+
+    def counters(self) -> dict:
+        b, c, m = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().tm_server_counters(self._h, ctypes.byref(b), ctypes.byref(c),
+                                        ctypes.byref(m)), "tm_server_counters")
+        return {"batches": b.value, "completed": c.value, "max_batch_groups": m.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().tm_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

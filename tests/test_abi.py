@@ -47,12 +47,14 @@ def test_binding_names_match_header(tm):
     for name in declared_functions():
         if name.startswith("tm_plan_") or name in ("tm_strerror", "tm_version"):
             continue
-        if name.startswith("tm_ranker_") and not hasattr(tm, name):
-            # methods of tm.Ranker (create / destroy are its constructor / close)
-            method = name[len("tm_ranker_"):]
-            assert method in ("create", "destroy") or hasattr(tm.Ranker, method), name
-            continue
-        assert hasattr(tm, name), name
+        for prefix, cls in (("tm_ranker_", tm.Ranker), ("tm_server_", tm.Server)):
+            if name.startswith(prefix) and not hasattr(tm, name):
+                # methods of the class (create / destroy are its constructor / close)
+                method = name[len(prefix):]
+                assert method in ("create", "destroy") or hasattr(cls, method), name
+                break
+        else:
+            assert hasattr(tm, name), name
 
 
 def test_ranker_rows_count(tm):
@@ -111,3 +113,17 @@ def test_plan_rejects_sizes_without_gpu(tm):
     with pytest.raises(tm.TMError) as e:
         tm.Plan([0, 13])
     assert e.value.code == -4
+
+
+def test_server_config_rejected_on_host(tm):
+    # argument checks run before any CUDA call
+    for kw in ({"exact_max_n": 13}, {"exact_max_n": -1}, {"lanes": 9},
+               {"beam_width": 65}, {"beam_width": 8}, {"lane_tasks": 8}):
+        with pytest.raises(tm.TMError) as e:
+            tm.Server(**kw)
+        assert e.value.code == -1, kw
+
+
+def test_result_layout(tm):
+    assert tm.RESULT_DTYPE.itemsize == 96
+    assert tm.RESULT_DTYPE.fields["order"][1] == 32
