@@ -46,6 +46,14 @@ WORKLOADS = {
     "ragged8192": ("8192 ragged groups, n~U{4..9}, each task dominant-kernel or dominant-transfer "
                    "(p=1/2), durations log-uniform [1e4,1e7] ns, seed 2, DMA engines alternating "
                    "2/1: exhaustive n! orders + heuristic per group"),
+    "beam12": ("2048 groups x 12 tasks (6 dominant-kernel + 6 dominant-transfer, log-uniform "
+               "[1e4,1e7] ns, seed 3), each under 2 and 1 DMA engines: learned beam search "
+               "(width 64; ranker trained on 2M exhaustively labelled groups, n~U{6..10}) "
+               "vs the exhaustive optimum"),
+    "serve20k": ("Poisson arrivals at 20k groups/s for 5 s, n~U{4..16}, each task dominant-kernel "
+                 "or dominant-transfer (p=1/2), log-uniform [1e4,1e7] ns, seed 4, DMA engines "
+                 "alternating 2/1: served one by one by the continuous-batching server "
+                 "(exhaustive optimum up to 12 tasks, learned beam 64 above)"),
 }
 WORKLOAD = WORKLOADS["dkdt64x10"]
 # Integer operations per evaluated order, as the plain method counts them:
@@ -458,6 +466,209 @@ def run_tm(args):
     return 0
 
 
+# ---- learned beam and serving (secondary workloads) --------------------------------
+
+FLOPS_PER_RANKER_ROW = 2 * (32 * 128 + 128 * 128 + 128 * 128 + 128)
+
+
+def trained_ranker(args, log):
+    from paper_1806_10113_gb300 import learn, tm
+    ranker = tm.Ranker(seed=5)
+    if args.ranker:
+        ranker.set_params(np.load(args.ranker))
+        return ranker, {"loaded": args.ranker}
+    info = learn.train(ranker, groups=args.train_groups, epochs=3, seed=5, lr=2e-3, log=log)
+    if args.ranker_out:
+        np.save(args.ranker_out, ranker.get_params())
+    return ranker, {k: info[k] for k in ("groups", "epochs", "losses", "label_s", "train_s")}
+
+
+def run_beam12(args):
+    import torch
+    from paper_1806_10113_gb300 import learn, tm
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr)
+    ranker, train_info = trained_ranker(args, log)
+    test = inputs.half_dk_half_dt(args.groups or 2048, 12, seed=3, models=(2, 1))
+    G, T = test.G, int(test.tasks.shape[0])
+    dev = learn.to_device(test)
+    d_tasks, d_offsets, d_devs = dev
+    # the exhaustive optimum, timed (one pass over all groups after a warm-up on a few)
+    plan_small = tm.Plan(test.offsets[:9])
+    d_stats = torch.zeros(G * 72, dtype=torch.uint8, device="cuda")
+    tm.tm_exhaustive_batch_dev(plan_small, d_tasks, d_devs, d_stats)
+    plan = tm.Plan(test.offsets, pdmax=5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tm.tm_exhaustive_batch_dev(plan, d_tasks, d_devs, d_stats)
+    e1.record()
+    torch.cuda.synchronize()
+    ex_s = e0.elapsed_time(e1) / 1000.0
+    best = learn.stats_host(d_stats, G)["best"].astype(np.int64)
+    plan.close()
+    # the beam search, device-timed over K steps
+    d_orders = torch.zeros(T, dtype=torch.int32, device="cuda")
+    d_ms = torch.zeros(G, dtype=torch.int32, device="cuda")
+    d_won = torch.zeros(G, dtype=torch.int32, device="cuda")
+    step = lambda: tm.tm_beam_batch_dev(ranker, d_tasks, d_offsets, test.offsets, d_devs, 64,
+                                        d_orders, d_ms, d_beam_won=d_won)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = min(args.steps, 50)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    sampler = ClockSampler(bus_id_of(0))
+    sampler.start()
+    time.sleep(0.2)
+    for k in range(K):
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    beam_s = statistics.mean(a.elapsed_time(c) for a, c in ev) / 1000.0
+    ms = d_ms.cpu().numpy().astype(np.int64)
+    gap = (ms - best) / best
+    # e2e: inputs from pinned host memory, orders and makespans read back
+    h_tasks = torch.from_numpy(test.tasks).pin_memory()
+    h_off = torch.from_numpy(test.offsets).pin_memory()
+    h_dma = torch.from_numpy(test.dma).pin_memory()
+    o_orders = torch.empty(T, dtype=torch.int32).pin_memory()
+    o_ms = torch.empty(G, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        d_tasks.copy_(h_tasks, non_blocking=True)
+        d_offsets.copy_(h_off, non_blocking=True)
+        d_devs.copy_(h_dma, non_blocking=True)
+        step()
+        o_orders.copy_(d_orders, non_blocking=True)
+        o_ms.copy_(d_ms, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / 5
+    # the ranker's forward kernel alone on the beam's row count, for its roofline
+    rows = sum(G * 64 * (12 - p) for p in range(12))
+    chunk = min(rows, 1 << 22)
+    X = torch.zeros(chunk * 32, dtype=torch.int16, device="cuda")
+    lg = torch.zeros(chunk, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ranker.forward_dev(X, chunk, lg)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(10):
+        ranker.forward_dev(X, chunk, lg)
+    f1.record()
+    torch.cuda.synchronize()
+    fwd_s = f0.elapsed_time(f1) / 1000.0 / 10
+    tflops = FLOPS_PER_RANKER_ROW * chunk / fwd_s / 1e12
+    peak = measured_peak("bf16_tflops") or 1900.0
+    out = {
+        "metric": "task groups scheduled/s at <=1% gap (learned beam, n=12)",
+        "value": G / beam_s, "unit": "groups/s", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": 1000 * beam_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 ranker, int32 model",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["beam12"], "groups": G, "beam": 64,
+                   "l2": "inputs < L2; no flush (ranker weights stay resident by design)"},
+        "gap_mean": float(gap.mean()), "gap_p99": float(np.quantile(gap, 0.99)),
+        "gap_max": float(gap.max()),
+        "within_1pct": float((gap <= 0.01).mean()), "optimal": float((gap == 0).mean()),
+        "beam_won": float(d_won.float().mean()),
+        "exhaustive_groups_per_s": G / ex_s,
+        "speedup_vs_exhaustive": (G / beam_s) / (G / ex_s),
+        "e2e": {"value": G / e2e_s, "unit": "groups/s",
+                "h2d_bytes_per_step": int(test.tasks.nbytes + test.offsets.nbytes + test.dma.nbytes),
+                "d2h_bytes_per_step": int(4 * T + 4 * G)},
+        "gpu_launches": 2 + 12 * 3 + 1,
+        "roofline": {"bound": "tensor", "kernel": "forward_kernel (ranker MLP, WMMA bf16)",
+                     "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tflops / peak, "traffic": None,
+                     "basis": f"{FLOPS_PER_RANKER_ROW} FLOP per row, {chunk} rows per launch, "
+                              "timed alone"},
+        "clocks": clocks,
+        "train": train_info,
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def run_serve(args):
+    import torch
+    from paper_1806_10113_gb300 import tm
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr)
+    ranker, train_info = trained_ranker(args, log)
+    rate, seconds = 20000.0, args.serve_seconds
+    G = int(rate * seconds)
+    b = inputs.training_groups(G, 4, 16, seed=4)
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1e9 / rate, G)).astype(np.int64)
+    srv = tm.Server(exact_max_n=args.exact_max_n, beam_width=64, ranker=ranker, lanes=4,
+                    lane_groups=1024, lane_subsets=1024 * 64)
+    warm = min(G, 2000)
+    srv.replay(b.tasks[:b.offsets[warm]], b.offsets[:warm + 1], b.dma[:warm],
+               arrivals[:warm] - arrivals[0])
+    sampler = ClockSampler(bus_id_of(0))
+    sampler.start()
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    res = srv.replay(b.tasks, b.offsets, b.dma, arrivals)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    counters = srv.counters()
+    srv.close()
+    if (res["status"] != 0).any():
+        raise RuntimeError("server reported errors")
+    lat_ms = res["latency_ns"] / 1e6
+    done_ns = arrivals + res["latency_ns"]
+    span_s = (done_ns.max() - arrivals.min()) / 1e9
+    meth = res["method"]
+    sizes = b.sizes()
+    _, h_ms = tm.tm_heuristic_batch(b.tasks, b.offsets, b.dma)
+    gain = (h_ms.astype(np.int64) - res["makespan"]) / h_ms
+    out = {
+        "metric": "decision latency p99 at Poisson 20k groups/s (n~U{4..16})",
+        "value": float(np.quantile(lat_ms, 0.99)), "unit": "ms", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1000 * wall, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 model, bf16 ranker",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve20k"], "groups": G,
+                   "exact_max_n": args.exact_max_n, "lanes": 4, "lane_groups": 1024},
+        "p50_ms": float(np.quantile(lat_ms, 0.5)), "p90_ms": float(np.quantile(lat_ms, 0.9)),
+        "p99_ms": float(np.quantile(lat_ms, 0.99)), "max_ms": float(lat_ms.max()),
+        "groups_per_s": G / span_s, "offered_groups_per_s": rate,
+        "batches": counters["batches"], "mean_batch_groups": G / max(1, counters["batches"] - 1),
+        "max_batch_groups": counters["max_batch_groups"],
+        "methods": {"exhaustive": int((meth == 0).sum()), "beam": int((meth == 1).sum()),
+                    "heuristic": int((meth == 2).sum())},
+        "latency_by_size_ms": {
+            str(n): {"p50": float(np.quantile(lat_ms[sizes == n], 0.5)),
+                     "p99": float(np.quantile(lat_ms[sizes == n], 0.99))}
+            for n in range(4, 17) if (sizes == n).any()},
+        "gain_over_heuristic_mean": float(gain.mean()),
+        "gain_over_heuristic_large_mean": float(gain[sizes > args.exact_max_n].mean()),
+        "e2e": {"value": G / span_s, "unit": "groups/s",
+                "h2d_bytes_per_step": int(b.tasks.nbytes + b.dma.nbytes),
+                "d2h_bytes_per_step": int(res.nbytes)},
+        "gpu_launches": None,
+        "clocks": clocks,
+        "train": train_info,
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def measured_peak(key: str):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get(key)
+        return float(v) if v else None
+    except (OSError, ValueError, TypeError):
+        return None
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,11 +680,21 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay each step as one CUDA graph")
     ap.add_argument("--tuning", default="",
                     help="pdmax,fuse_finalize,blocks_per_sm (skips the autotuner)")
+    ap.add_argument("--groups", type=int, default=0, help="beam12: test groups (default 2048)")
+    ap.add_argument("--train-groups", type=int, default=2_000_000)
+    ap.add_argument("--ranker", default="", help="load ranker parameters (.npy) instead of training")
+    ap.add_argument("--ranker-out", default="", help="save the trained ranker parameters (.npy)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--exact-max-n", type=int, default=12)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "beam12":
+        return run_beam12(args)
+    if args.workload == "serve20k":
+        return run_serve(args)
     return run_tm(args)
 
 

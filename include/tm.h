@@ -334,15 +334,16 @@ int tm_ranker_rows_dev(tm_ranker* ranker, const tm_task* d_tasks,
                        int32_t* d_state_off, int32_t* d_target,
                        int32_t* d_status, void* stream);
 
-/* Scores rows: d_logits[rows] from d_X [rows x 32].  Stream-ordered. */
+/* Scores rows: d_logits[rows] from d_X [rows x 32] (d_X 16-byte aligned,
+ * else TM_EINVAL).  Stream-ordered. */
 int tm_ranker_forward_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
                           float* d_logits, void* stream);
 
 /* Loss (mean over states of the softmax cross-entropy) and its gradient with
  * respect to the parameters, kept in the ranker for tm_ranker_adam_dev and
  * copied to d_grad [TM_RANKER_PARAMS] / d_loss [1] when those are not NULL.
- * d_X must hold ceil16(rows) rows whose tail past `rows` is zero (as
- * tm_ranker_rows_dev leaves it).  Stream-ordered. */
+ * d_X must be 16-byte aligned and hold ceil16(rows) rows whose tail past
+ * `rows` is zero (as tm_ranker_rows_dev leaves it).  Stream-ordered. */
 int tm_ranker_grad_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
                        const int32_t* d_state_off, const int32_t* d_target,
                        int32_t states, float* d_grad, float* d_loss, void* stream);

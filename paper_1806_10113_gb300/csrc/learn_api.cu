@@ -42,7 +42,7 @@ int forward_blocks(const tm_ranker* r, int64_t M)
 {
     const int64_t slabs = (M + 15) / 16;
     const int64_t want = (slabs + 7) / 8;   // 8 warps per block, one slab per warp
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, r->sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * r->sms));   // 2 blocks per SM
 }
 
 int on_device(const tm_ranker* r)
@@ -222,6 +222,7 @@ int tm_ranker_forward_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows, float
                           void* stream)
 {
     if (!r || rows < 0 || (rows > 0 && (!d_X || !d_logits))) return TM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_X) % 16) return TM_EINVAL;   // rows are read 16 bytes at a time
     if (int rc = on_device(r)) return rc;
     if (rows == 0) return TM_OK;
     cudaError_t e = tmgpu::ranker_forward(d_X, rows, r->Wb, r->P, d_logits, nullptr, 0,
@@ -234,6 +235,7 @@ int tm_ranker_grad_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows,
                        float* d_grad, float* d_loss, void* stream)
 {
     if (!r || rows <= 0 || states <= 0 || !d_X || !d_state_off || !d_target) return TM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_X) % 16) return TM_EINVAL;
     if (rows > INT32_MAX - 16) return TM_EINVAL;
     if (int rc = on_device(r)) return rc;
     const int64_t M_pad = (rows + 15) / 16 * 16;

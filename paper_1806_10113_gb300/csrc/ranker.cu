@@ -24,78 +24,129 @@ constexpr int kSlab = 16;         // rows per warp
 
 // ---- forward ----------------------------------------------------------------
 
-// One warp's 16-row slab through a [16 x K] x [K x 128] layer: the
-// accumulators land in `stage` (row-major float, ld 128).
-template <int K>
-__device__ __forceinline__ void slab_layer(const bf16* __restrict__ act, const bf16* __restrict__ W,
-                                           float* __restrict__ stage)
-{
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) wmma::fill_fragment(acc[t], 0.0f);
-#pragma unroll
-    for (int kk = 0; kk < K; kk += 16) {
-        wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> a;
-        wmma::load_matrix_sync(a, act + kk, K);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> b;
-            wmma::load_matrix_sync(b, W + kk * kH + 16 * t, kH);
-            wmma::mma_sync(acc[t], a, b, acc[t]);
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) wmma::store_matrix_sync(stage + 16 * t, acc[t], kH, wmma::mem_row_major);
-    __syncwarp();
-}
+// The forward pass keeps each warp's 16 rows in registers from the input to
+// the logit: mma.sync m16n8k16 (bf16 in, f32 accumulate).  The f32
+// accumulator fragment of an output n-tile pair has exactly the register
+// layout of the bf16 A fragment of the next layer's k-tile (PTX ISA,
+// "Matrix fragments for mma.m16n8k16"), so bias, ReLU and the bfloat16
+// rounding happen in registers and no activation goes through shared
+// memory.  Weights sit in shared memory transposed (n-major, rows padded by
+// 16 bytes so that ldmatrix is free of bank conflicts); one ldmatrix.x4
+// gives the B fragments of two n-tiles.
+//
+// Fragment coordinates, with g = lane / 4 and t = lane % 4:
+//   A (16 x 16): reg0 = (g, 2t..2t+1), reg1 = (g+8, 2t..), reg2 = (g, 8+2t..),
+//                reg3 = (g+8, 8+2t..)
+//   C (16 x 8):  c0, c1 = (g, 2t..2t+1), c2, c3 = (g+8, 2t..2t+1)
+// The first layer reads each row's 32 features with one 16-byte load per
+// thread: thread t takes features 8t .. 8t+7, which it feeds to the mma as
+// k = 16 kt + 8 h + 2t + j  <->  feature 8t + 4 kt + 2 h + j  (j, h in {0, 1});
+// the rows of W1 are stored in that order.
 
-// stage + bias, ReLU, rounded to bfloat16 into `out` (and `keep` if given).
-__device__ __forceinline__ void slab_epilogue(const float* __restrict__ stage,
-                                              const float* __restrict__ bias, bf16* __restrict__ out,
-                                              bf16* __restrict__ keep, int rows_valid)
-{
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < kSlab * kH; i += 32) {
-        const int r = i / kH, c = i - r * kH;
-        const bf16 v = __float2bfloat16_rn(fmaxf(stage[i] + bias[c], 0.0f));
-        out[i] = v;
-        if (keep && r < rows_valid) keep[(size_t)r * kH + c] = v;
-    }
-    __syncwarp();
-}
+constexpr int kW1Ld = kF + 8;     // padded row length (elements) of W1^T in shared memory
+constexpr int kWLd = kH + 8;      // ... of W2^T and W3^T
 
-struct __align__(128) FwdShared {
-    bf16 W1[kF * kH];
-    bf16 W2[kH * kH];
-    bf16 W3[kH * kH];
-    float w4[kH];
-    float b1[kH], b2[kH], b3[kH];
+struct __align__(16) FwdShared {
+    bf16 W1t[kH * kW1Ld];
+    bf16 W2t[kH * kWLd];
+    bf16 W3t[kH * kWLd];
+    float b1[kH], b2[kH], b3[kH], w4[kH];
     float b4;
-    struct __align__(128) Slab {
-        bf16 x[kSlab * kF];
-        bf16 a[kSlab * kH];
-        bf16 b[kSlab * kH];
-        float stage[kSlab * kH];
-    } slab[kWarps];
 };
 
 __device__ __forceinline__ float bf(const bf16 v) { return __bfloat162float(v); }
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// acc[16 n-tiles][4] += A (16 x 16 KT) x W^T-tile, W^T in shared memory at
+// `wt` with row length ld (elements).
+template <int KT>
+__device__ __forceinline__ void layer_mma(float (&acc)[16][4], const uint32_t (&A)[KT][4],
+                                          uint32_t wt, int ld, int lane)
+{
+    // lanes 0-7 / 8-15 / 16-23 / 24-31 address the rows of the four 8x8
+    // matrices: (n-tile 2p, k 0-7), (2p, k 8-15), (2p+1, k 0-7), (2p+1, k 8-15)
+    const int n_in = (lane & 7) + ((lane >> 4) << 3);
+    const int k_in = ((lane >> 3) & 1) * 8;
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4(wt + (uint32_t)(((16 * p + n_in) * ld + 16 * kt + k_in) * 2), b0, b1, b2, b3);
+            mma_bf16(acc[2 * p], A[kt], b0, b1);
+            mma_bf16(acc[2 * p + 1], A[kt], b2, b3);
+        }
+    }
+}
+
+// Bias + ReLU + bfloat16 rounding of a 16 x 128 accumulator into the A
+// fragments of the next layer (and the kept activations, row-major, when
+// `keep` is set).
+__device__ __forceinline__ void layer_epilogue(float (&acc)[16][4], const float* __restrict__ bias,
+                                               uint32_t (&A)[8][4], bf16* __restrict__ keep,
+                                               int rows, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float bl = bias[8 * j + 2 * t], bh = bias[8 * j + 2 * t + 1];
+        const uint32_t top = pack_bf16(fmaxf(acc[j][0] + bl, 0.f), fmaxf(acc[j][1] + bh, 0.f));
+        const uint32_t bot = pack_bf16(fmaxf(acc[j][2] + bl, 0.f), fmaxf(acc[j][3] + bh, 0.f));
+        A[j >> 1][(j & 1) * 2] = top;
+        A[j >> 1][(j & 1) * 2 + 1] = bot;
+        if (keep) {
+            if (g < rows) *reinterpret_cast<uint32_t*>(keep + (size_t)g * kH + 8 * j + 2 * t) = top;
+            if (g + 8 < rows)
+                *reinterpret_cast<uint32_t*>(keep + (size_t)(g + 8) * kH + 8 * j + 2 * t) = bot;
+        }
+    }
+}
+
 // logits[r] for rows r < M of X; with keep != null also stores a1, a2, a3
 // ([stride x 128] each, at keep + l * stride * 128).  Persistent: each warp
 // takes 16-row slabs in turn.
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 2)
 forward_kernel(const bf16* __restrict__ X, int64_t M, const bf16* __restrict__ Wb,
                const float* __restrict__ P, float* __restrict__ logits, bf16* __restrict__ keep,
                int64_t stride)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdShared& s = *reinterpret_cast<FwdShared*>(smem_raw);
-    for (int i = threadIdx.x; i < kF * kH; i += blockDim.x) s.W1[i] = Wb[kBfW1 + i];
+    // W1 (in x out) -> W1^T with the input features permuted (see above)
+    for (int i = threadIdx.x; i < kF * kH; i += blockDim.x) {
+        const int k = i / kH, n = i - k * kH;          // W1[k][n], k a feature
+        const int tt = k >> 3, r = k & 7;               // feature 8 tt + r
+        const int kt = r >> 2, h = (r >> 1) & 1, j = r & 1;
+        s.W1t[n * kW1Ld + 16 * kt + 8 * h + 2 * tt + j] = Wb[kBfW1 + i];
+    }
     for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-        s.W2[i] = Wb[kBfW2 + i];
-        s.W3[i] = Wb[kBfW3 + i];
+        const int k = i / kH, n = i - k * kH;
+        s.W2t[n * kWLd + k] = Wb[kBfW2 + i];
+        s.W3t[n * kWLd + k] = Wb[kBfW3 + i];
     }
     for (int i = threadIdx.x; i < kH; i += blockDim.x) {
         s.w4[i] = bf(Wb[kBfW4 + i]);
@@ -106,35 +157,54 @@ forward_kernel(const bf16* __restrict__ X, int64_t M, const bf16* __restrict__ W
     if (threadIdx.x == 0) s.b4 = P[kOffB4];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    FwdShared::Slab& w = s.slab[warp];
+    const int g = lane >> 2, t = lane & 3;
+    const uint32_t w1 = (uint32_t)__cvta_generic_to_shared(s.W1t);
+    const uint32_t w2 = (uint32_t)__cvta_generic_to_shared(s.W2t);
+    const uint32_t w3 = (uint32_t)__cvta_generic_to_shared(s.W3t);
     const int64_t slabs = (M + kSlab - 1) / kSlab;
     for (int64_t sl = (int64_t)blockIdx.x * kWarps + warp; sl < slabs;
          sl += (int64_t)gridDim.x * kWarps) {
         const int64_t r0 = sl * kSlab;
         const int rows = (int)lmin(kSlab, M - r0);
-        for (int i = lane; i < kSlab * kF; i += 32) {
-            const int r = i / kF;
-            w.x[i] = r < rows ? X[(size_t)r0 * kF + i] : __float2bfloat16_rn(0.0f);
-        }
-        __syncwarp();
-        bf16* k1 = keep ? keep + (size_t)r0 * kH : nullptr;
-        bf16* k2 = keep ? keep + (size_t)stride * kH + (size_t)r0 * kH : nullptr;
-        bf16* k3 = keep ? keep + 2 * (size_t)stride * kH + (size_t)r0 * kH : nullptr;
-        slab_layer<kF>(w.x, s.W1, w.stage);
-        slab_epilogue(w.stage, s.b1, w.a, k1, rows);
-        slab_layer<kH>(w.a, s.W2, w.stage);
-        slab_epilogue(w.stage, s.b2, w.b, k2, rows);
-        slab_layer<kH>(w.b, s.W3, w.stage);
-        slab_epilogue(w.stage, s.b3, w.a, k3, rows);
-        // head: one row per half-warp pass, lanes over the 128 inputs
-        for (int r = 0; r < rows; ++r) {
-            float acc = 0.0f;
-            for (int c = lane; c < kH; c += 32) acc += bf(w.a[r * kH + c]) * s.w4[c];
+        // layer 1 A fragments straight from global memory
+        uint4 top = make_uint4(0, 0, 0, 0), bot = make_uint4(0, 0, 0, 0);
+        if (g < rows) top = *reinterpret_cast<const uint4*>(X + (size_t)(r0 + g) * kF + 8 * t);
+        if (g + 8 < rows) bot = *reinterpret_cast<const uint4*>(X + (size_t)(r0 + g + 8) * kF + 8 * t);
+        uint32_t A1[2][4] = {{top.x, bot.x, top.y, bot.y}, {top.z, bot.z, top.w, bot.w}};
+        float acc[16][4];
+        uint32_t A[8][4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            if (lane == 0) logits[r0 + r] = acc + s.b4;
+        for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        layer_mma<2>(acc, A1, w1, kW1Ld, lane);
+        layer_epilogue(acc, s.b1, A, keep ? keep + (size_t)r0 * kH : nullptr, rows, lane);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        layer_mma<8>(acc, A, w2, kWLd, lane);
+        layer_epilogue(acc, s.b2, A, keep ? keep + ((size_t)stride + r0) * kH : nullptr, rows, lane);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        layer_mma<8>(acc, A, w3, kWLd, lane);
+        layer_epilogue(acc, s.b3, A, keep ? keep + (2 * (size_t)stride + r0) * kH : nullptr, rows,
+                       lane);
+        // head: a3 . w4 over this thread's columns, then over the 4 threads of a row
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const __nv_bfloat162 vt = *reinterpret_cast<const __nv_bfloat162*>(&A[j >> 1][(j & 1) * 2]);
+            const __nv_bfloat162 vb =
+                *reinterpret_cast<const __nv_bfloat162*>(&A[j >> 1][(j & 1) * 2 + 1]);
+            const float wl = s.w4[8 * j + 2 * t], wh = s.w4[8 * j + 2 * t + 1];
+            lo += __low2float(vt) * wl + __high2float(vt) * wh;
+            hi += __low2float(vb) * wl + __high2float(vb) * wh;
         }
-        __syncwarp();
+        lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 1);
+        lo += __shfl_xor_sync(0xFFFFFFFFu, lo, 2);
+        hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 1);
+        hi += __shfl_xor_sync(0xFFFFFFFFu, hi, 2);
+        if (t == 0) {
+            if (g < rows) logits[r0 + g] = lo + s.b4;
+            if (g + 8 < rows) logits[r0 + g + 8] = hi + s.b4;
+        }
     }
 }
 
