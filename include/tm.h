@@ -168,12 +168,18 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  work split, 1..occupancy limit; 0: the occupancy limit
  *   item_cost      the work split gives each thread the same estimated cost,
  *                  a work item costing its orders plus item_cost (fixed
- *                  per-item work, in orders); 0: default 4096 */
+ *                  per-item work, in orders); 0: default 4096
+ *   chunks_per_thread  1: each enumeration thread takes one fixed share of
+ *                  the cost; 2..64: the cost is cut into that many chunks per
+ *                  thread, which warps take from a counter as they finish
+ *                  (dynamic balance, for batches whose orders cost unevenly;
+ *                  needs fuse_finalize != 1); 0: default 1 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;
     int32_t blocks_per_sm;
     int32_t item_cost;
+    int32_t chunks_per_thread;
 } tm_tuning;
 
 int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tuning,
@@ -374,18 +380,20 @@ int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
 /* A scheduling server for task groups that arrive one at a time (the paper
  * schedules each group as it is submitted to the device, Sec. 5.1; it has no
  * serving system).  A host worker thread gathers every waiting group into a
- * batch as soon as one of the server's lanes is free (continuous batching)
- * and runs it on that lane's two CUDA streams: groups of n <= exact_max_n
- * get the exhaustive optimum (first best order, as tm_exhaustive_batch_dev),
- * larger ones the beam search with `ranker` (tm_beam_batch_dev) if
- * beam_width > 0, else the heuristic (tm_heuristic_batch_dev).  A group's
- * result does not depend on the other groups of its batch.
+ * batch as soon as a lane of the right kind is free (continuous batching)
+ * and runs it on that lane's CUDA stream.  Exact lanes give groups of
+ * n <= exact_max_n the exhaustive optimum (first best order, as
+ * tm_exhaustive_batch_dev); search lanes give larger groups the beam search
+ * with `ranker` (tm_beam_batch_dev) if beam_width > 0, else the heuristic
+ * (tm_heuristic_batch_dev).  The two kinds run side by side, so a small
+ * group never waits behind a long search.  A group's result does not depend
+ * on the other groups of its batch.
  *
  * Memory: each lane owns fixed device and pinned host memory sized by the
  * config at creation; a batch takes at most lane_groups groups, lane_tasks
- * tasks and lane_subsets 4-task subsets of exhaustively searched groups
- * (C(n, 4) per group), and a group waits on the host until a lane has room
- * (first come, first served).  Serving itself allocates nothing.
+ * tasks and (exact lanes) lane_subsets 4-task subsets (C(n, 4) per group),
+ * and a group waits on the host until a lane of its kind has room (first
+ * come, first served within a kind).  Serving itself allocates nothing.
  *
  * Threads: submit / poll / replay may be called from any host thread; the
  * server runs on the device current at creation.  Results are delivered
@@ -393,7 +401,7 @@ int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
 typedef struct tm_server tm_server;
 
 typedef struct tm_server_config {
-    int32_t lanes;          /* batches in flight, 1..8 (0: 2) */
+    int32_t lanes;          /* lanes of each kind (batches in flight), 1..8 (0: 2) */
     int32_t lane_groups;    /* groups per batch (0: 1024) */
     int32_t lane_tasks;     /* tasks per batch, >= 16 (0: 16 x lane_groups) */
     int32_t lane_subsets;   /* 4-task subsets per batch, >= 495 (0: 210 x lane_groups) */

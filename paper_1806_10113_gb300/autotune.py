@@ -1,7 +1,8 @@
 """Autotuner for exhaustive-search plans.
 
 Picks the tm_tuning (prefix depth per work item, fused or separate
-finalize, resident blocks per SM) that runs a given batch fastest, by
+finalize, resident blocks per SM, per-item cost weight, static or dynamic
+work split) that runs a given batch fastest, by
 timing each candidate on the device with CUDA events (L2 flushed between
 runs), and caches the choice in a JSON file keyed by the batch's shape (the
 number of groups of each size), so later plans for the same shape reuse it
@@ -24,7 +25,8 @@ CANDIDATES = {
     "pdmax": (3, 4, 5),
     "fuse_finalize": (2,),
     "blocks_per_sm": (0, 3),
-    "item_cost": (1024, 4096, 16384),
+    "item_cost": (4096, 16384, 65536),
+    "chunks_per_thread": (1, 3, 6, 12),
 }
 _lock = threading.Lock()
 

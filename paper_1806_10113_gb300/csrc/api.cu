@@ -111,7 +111,7 @@ struct Context {
 thread_local std::unique_ptr<Context> t_ctx;
 
 std::mutex g_tune_mu;
-tm_tuning g_default_tuning{0, 0, 0, 0};
+tm_tuning g_default_tuning{0, 0, 0, 0, 0};
 unsigned g_tuning_epoch = 0;   // bumped on every change; cached plans compare it
 
 int context(Context** out)
@@ -152,6 +152,14 @@ int first_error(const int32_t* status, int G)
 
 // ---- plans -----------------------------------------------------------------
 
+bool tuning_invalid(const tm_tuning& t)
+{
+    return (t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
+           t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 ||
+           t.item_cost > (1 << 20) || t.chunks_per_thread < 0 || t.chunks_per_thread > 64 ||
+           (t.fuse_finalize == 1 && t.chunks_per_thread != 1);
+}
+
 void free_plan(Plan& p)
 {
     if (p.d_gp) cudaFree(p.d_gp);   // the start of the plan's single block
@@ -191,14 +199,13 @@ int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
     const int pdmax = tune.pdmax == 0 ? 4 : tune.pdmax;
     const bool fused = tune.fuse_finalize == 1;
     const uint32_t item_cost = tune.item_cost == 0 ? 4096u : (uint32_t)tune.item_cost;
-    if (pdmax < 3 || pdmax > 5 || tune.fuse_finalize < 0 || tune.fuse_finalize > 2 ||
-        tune.blocks_per_sm < 0 || tune.item_cost < 0 || tune.item_cost > (1 << 20))
-        return TM_EINVAL;
+    if (tuning_invalid(tune)) return TM_EINVAL;
     if (!h_offsets || G < 0) return TM_EINVAL;
     std::vector<tmgpu::GroupPlan> gp((size_t)G + 1);
     int rc = tmgpu::plan_decompose(h_offsets, G, pdmax, item_cost, gp.data(), &p);
     if (rc != TM_OK) return rc;
     TM_CUDA(cudaGetDevice(&p.device));
+    p.chunks_per_thread = tune.chunks_per_thread == 0 ? 1 : tune.chunks_per_thread;
     tmgpu::exhaustive_partition(p, p.device, tune.blocks_per_sm);
     std::vector<uint32_t> target;
     fused_tables(p, gp, target);
@@ -221,6 +228,7 @@ int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
                            cudaMemcpyHostToDevice) == cudaSuccess &&
                 cudaMemset(p.d_done, 0, tmgpu::kDoneStride * target.size() * sizeof(uint32_t)) ==
                     cudaSuccess));
+    ok = ok && cudaMemset(p.d_next, 0, sizeof(uint32_t)) == cudaSuccess;
     if (!ok) { free_plan(p); return TM_ECUDA; }
     return TM_OK;
 }
@@ -251,7 +259,7 @@ int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tunin
                          tm_plan** plan_out)
 {
     if (!plan_out) return TM_EINVAL;
-    tm_tuning tune{0, 0, 0, 0};
+    tm_tuning tune{0, 0, 0, 0, 0};
     if (tuning) tune = *tuning;
     std::unique_ptr<tm_plan> plan(new (std::nothrow) tm_plan());
     if (!plan) return TM_ENOMEM;
@@ -273,11 +281,9 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
 
 int tm_set_default_tuning(const tm_tuning* tuning)
 {
-    tm_tuning t{0, 0, 0, 0};
+    tm_tuning t{0, 0, 0, 0, 0};
     if (tuning) t = *tuning;
-    if ((t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
-        t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 || t.item_cost > (1 << 20))
-        return TM_EINVAL;
+    if (tuning_invalid(t)) return TM_EINVAL;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_default_tuning = t;
     ++g_tuning_epoch;

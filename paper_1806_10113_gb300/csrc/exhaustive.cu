@@ -241,6 +241,7 @@ struct PrepArgs {
     int32_t* status;
     int32_t* orders;              // heuristic outputs; null: no heuristic
     int32_t* makespans;
+    uint32_t* next;               // dynamic chunk counter to zero, or null
 };
 
 __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
     __shared__ int4 s_task[TM_MAX_EXHAUSTIVE];
     __shared__ int s_status, s_hs;
 
+    if (a.next && g == 0 && tid == 0) *a.next = 0;
     const bool heur = a.orders != nullptr;
     if (heur && warp == kPrepThreads / 32 - 1) {
         heur::heuristic_group(a.tasks, off, n, dma, g, lane, a.orders, a.makespans, nullptr);
@@ -638,21 +640,22 @@ __device__ __noinline__ uint32_t item_rank(uint32_t at, int32_t v, uint32_t hd, 
     return prefix_rank(placed, n, f + pd) + (uint32_t)first_completion(st.k, st.d, v, tab);
 }
 
+// The items whose first cost unit lies in [x0, x1), in order: walk them,
+// settle each against the thread's running best / worst, and report to the
+// group accumulators when the group changes and at the end.
 template <int PDMAX>
-__global__ void __launch_bounds__(kEnumBlock, 4)
-enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
-            const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
-            uint64_t per_thread, uint32_t item_cost, Sink sink)
+__device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
+                                           const GroupInfo* __restrict__ info,
+                                           const int4* __restrict__ tbl,
+                                           const SuffixTab* __restrict__ sub, int G, uint64_t x0,
+                                           uint64_t x1, uint32_t item_cost, const Sink& sink)
 {
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t x0 = t * per_thread;
     const uint64_t total = gp[G].cost_base;
     if (x0 >= total) return;
     uint32_t i = plan_first_item(gp, G, PDMAX, item_cost, x0);
-    const uint32_t end = plan_first_item(gp, G, PDMAX, item_cost, min(x0 + per_thread, total));
+    const uint32_t end = plan_first_item(gp, G, PDMAX, item_cost, min(x1, total));
     if (i >= end) return;
     int g = search_group(G, i, [&](int j) { return (uint64_t)gp[j].item_base; });
-
     Acc a;
     a.reset();
     Sfx S;
@@ -739,6 +742,32 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
     flush_final(a, sink, g);
 }
 
+template <int PDMAX>
+__global__ void __launch_bounds__(kEnumBlock, 4)
+enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
+            const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
+            uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks)
+{
+    if (!next) {   // static split: one range per thread
+        const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        enum_range<PDMAX>(gp, info, tbl, sub, G, t * per_thread, (t + 1) * per_thread, item_cost,
+                          sink);
+        return;
+    }
+    // dynamic: each warp takes 32 consecutive chunks at a time, one per lane
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t c0 = 0;
+        if (lane == 0) c0 = atomicAdd(next, 32u);
+        c0 = __shfl_sync(kFull, c0, 0);
+        if (c0 >= nchunks) break;
+        const uint64_t c = (uint64_t)c0 + lane;
+        enum_range<PDMAX>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
+                          sink);
+        __syncwarp();
+    }
+}
+
 // ---- finalize ---------------------------------------------------------------
 
 // Separate finalize (when the plan has no completion counters): one warp
@@ -757,9 +786,10 @@ template <int PDMAX>
 cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
 {
     uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
-    enum_kernel<PDMAX><<<blocks, kEnumBlock, 0, stream>>>(p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G,
-                                                           p.leaves_per_thread, p.item_cost,
-                                                           sink);
+    const bool dyn = p.chunks_per_thread > 1;
+    enum_kernel<PDMAX><<<blocks, kEnumBlock, 0, stream>>>(
+        p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
+        sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u);
     return cudaGetLastError();
 }
 
@@ -787,6 +817,15 @@ void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
                                           std::max<uint64_t>(p.total_items, 1));
     p.leaves_per_thread = std::max<uint64_t>(1, (p.total_leaves + threads - 1) / threads);
     p.threads = (uint32_t)((p.total_leaves + p.leaves_per_thread - 1) / p.leaves_per_thread);
+    if (p.chunks_per_thread > 1) {
+        p.chunk = std::max<uint64_t>(1, p.leaves_per_thread / (uint64_t)p.chunks_per_thread);
+        const uint64_t nch = (p.total_leaves + p.chunk - 1) / p.chunk;
+        if (nch >= 0xFFFFFF00ull) {           // counter range: fall back to the static split
+            p.chunks_per_thread = 1;
+        } else {
+            p.nchunks = (uint32_t)nch;
+        }
+    }
     p.launches = exhaustive_launch_count(p);
 }
 
@@ -813,6 +852,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.status = d_status;
     pa.orders = d_orders;
     pa.makespans = d_makespans;
+    pa.next = (p.chunks_per_thread > 1 && p.total_items > 0) ? p.d_next : nullptr;
     // many (subset, order) pairs per group (n >= 9: >= 3,024): a bigger block
     prep_kernel<<<p.G, p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();

@@ -1,17 +1,17 @@
 // server.cu -- the serving loop (declared in include/tm.h, "serving"): task
 // groups arrive one by one; a host worker thread gathers whatever is waiting
 // into a batch whenever one of the server's lanes is free (continuous
-// batching) and runs it on that lane's streams: the exhaustive search for
-// groups small enough to solve exactly, the beam search (or the paper's
-// heuristic, Sec. 5.1) for the rest.  Each lane owns fixed device and pinned
-// host memory sized at creation; a request waits on the host until a lane
-// has room for it (memory-admitted slots), so serving allocates nothing.
+// batching) and runs it on that lane's CUDA stream.  Exact lanes run the
+// exhaustive search for groups small enough to solve exactly; search lanes
+// run the beam search (or the paper's heuristic, Sec. 5.1) for the rest, so
+// that a small group never waits behind a long search.  Each lane owns fixed
+// device and pinned host memory sized at creation; a request waits on the
+// host until a lane of its kind has room for it (memory-admitted slots), so
+// serving allocates nothing.
 //
-// Per batch, on the lane's two streams:
-//   s_exact: H2D copy of the packed batch -> prep/enumerate/finalize of the
-//            exact groups -> (wait for s_beam) -> D2H copy of the results
-//   s_beam:  (wait for the H2D copy) -> heuristic + beam search of the rest
-// Results of one group do not depend on the other groups of its batch.
+// Per batch, on the lane's stream: one H2D copy of the packed batch, the
+// kernels, one D2H copy of the packed results, an event.  Results of one
+// group do not depend on the other groups of its batch.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -39,7 +39,7 @@ struct Request {
 
 inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Byte layout of one batch's packed input (H2D) or output (D2H) block.
+// Byte layout of one batch's packed input (H2D) block.
 struct InLayout {
     size_t off, dev, gp, tasks, bytes;
     InLayout(int G, int T)
@@ -51,28 +51,31 @@ struct InLayout {
         bytes = al16(tasks + (size_t)T * sizeof(tm_task));
     }
 };
+
+// ... and of its output (D2H) block: exact lanes fill stats and status,
+// search lanes status, ms, won and orders.
 struct OutLayout {
-    size_t stats, ms, status, won, orders, bytes;
-    OutLayout(int G, int Ge, int T)
+    size_t stats, status, ms, won, orders, bytes;
+    OutLayout(bool exact, int G, int T)
     {
         stats = 0;
-        ms = al16(stats + (size_t)Ge * sizeof(tm_stats));
-        status = al16(ms + (size_t)G * 4);
-        won = al16(status + (size_t)G * 4);
-        orders = al16(won + (size_t)G * 4);
-        bytes = al16(orders + (size_t)T * 4);
+        status = al16(exact ? (size_t)G * sizeof(tm_stats) : 0);
+        ms = al16(status + (size_t)G * 4);
+        won = al16(ms + (exact ? 0 : (size_t)G * 4));
+        orders = al16(won + (exact ? 0 : (size_t)G * 4));
+        bytes = al16(orders + (exact ? 0 : (size_t)T * 4));
     }
 };
 
 struct Lane {
-    cudaStream_t s_exact = nullptr, s_beam = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_beam = nullptr, ev_done = nullptr;
+    bool exact = true;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_done = nullptr;
     unsigned char *h_in = nullptr, *d_in = nullptr, *h_out = nullptr, *d_out = nullptr;
     void* plan_block = nullptr;
-    Plan plan;
-    tmgpu::BeamScratch beam;
-    std::vector<Request> reqs;   // exact groups first
-    int Ge = 0;
+    Plan plan;                       // exact lanes
+    tmgpu::BeamScratch beam;         // search lanes
+    std::vector<Request> reqs;
     int T = 0;
     bool busy = false;
     int launch_rc = TM_OK;
@@ -89,13 +92,15 @@ struct tm_server {
     std::vector<std::unique_ptr<Lane>> lanes;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending;
+    std::deque<Request> pending[2];          // [0] exact, [1] search
     std::deque<tm_server_result> done;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
     std::atomic<int64_t> batches{0}, completed{0}, max_batch{0};
 
+    void enqueue(const Request& r) { pending[r.n <= cfg.exact_max_n ? 0 : 1].push_back(r); }
+    bool idle() const { return pending[0].empty() && pending[1].empty(); }
     void run();
     bool try_launch(Lane& L);
     void complete(Lane& L);
@@ -118,33 +123,31 @@ int check_request(const tm_task* tasks, int n, const tm_device* dev)
 
 }  // namespace
 
-// Gathers waiting requests into lane L (first come, first served, while the
-// lane has room) and enqueues the batch.  Called with `mu` held.
+// Gathers waiting requests of the lane's kind into lane L (first come, first
+// served, while the lane has room) and enqueues the batch.  Called with `mu`
+// held.
 bool tm_server::try_launch(Lane& L)
 {
-    if (pending.empty()) return false;
+    std::deque<Request>& q = pending[L.exact ? 0 : 1];
+    if (q.empty()) return false;
     const int Gcap = cfg.lane_groups, Tcap = cfg.lane_tasks;
     const uint32_t Scap = (uint32_t)cfg.lane_subsets;
-    std::vector<Request> exact, large;
     int tasks = 0;
     uint32_t subs = 0;
-    while (!pending.empty() && (int)(exact.size() + large.size()) < Gcap) {
-        const Request& r = pending.front();
-        const bool is_exact = r.n <= cfg.exact_max_n;
-        const uint32_t c4 = is_exact ? tmgpu::choose4(r.n) : 0u;
+    L.reqs.clear();
+    while (!q.empty() && (int)L.reqs.size() < Gcap) {
+        const Request& r = q.front();
+        const uint32_t c4 = L.exact ? tmgpu::choose4(r.n) : 0u;
         if (tasks + r.n > Tcap || subs + c4 > Scap) break;   // waits for the next free lane
         tasks += r.n;
         subs += c4;
-        (is_exact ? exact : large).push_back(r);
-        pending.pop_front();
+        L.reqs.push_back(r);
+        q.pop_front();
     }
-    if (exact.empty() && large.empty()) return false;
-    L.Ge = (int)exact.size();
-    L.reqs = std::move(exact);
-    L.reqs.insert(L.reqs.end(), large.begin(), large.end());
+    if (L.reqs.empty()) return false;
     L.T = tasks;
     L.busy = true;
-    const int G = (int)L.reqs.size(), Ge = L.Ge, T = tasks;
+    const int G = (int)L.reqs.size(), T = tasks;
     batches.fetch_add(1);
     int64_t mb = max_batch.load();
     while (G > mb && !max_batch.compare_exchange_weak(mb, G)) {}
@@ -165,45 +168,39 @@ bool tm_server::try_launch(Lane& L)
     }
     h_off[G] = off;
     int rc = TM_OK;
-    if (Ge > 0) {
-        rc = tmgpu::plan_decompose(h_off, Ge, pdmax, item_cost, h_gp, &L.plan);
+    if (L.exact) {
+        rc = tmgpu::plan_decompose(h_off, G, pdmax, item_cost, h_gp, &L.plan);
         if (rc == TM_OK) tmgpu::exhaustive_partition(L.plan, device, cfg.tuning.blocks_per_sm);
+        L.plan.d_gp = reinterpret_cast<GroupPlan*>(L.d_in + in.gp);
     }
-    const OutLayout out(G, Ge, T);
-    unsigned char* d = L.d_in;
-    const int32_t* d_off = reinterpret_cast<const int32_t*>(d + in.off);
-    const tm_device* d_dev = reinterpret_cast<const tm_device*>(d + in.dev);
-    const tm_task* d_tasks = reinterpret_cast<const tm_task*>(d + in.tasks);
-    tm_stats* d_stats = reinterpret_cast<tm_stats*>(L.d_out + out.stats);
-    int32_t* d_ms = reinterpret_cast<int32_t*>(L.d_out + out.ms);
+    const OutLayout out(L.exact, G, T);
+    const int32_t* d_off = reinterpret_cast<const int32_t*>(L.d_in + in.off);
+    const tm_device* d_dev = reinterpret_cast<const tm_device*>(L.d_in + in.dev);
+    const tm_task* d_tasks = reinterpret_cast<const tm_task*>(L.d_in + in.tasks);
     int32_t* d_status = reinterpret_cast<int32_t*>(L.d_out + out.status);
-    int32_t* d_won = reinterpret_cast<int32_t*>(L.d_out + out.won);
-    int32_t* d_orders = reinterpret_cast<int32_t*>(L.d_out + out.orders);
-    L.plan.d_gp = reinterpret_cast<GroupPlan*>(d + in.gp);
     auto ok = [&](cudaError_t e) { if (e != cudaSuccess && rc == TM_OK) rc = TM_ECUDA; };
-    if (rc == TM_OK) {
-        ok(cudaMemcpyAsync(L.d_in, L.h_in, in.bytes, cudaMemcpyHostToDevice, L.s_exact));
-        ok(cudaEventRecord(L.ev_in, L.s_exact));
-    }
-    if (rc == TM_OK && Ge > 0)
-        ok(tmgpu::launch_exhaustive(L.plan, d_tasks, d_dev, d_stats, d_status, L.s_exact));
-    if (rc == TM_OK && G > Ge) {
-        ok(cudaStreamWaitEvent(L.s_beam, L.ev_in, 0));
+    if (rc == TM_OK) ok(cudaMemcpyAsync(L.d_in, L.h_in, in.bytes, cudaMemcpyHostToDevice, L.stream));
+    if (rc == TM_OK && L.exact) {
+        ok(tmgpu::launch_exhaustive(L.plan, d_tasks, d_dev,
+                                    reinterpret_cast<tm_stats*>(L.d_out + out.stats), d_status,
+                                    L.stream));
+    } else if (rc == TM_OK) {
+        int32_t* d_ms = reinterpret_cast<int32_t*>(L.d_out + out.ms);
+        int32_t* d_won = reinterpret_cast<int32_t*>(L.d_out + out.won);
+        int32_t* d_orders = reinterpret_cast<int32_t*>(L.d_out + out.orders);
         if (cfg.beam_width > 0 && ranker) {
-            const int brc = tmgpu::beam_batch(ranker, L.beam, d_tasks, d_off + Ge, h_off + Ge,
-                                              G - Ge, d_dev + Ge, cfg.beam_width, d_orders,
-                                              d_ms + Ge, d_status + Ge, d_won + Ge, L.s_beam);
-            if (brc != TM_OK && rc == TM_OK) rc = brc;
+            const int brc = tmgpu::beam_batch(ranker, L.beam, d_tasks, d_off, h_off, G, d_dev,
+                                              cfg.beam_width, d_orders, d_ms, d_status, d_won,
+                                              L.stream);
+            if (brc != TM_OK) rc = brc;
         } else {
-            ok(tmgpu::launch_heuristic(d_tasks, d_off + Ge, G - Ge, d_dev + Ge, d_orders, d_ms + Ge,
-                                       d_status + Ge, L.s_beam));
-            ok(cudaMemsetAsync(d_won + Ge, 0, (size_t)(G - Ge) * 4, L.s_beam));
+            ok(tmgpu::launch_heuristic(d_tasks, d_off, G, d_dev, d_orders, d_ms, d_status,
+                                       L.stream));
+            ok(cudaMemsetAsync(d_won, 0, (size_t)G * 4, L.stream));
         }
-        ok(cudaEventRecord(L.ev_beam, L.s_beam));
-        ok(cudaStreamWaitEvent(L.s_exact, L.ev_beam, 0));
     }
-    if (rc == TM_OK) ok(cudaMemcpyAsync(L.h_out, L.d_out, out.bytes, cudaMemcpyDeviceToHost, L.s_exact));
-    ok(cudaEventRecord(L.ev_done, L.s_exact));
+    if (rc == TM_OK) ok(cudaMemcpyAsync(L.h_out, L.d_out, out.bytes, cudaMemcpyDeviceToHost, L.stream));
+    ok(cudaEventRecord(L.ev_done, L.stream));
     L.launch_rc = rc;
     return true;
 }
@@ -212,11 +209,11 @@ bool tm_server::try_launch(Lane& L)
 void tm_server::complete(Lane& L)
 {
     const auto now = Clock::now();
-    const int G = (int)L.reqs.size(), Ge = L.Ge;
-    const OutLayout out(G, Ge, L.T);
+    const int G = (int)L.reqs.size();
+    const OutLayout out(L.exact, G, L.T);
     const tm_stats* stats = reinterpret_cast<const tm_stats*>(L.h_out + out.stats);
-    const int32_t* ms = reinterpret_cast<const int32_t*>(L.h_out + out.ms);
     const int32_t* status = reinterpret_cast<const int32_t*>(L.h_out + out.status);
+    const int32_t* ms = reinterpret_cast<const int32_t*>(L.h_out + out.ms);
     const int32_t* won = reinterpret_cast<const int32_t*>(L.h_out + out.won);
     const int32_t* orders = reinterpret_cast<const int32_t*>(L.h_out + out.orders);
     int off = 0;
@@ -230,7 +227,7 @@ void tm_server::complete(Lane& L)
         res.status = L.launch_rc != TM_OK ? L.launch_rc : status[g];
         for (int i = r.n; i < TM_MAX_TASKS; ++i) res.order[i] = -1;
         if (res.status == TM_OK) {
-            if (g < Ge) {
+            if (L.exact) {
                 res.method = TM_METHOD_EXHAUSTIVE;
                 res.makespan = stats[g].best;
                 for (int i = 0; i < r.n; ++i) res.order[i] = stats[g].best_order[i];
@@ -272,7 +269,7 @@ void tm_server::run()
                 progressed = true;
             }
         }
-        if (stop && pending.empty() && !any_busy) break;
+        if (stop && idle() && !any_busy) break;
         if (progressed) continue;
         if (any_busy) {
             // poll the lanes' events; new requests are picked up on the next pass
@@ -280,7 +277,7 @@ void tm_server::run()
             std::this_thread::yield();
             lock.lock();
         } else {
-            cv_work.wait(lock, [&] { return stop || !pending.empty(); });
+            cv_work.wait(lock, [&] { return stop || !idle(); });
         }
     }
 }
@@ -289,10 +286,9 @@ void tm_server::release()
 {
     for (auto& lp : lanes) {
         Lane& L = *lp;
-        if (L.s_exact) cudaStreamSynchronize(L.s_exact);
-        if (L.s_beam) cudaStreamSynchronize(L.s_beam);
-        for (cudaEvent_t e : {L.ev_in, L.ev_beam, L.ev_done}) if (e) cudaEventDestroy(e);
-        for (cudaStream_t s : {L.s_exact, L.s_beam}) if (s) cudaStreamDestroy(s);
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        if (L.ev_done) cudaEventDestroy(L.ev_done);
+        if (L.stream) cudaStreamDestroy(L.stream);
         if (L.h_in) cudaFreeHost(L.h_in);
         if (L.h_out) cudaFreeHost(L.h_out);
         if (L.d_in) cudaFree(L.d_in);
@@ -324,7 +320,7 @@ int tm_server_create(const tm_server_config* config, const tm_ranker* ranker,
     const tm_tuning& t = c.tuning;
     if ((t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize == 1 ||
         t.fuse_finalize < 0 || t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 ||
-        t.item_cost > (1 << 20))
+        t.item_cost > (1 << 20) || t.chunks_per_thread < 0 || t.chunks_per_thread > 64)
         return TM_EINVAL;
     std::unique_ptr<tm_server> s(new (std::nothrow) tm_server());
     if (!s) return TM_ENOMEM;
@@ -336,42 +332,48 @@ int tm_server_create(const tm_server_config* config, const tm_ranker* ranker,
     if (ranker && ranker->device != s->device) return TM_EINVAL;
     const int Gc = c.lane_groups, Tc = c.lane_tasks;
     const InLayout in(Gc, Tc);
-    const OutLayout out(Gc, Gc, Tc);
     int rc = TM_OK;
-    for (int l = 0; l < c.lanes && rc == TM_OK; ++l) {
+    // c.lanes exact lanes (if any group size is solved exactly), then c.lanes
+    // search lanes
+    for (int l = 0; l < 2 * c.lanes && rc == TM_OK; ++l) {
+        const bool exact = l < c.lanes;
+        if (exact && c.exact_max_n == 0) continue;
+        if (!exact && c.exact_max_n == TM_MAX_TASKS) continue;
         s->lanes.emplace_back(new Lane());
         Lane& L = *s->lanes.back();
+        L.exact = exact;
+        const OutLayout out(exact, Gc, Tc);
         auto ok = [&](cudaError_t e) { if (e != cudaSuccess && rc == TM_OK) rc = TM_ENOMEM; };
-        ok(cudaStreamCreateWithFlags(&L.s_exact, cudaStreamNonBlocking));
-        ok(cudaStreamCreateWithFlags(&L.s_beam, cudaStreamNonBlocking));
-        ok(cudaEventCreateWithFlags(&L.ev_in, cudaEventDisableTiming));
-        ok(cudaEventCreateWithFlags(&L.ev_beam, cudaEventDisableTiming));
+        ok(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
         ok(cudaEventCreateWithFlags(&L.ev_done, cudaEventDisableTiming));
         ok(cudaHostAlloc(reinterpret_cast<void**>(&L.h_in), in.bytes, cudaHostAllocDefault));
         ok(cudaHostAlloc(reinterpret_cast<void**>(&L.h_out), out.bytes, cudaHostAllocDefault));
         ok(cudaMalloc(reinterpret_cast<void**>(&L.d_in), in.bytes));
         ok(cudaMalloc(reinterpret_cast<void**>(&L.d_out), out.bytes));
         if (rc != TM_OK) break;
-        // exhaustive-search working memory at the lane's capacity
-        Plan& p = L.plan;
-        p.G = Gc;
-        p.T = Tc;
-        p.total_subs = (uint32_t)c.lane_subsets;
-        const size_t bytes = tmgpu::plan_carve(p, nullptr);
-        ok(cudaMalloc(&L.plan_block, bytes));
-        if (rc != TM_OK) break;
-        tmgpu::plan_carve(p, static_cast<unsigned char*>(L.plan_block));
-        p.d_target = p.d_done = nullptr;   // separate finalize kernel
-        p.device = s->device;
-        // every group's reduction words start (and are left by each
-        // finalize) at min = ~0, max = 0, sum = 0
-        std::vector<unsigned long long> acc((size_t)tmgpu::kAccStride * Gc, 0ull);
-        for (int g = 0; g < Gc; ++g) acc[(size_t)g * tmgpu::kAccStride] = ~0ull;
-        ok(cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
-                      cudaMemcpyHostToDevice));
-        if (c.beam_width > 0)
+        if (exact) {
+            // exhaustive-search working memory at the lane's capacity
+            Plan& p = L.plan;
+            p.G = Gc;
+            p.T = Tc;
+            p.total_subs = (uint32_t)c.lane_subsets;
+            const size_t bytes = tmgpu::plan_carve(p, nullptr);
+            ok(cudaMalloc(&L.plan_block, bytes));
+            if (rc != TM_OK) break;
+            tmgpu::plan_carve(p, static_cast<unsigned char*>(L.plan_block));
+            p.d_target = p.d_done = nullptr;   // separate finalize kernel
+            p.device = s->device;
+            p.chunks_per_thread = t.chunks_per_thread == 0 ? 1 : t.chunks_per_thread;
+            // every group's reduction words start (and are left by each
+            // finalize) at min = ~0, max = 0, sum = 0
+            std::vector<unsigned long long> acc((size_t)tmgpu::kAccStride * Gc, 0ull);
+            for (int g = 0; g < Gc; ++g) acc[(size_t)g * tmgpu::kAccStride] = ~0ull;
+            ok(cudaMemcpy(p.d_acc, acc.data(), acc.size() * sizeof(unsigned long long),
+                          cudaMemcpyHostToDevice));
+        } else if (c.beam_width > 0) {
             for (int nm = c.exact_max_n + 1; nm <= TM_MAX_TASKS && rc == TM_OK; ++nm)
                 if (!L.beam.reserve(Gc, nm, c.beam_width)) rc = TM_ENOMEM;
+        }
     }
     if (rc != TM_OK) {
         s->release();
@@ -397,7 +399,7 @@ int tm_server_submit(tm_server* s, const tm_task* tasks, int n, const tm_device*
         std::lock_guard<std::mutex> lock(s->mu);
         if (s->stop) return TM_EINVAL;
         r.ticket = s->next_ticket++;
-        s->pending.push_back(r);
+        s->enqueue(r);
     }
     s->cv_work.notify_one();
     if (ticket_out) *ticket_out = r.ticket;
@@ -478,7 +480,7 @@ int tm_server_replay(tm_server* s, const tm_task* tasks, const int32_t* offsets,
                 r.dma = devs[g].dma_engines;
                 std::memcpy(r.tasks, tasks + offsets[g], (size_t)r.n * sizeof(tm_task));
                 r.t0 = start + std::chrono::nanoseconds(arrival_ns[g]);   // the scheduled arrival
-                s->pending.push_back(r);
+                s->enqueue(r);
             }
         }
         s->cv_work.notify_one();

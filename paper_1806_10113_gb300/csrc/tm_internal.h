@@ -84,6 +84,14 @@ struct Plan {
     uint32_t threads = 0;         // enumeration threads
     uint64_t leaves_per_thread = 0;
     int launches = 0;
+    // Work distribution of the enumeration: 1 = a static split (thread t
+    // takes cost units [t W, (t + 1) W)); c > 1 = dynamic: c chunks of W / c
+    // units per thread, which warps take in turn from the counter *d_next
+    // (zeroed by the prep kernel), so threads that meet cheap orders take
+    // more work.
+    int chunks_per_thread = 1;
+    uint64_t chunk = 0;                   // cost units per chunk (dynamic)
+    uint32_t nchunks = 0;
     GroupPlan* d_gp = nullptr;            // [G + 1]
     GroupInfo* d_info = nullptr;          // [G]
     int4* d_tbl = nullptr;                // [T] {htd, k, dth, 0}
@@ -95,6 +103,7 @@ struct Plan {
     // (nullptr) a separate finalize kernel runs.
     uint32_t* d_target = nullptr;         // [G]
     uint32_t* d_done = nullptr;           // [kDoneStride G]
+    uint32_t* d_next = nullptr;           // dynamic chunk counter
     cudaEvent_t ev_before = nullptr;      // optional timing hook
     cudaEvent_t ev_after = nullptr;
 };
@@ -166,6 +175,7 @@ inline size_t plan_carve(Plan& p, unsigned char* base)
     p.d_sub = reinterpret_cast<SuffixTab*>(take(S1 * sizeof(SuffixTab)));
     p.d_acc = reinterpret_cast<unsigned long long*>(
         take(kAccStride * G1 * sizeof(unsigned long long)));
+    p.d_next = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t)));
     return off;
 }
 

@@ -261,10 +261,14 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
     plan.close()
 
 
-@pytest.mark.parametrize("tuning", [dict(pdmax=3), dict(pdmax=5), dict(fuse_finalize=1),
-                                    dict(pdmax=5, fuse_finalize=1, blocks_per_sm=2),
+@pytest.mark.parametrize("tuning", [dict(pdmax=3), dict(pdmax=5),
+                                    dict(fuse_finalize=1, chunks_per_thread=1),
+                                    dict(pdmax=5, fuse_finalize=1, blocks_per_sm=2,
+                                         chunks_per_thread=1),
                                     dict(pdmax=3, blocks_per_sm=1), dict(item_cost=1),
-                                    dict(pdmax=4, item_cost=5000)])
+                                    dict(pdmax=4, item_cost=5000), dict(chunks_per_thread=1),
+                                    dict(pdmax=3, chunks_per_thread=64),
+                                    dict(chunks_per_thread=2, item_cost=1, blocks_per_sm=1)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
