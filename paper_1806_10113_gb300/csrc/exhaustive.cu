@@ -226,7 +226,8 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 // i) and writes its GroupInfo and padded task table (and finishes groups of
 // n <= 3 outright); then the block's threads stride over the (4-subset,
 // order) pairs of the group and tabulate alpha / beta / gamma.  When the
-// heuristic is requested, the last warp runs it for the group meanwhile.
+// heuristic is requested, blocks G.. of the same launch run it, one warp per
+// group, beside the table blocks.
 constexpr int kPrepMaxThreads = 512;
 
 struct PrepArgs {
@@ -247,9 +248,20 @@ struct PrepArgs {
 __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
 {
     const int kPrepThreads = blockDim.x;
-    const int g = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GroupPlan* __restrict__ gp = a.gp;
+    if (blockIdx.x >= (unsigned)a.G) {
+        // blocks past the groups run the heuristic, a warp per group, so that
+        // no table block waits for a heuristic warp
+        const int hg = (blockIdx.x - a.G) * (kPrepThreads / 32) + warp;
+        if (hg < a.G) {
+            const int hoff = gp[hg].off;
+            heur::heuristic_group(a.tasks, hoff, gp[hg + 1].off - hoff, a.devs[hg].dma_engines, hg,
+                                  lane, a.orders, a.makespans, nullptr);
+        }
+        return;
+    }
+    const int g = blockIdx.x;
     const int off = gp[g].off;
     const int n = gp[g + 1].off - off;
     const int dma = a.devs[g].dma_engines;
@@ -257,11 +269,6 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
     __shared__ int s_status, s_hs;
 
     if (a.next && g == 0 && tid == 0) *a.next = 0;
-    const bool heur = a.orders != nullptr;
-    if (heur && warp == kPrepThreads / 32 - 1) {
-        heur::heuristic_group(a.tasks, off, n, dma, g, lane, a.orders, a.makespans, nullptr);
-        return;   // this warp takes no part in the barrier below
-    }
     if (warp == 0) {
         const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
         tm_task t = mine ? a.tasks[off + lane] : tm_task{0, 0, 0};
@@ -299,8 +306,8 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
             if (lane == 0 && a.status) a.status[g] = 0;
         }
     }
-    const int workers = heur ? kPrepThreads - 32 : kPrepThreads;
-    asm volatile("bar.sync 1, %0;" ::"r"(workers));   // the warps below only
+    const int workers = kPrepThreads;
+    __syncthreads();
     if (s_status != 0 || n < 4) return;
 
     // beta: the makespan when only the K-engine time (= 0) enters S;
@@ -854,7 +861,9 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.makespans = d_makespans;
     pa.next = (p.chunks_per_thread > 1 && p.total_items > 0) ? p.d_next : nullptr;
     // many (subset, order) pairs per group (n >= 9: >= 3,024): a bigger block
-    prep_kernel<<<p.G, p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128, 0, stream>>>(pa);
+    const int prep_threads = p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128;
+    const int heur_blocks = d_orders ? (p.G + prep_threads / 32 - 1) / (prep_threads / 32) : 0;
+    prep_kernel<<<p.G + heur_blocks, prep_threads, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
