@@ -78,9 +78,15 @@ def _load():
         lib.orc_exhaustive_prefixes.argtypes = [P(OrcTask), P(ctypes.c_int32), P(ctypes.c_int32),
                                                 P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, P(OrcStats)]
+        lib.orc_predict_overlap.argtypes = [P(OrcTask), ctypes.c_int, P(ctypes.c_int32),
+                                            ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                            P(ctypes.c_int64), P(ctypes.c_int64)]
+        lib.orc_exhaustive_overlap.argtypes = [P(OrcTask), ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int32, ctypes.c_int32, P(OrcStats)]
         lib.orc_hardware_threads.argtypes = []
         for f in ("orc_predict", "orc_exhaustive", "orc_exhaustive_batch", "orc_heuristic",
-                  "orc_heuristic_batch", "orc_hardware_threads", "orc_exhaustive_prefixes"):
+                  "orc_heuristic_batch", "orc_hardware_threads", "orc_exhaustive_prefixes",
+                  "orc_predict_overlap", "orc_exhaustive_overlap"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -121,6 +127,37 @@ def predict(tasks, order, dma_engines: int, timeline: bool = False):
     if timeline:
         return int(ms.value), tl.reshape(n, 3, 2)
     return int(ms.value)
+
+
+def predict_overlap(tasks, order, dma_engines: int, rate_num: int, rate_den: int,
+                    timeline: bool = False):
+    """Total time of one order under the partial-overlap variant: concurrent
+    HtD and DtH transfers each run at rate_num / rate_den of full speed, end
+    times re-estimated on every change, rounded up to whole ns (Sec. 4.2.1;
+    parity unpinned by the paper).  Same conventions as `predict`."""
+    t = _tasks(tasks)
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    n = t.shape[0]
+    ms = ctypes.c_int64(0)
+    tl = np.zeros(6 * n, dtype=np.int64)
+    rc = _load().orc_predict_overlap(_ptr(t, OrcTask), n, _ptr(o, ctypes.c_int32),
+                                     int(dma_engines), int(rate_num), int(rate_den),
+                                     ctypes.byref(ms), _ptr(tl, ctypes.c_int64))
+    _check(rc, "predict_overlap")
+    if timeline:
+        return int(ms.value), tl.reshape(n, 3, 2)
+    return int(ms.value)
+
+
+def exhaustive_overlap(tasks, dma_engines: int, rate_num: int, rate_den: int) -> dict:
+    """Best / worst / sum / mean over all n! orders under the partial-overlap
+    variant (n <= 12)."""
+    t = _tasks(tasks)
+    s = OrcStats()
+    rc = _load().orc_exhaustive_overlap(_ptr(t, OrcTask), t.shape[0], int(dma_engines),
+                                        int(rate_num), int(rate_den), ctypes.byref(s))
+    _check(rc, "exhaustive_overlap")
+    return _stats_dict(s, t.shape[0])
 
 
 def _stats_dict(s: OrcStats, n: int) -> dict:

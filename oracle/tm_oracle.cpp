@@ -158,6 +158,93 @@ int64_t simulate(const orc_task* tasks, int n, const int32_t* order,
     return T_sim;
 }
 
+/* The partial-overlap variant (Sec. 4.2.1; reading R1' of the build's design
+ * notes): while an HtD and a DtH transfer run at the same time, each
+ * progresses at the fraction rate_num / rate_den of its full speed, and the
+ * end times of the running transfers are re-estimated whenever that changes
+ * (Sec. 4.1, Fig. 6: "the overlapping degree is calculated and new end times
+ * for both commands are re-calculated").  Time stays on whole nanoseconds: a
+ * transfer of d ns holds d * rate_den units of work, progresses rate_den
+ * units per ns alone and rate_num units per ns overlapped, and ends at the
+ * first whole nanosecond by which its work is done.  Kernels are unaffected.
+ * With one DMA engine no two transfers ever run together.  The queue and
+ * dependency rules are those of simulate() above. */
+int64_t simulate_overlap(const orc_task* tasks, int n, const int32_t* order, int dma_engines,
+                         int64_t rate_num, int64_t rate_den, int64_t* timeline)
+{
+    std::vector<Fifo> fifo(dma_engines == 2 ? 3 : 2);
+    for (int i = 0; i < n; ++i) {
+        const orc_task& t = tasks[order[i]];
+        fifo[0].items.push_back({i, HTD, stage(t, HTD)});
+        if (dma_engines == 2) {
+            fifo[1].items.push_back({i, KER, stage(t, KER)});
+            fifo[2].items.push_back({i, DTH, stage(t, DTH)});
+        }
+    }
+    if (dma_engines == 1) {
+        for (int i = 0; i < n; ++i) fifo[0].items.push_back({i, DTH, stage(tasks[order[i]], DTH)});
+        for (int i = 0; i < n; ++i) fifo[1].items.push_back({i, KER, stage(tasks[order[i]], KER)});
+    }
+    std::vector<char> done(3 * n, 0);
+    std::vector<int64_t> t_start(3 * n, 0), t_end(3 * n, 0);
+    std::vector<int64_t> left(fifo.size(), 0);   /* work left of each running head */
+    int64_t T_sim = 0;
+    for (;;) {
+        for (size_t q = 0; q < fifo.size(); ++q) {
+            Fifo& f = fifo[q];
+            if (f.busy || f.empty()) continue;
+            const Cmd& c = f.front();
+            bool ready = (c.type == HTD) || done[3 * c.pos + (c.type - 1)];
+            if (!ready) continue;
+            f.busy = true;
+            left[q] = c.type == KER ? c.dur : c.dur * rate_den;
+            t_start[3 * c.pos + c.type] = T_sim;
+        }
+        /* how many transfers run now decides their speed */
+        int transfers = 0;
+        for (const Fifo& f : fifo)
+            if (f.busy && f.front().type != KER) ++transfers;
+        auto speed = [&](const Fifo& f) -> int64_t {
+            if (f.front().type == KER) return 1;
+            return transfers >= 2 ? rate_num : rate_den;
+        };
+        /* re-estimate every running command's end from its work left */
+        bool any = false;
+        int64_t next = INT64_MAX;
+        for (size_t q = 0; q < fifo.size(); ++q) {
+            Fifo& f = fifo[q];
+            if (!f.busy) continue;
+            const int64_t v = speed(f);
+            f.end = T_sim + (left[q] + v - 1) / v;
+            any = true;
+            next = std::min(next, f.end);
+        }
+        if (!any) break;
+        for (size_t q = 0; q < fifo.size(); ++q)
+            if (fifo[q].busy) left[q] -= speed(fifo[q]) * (next - T_sim);
+        T_sim = next;
+        for (size_t q = 0; q < fifo.size(); ++q) {
+            Fifo& f = fifo[q];
+            if (!f.busy || f.end != T_sim) continue;
+            const Cmd& c = f.front();
+            done[3 * c.pos + c.type] = 1;
+            t_end[3 * c.pos + c.type] = T_sim;
+            f.head++;
+            f.busy = false;
+        }
+    }
+    for (const Fifo& f : fifo)
+        if (!f.empty()) return -1;
+    if (timeline) {
+        for (int i = 0; i < n; ++i)
+            for (int ty = 0; ty < 3; ++ty) {
+                timeline[6 * i + 2 * ty + 0] = t_start[3 * i + ty];
+                timeline[6 * i + 2 * ty + 1] = t_end[3 * i + ty];
+            }
+    }
+    return T_sim;
+}
+
 uint64_t factorial(int n)
 {
     uint64_t f = 1;
@@ -511,6 +598,59 @@ int orc_heuristic_batch(const orc_task* tasks, const int32_t* offsets, int G,
                   orders_out + offsets[g],
                   makespans_out ? makespans_out + g : nullptr);
     });
+    return 0;
+}
+
+int orc_predict_overlap(const orc_task* tasks, int n, const int32_t* order, int dma_engines,
+                        int32_t rate_num, int32_t rate_den, int64_t* makespan,
+                        int64_t* timeline)
+{
+    if (!tasks || !order || !makespan || n < 1 || n > 64) return -1;
+    if (dma_engines != 1 && dma_engines != 2) return -1;
+    if (rate_num < 1 || rate_den < rate_num) return -1;
+    if (!valid_tasks(tasks, n)) return -1;
+    std::vector<char> seen(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (order[i] < 0 || order[i] >= n || seen[order[i]]) return -1;
+        seen[order[i]] = 1;
+    }
+    int64_t ms = simulate_overlap(tasks, n, order, dma_engines, rate_num, rate_den, timeline);
+    if (ms < 0) return -1;
+    *makespan = ms;
+    return 0;
+}
+
+int orc_exhaustive_overlap(const orc_task* tasks, int n, int dma_engines, int32_t rate_num,
+                           int32_t rate_den, orc_stats* out)
+{
+    if (!tasks || !out || n < 1 || n > 12) return -1;
+    if (dma_engines != 1 && dma_engines != 2) return -1;
+    if (rate_num < 1 || rate_den < rate_num) return -1;
+    if (!valid_tasks(tasks, n)) return -1;
+    std::vector<int32_t> p(n);
+    std::iota(p.begin(), p.end(), 0);
+    int64_t best = INT64_MAX, worst = INT64_MIN, sum = 0;
+    uint64_t rank = 0, best_rank = 0, worst_rank = 0;
+    std::vector<int32_t> best_order, worst_order;
+    do {
+        const int64_t ms = simulate_overlap(tasks, n, p.data(), dma_engines, rate_num, rate_den,
+                                            nullptr);
+        if (ms < 0) return -1;
+        sum += ms;
+        if (ms < best) { best = ms; best_rank = rank; best_order = p; }
+        if (ms > worst) { worst = ms; worst_rank = rank; worst_order = p; }
+        ++rank;
+    } while (std::next_permutation(p.begin(), p.end()));
+    out->best = best;
+    out->worst = worst;
+    out->sum = sum;
+    out->mean = (double)sum / (double)factorial(n);
+    out->best_rank = best_rank;
+    out->worst_rank = worst_rank;
+    for (int i = 0; i < 16; ++i) {
+        out->best_order[i] = i < n ? best_order[i] : -1;
+        out->worst_order[i] = i < n ? worst_order[i] : -1;
+    }
     return 0;
 }
 

@@ -79,6 +79,19 @@ int orc_heuristic_batch(const orc_task* tasks, const int32_t* offsets, int G,
                         int32_t* orders_out, int64_t* makespans_out);
 
 /* Number of hardware threads the batch calls use when nthreads <= 0. */
+/* The partial-overlap variant of the model (Sec. 4.2.1; no formula in the
+ * paper, so PARITY UNPINNED beyond the properties its tests check): an HtD
+ * and a DtH transfer running together each progress at rate_num / rate_den
+ * of full speed (1 <= rate_num <= rate_den); running transfers' end times
+ * are re-estimated whenever that changes; ends are rounded up to whole ns.
+ * rate_num == rate_den is the ideal model.  Same arguments otherwise as
+ * orc_predict / orc_exhaustive (n <= 12). */
+int orc_predict_overlap(const orc_task* tasks, int n, const int32_t* order,
+                        int dma_engines, int32_t rate_num, int32_t rate_den,
+                        int64_t* makespan, int64_t* timeline);
+int orc_exhaustive_overlap(const orc_task* tasks, int n, int dma_engines,
+                           int32_t rate_num, int32_t rate_den, orc_stats* out);
+
 int orc_hardware_threads(void);
 
 #ifdef __cplusplus
