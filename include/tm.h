@@ -275,6 +275,49 @@ int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t* h_offsets
                                 int G, const tm_device* d_devs, tm_stats* d_stats,
                                 int32_t* d_status /* may be NULL */, void* stream);
 
+/* ---- partial-overlap variant of the model --------------------------------- */
+
+/* The paper's simulator also slows down an HtD and a DtH transfer that run
+ * at the same time on two DMA engines, re-estimating both end times whenever
+ * such an overlap starts or ends (Sec. 4.1, Fig. 6; Sec. 4.2.1); it gives no
+ * formula.  Here the slowdown is a fixed rate: while both transfers run,
+ * each progresses at rate_num / rate_den of its full speed
+ * (1 <= rate_num <= rate_den <= 1024; rate_num == rate_den is the plain
+ * model).  Time stays on whole nanoseconds: a transfer of d ns is
+ * d * rate_den units of work, moving rate_den units per ns alone and
+ * rate_num overlapped, and ends at the first whole ns by which its work is
+ * done.  Kernels never slow down; with one DMA engine transfers never
+ * overlap, so such groups get the plain model.  Every time the model can
+ * reach stays below the sum of the kernels and of the transfers stretched by
+ * rate_den / rate_num (rounded up); a group where that sum passes INT32_MAX
+ * is rejected with TM_EOVERFLOW.  Arguments otherwise as the plain forms. */
+int tm_predict_overlap(const tm_task* tasks, int n, const int32_t* order,
+                       const tm_device* dev, int32_t rate_num, int32_t rate_den,
+                       int32_t* makespan);
+int tm_predict_overlap_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                             const int32_t* orders, const tm_device* devs,
+                             int32_t rate_num, int32_t rate_den, int32_t* makespans);
+int tm_predict_overlap_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                                 int G, const int32_t* d_orders,
+                                 const tm_device* d_devs, int32_t rate_num,
+                                 int32_t rate_den, int32_t* d_makespans,
+                                 int32_t* d_status /* may be NULL */, void* stream);
+
+/* Exhaustive search under the partial-overlap rule (n <= 12): every order is
+ * simulated (the max-plus shortcut of the plain search does not apply), a
+ * thread walking consecutive ranks.  Same tm_stats as tm_exhaustive_batch.
+ * The _dev form takes the HOST copy of the offsets too, and uses working
+ * memory owned by the library per host thread: calls from one host thread
+ * must not overlap on the GPU (use one stream). */
+int tm_exhaustive_overlap_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                                const tm_device* devs, int32_t rate_num,
+                                int32_t rate_den, tm_stats* stats);
+int tm_exhaustive_overlap_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                                    const int32_t* h_offsets, int G,
+                                    const tm_device* d_devs, int32_t rate_num,
+                                    int32_t rate_den, tm_stats* d_stats,
+                                    int32_t* d_status /* may be NULL */, void* stream);
+
 /* ---- learned order ranker and beam search --------------------------------- */
 
 /* The paper has no learned component and no search beyond its O(n^2)

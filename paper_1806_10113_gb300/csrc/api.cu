@@ -49,6 +49,21 @@ int check_batch(const tm_task* tasks, const int32_t* offsets, int G, const tm_de
     return TM_OK;
 }
 
+// Every time of the partial-overlap loop stays below the sum of kernels and
+// of transfers stretched by den / num (rounded up).
+int check_overlap(const tm_task* tasks, const int32_t* offsets, int G, int32_t num, int32_t den)
+{
+    if (!tmgpu::overlap_rate_ok(num, den)) return TM_EINVAL;
+    for (int g = 0; g < G; ++g) {
+        int64_t bound = 0;
+        for (int i = offsets[g]; i < offsets[g + 1]; ++i)
+            bound += tasks[i].k + ((int64_t)tasks[i].htd * den + num - 1) / num +
+                     ((int64_t)tasks[i].dth * den + num - 1) / num;
+        if (bound > INT32_MAX) return TM_EOVERFLOW;
+    }
+    return TM_OK;
+}
+
 int check_orders(const int32_t* orders, const int32_t* offsets, int G)
 {
     if (G > 0 && !orders) return TM_EINVAL;
@@ -591,6 +606,114 @@ int tm_heuristic(const tm_task* tasks, int n, const tm_device* dev, int32_t* ord
     if (n < 1 || n > TM_MAX_TASKS) return TM_EINVAL;
     int32_t offsets[2] = {0, n};
     return tm_heuristic_batch(tasks, offsets, 1, dev, order_out, makespan_out);
+}
+
+// ---- partial-overlap variant ---------------------------------------------------
+
+int tm_predict_overlap_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                             const int32_t* orders, const tm_device* devs, int32_t rate_num,
+                             int32_t rate_den, int32_t* makespans)
+{
+    int rc = check_batch(tasks, offsets, G, devs, TM_MAX_TASKS);
+    if (rc == TM_OK) rc = check_orders(orders, offsets, G);
+    if (rc == TM_OK) rc = check_overlap(tasks, offsets, G, rate_num, rate_den);
+    if (rc != TM_OK) return rc;
+    if (G == 0) return TM_OK;
+    if (!makespans) return TM_EINVAL;
+    Context* c = nullptr;
+    if ((rc = context(&c)) != TM_OK) return rc;
+    const int T = offsets[G];
+    cudaStream_t s = c->stream;
+    if ((rc = copy_in(c->tasks, tasks, T * sizeof(tm_task), s)) != TM_OK) return rc;
+    if ((rc = copy_in(c->offsets, offsets, (G + 1) * sizeof(int32_t), s)) != TM_OK) return rc;
+    if ((rc = copy_in(c->orders, orders, T * sizeof(int32_t), s)) != TM_OK) return rc;
+    if ((rc = copy_in(c->devs, devs, G * sizeof(tm_device), s)) != TM_OK) return rc;
+    if (!c->out.ensure(G * sizeof(int32_t)) || !c->status.ensure(G * sizeof(int32_t)))
+        return TM_ENOMEM;
+    TM_CUDA(tmgpu::launch_overlap_predict(c->tasks.as<tm_task>(), c->offsets.as<int32_t>(), G,
+                                          c->orders.as<int32_t>(), c->devs.as<tm_device>(),
+                                          rate_num, rate_den, c->out.as<int32_t>(),
+                                          c->status.as<int32_t>(), s));
+    std::vector<int32_t> out(G), status(G);
+    TM_CUDA(cudaMemcpyAsync(out.data(), c->out.p, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TM_CUDA(cudaMemcpyAsync(status.data(), c->status.p, G * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    TM_CUDA(cudaStreamSynchronize(s));
+    if ((rc = first_error(status.data(), G)) != TM_OK) return rc;
+    std::memcpy(makespans, out.data(), G * sizeof(int32_t));
+    return TM_OK;
+}
+
+int tm_predict_overlap(const tm_task* tasks, int n, const int32_t* order, const tm_device* dev,
+                       int32_t rate_num, int32_t rate_den, int32_t* makespan)
+{
+    if (n < 1 || n > TM_MAX_TASKS) return TM_EINVAL;
+    int32_t offsets[2] = {0, n};
+    return tm_predict_overlap_batch(tasks, offsets, 1, order, dev, rate_num, rate_den, makespan);
+}
+
+int tm_predict_overlap_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets, int G,
+                                 const int32_t* d_orders, const tm_device* d_devs,
+                                 int32_t rate_num, int32_t rate_den, int32_t* d_makespans,
+                                 int32_t* d_status, void* stream)
+{
+    if (G < 0 || !tmgpu::overlap_rate_ok(rate_num, rate_den)) return TM_EINVAL;
+    if (G > 0 && (!d_tasks || !d_offsets || !d_orders || !d_devs || !d_makespans)) return TM_EINVAL;
+    cudaError_t e = tmgpu::launch_overlap_predict(d_tasks, d_offsets, G, d_orders, d_devs, rate_num,
+                                                  rate_den, d_makespans, d_status,
+                                                  (cudaStream_t)stream);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_exhaustive_overlap_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                                    const int32_t* h_offsets, int G, const tm_device* d_devs,
+                                    int32_t rate_num, int32_t rate_den, tm_stats* d_stats,
+                                    int32_t* d_status, void* stream)
+{
+    if (G < 0 || !tmgpu::overlap_rate_ok(rate_num, rate_den)) return TM_EINVAL;
+    if (G == 0) return TM_OK;
+    if (!d_tasks || !d_offsets || !h_offsets || !d_devs || !d_stats) return TM_EINVAL;
+    if (h_offsets[0] != 0) return TM_EINVAL;
+    for (int g = 0; g < G; ++g) {
+        const int n = h_offsets[g + 1] - h_offsets[g];
+        if (n < 1) return TM_EINVAL;
+        if (n > TM_MAX_EXHAUSTIVE) return TM_ETOOBIG;
+    }
+    return tmgpu::overlap_exhaustive(d_tasks, d_offsets, h_offsets, G, d_devs, rate_num, rate_den,
+                                     d_stats, d_status, (cudaStream_t)stream);
+}
+
+int tm_exhaustive_overlap_batch(const tm_task* tasks, const int32_t* offsets, int G,
+                                const tm_device* devs, int32_t rate_num, int32_t rate_den,
+                                tm_stats* stats)
+{
+    int rc = check_batch(tasks, offsets, G, devs, TM_MAX_EXHAUSTIVE);
+    if (rc == TM_OK) rc = check_overlap(tasks, offsets, G, rate_num, rate_den);
+    if (rc != TM_OK) return rc;
+    if (G == 0) return TM_OK;
+    if (!stats) return TM_EINVAL;
+    Context* c = nullptr;
+    if ((rc = context(&c)) != TM_OK) return rc;
+    const int T = offsets[G];
+    cudaStream_t s = c->stream;
+    if ((rc = copy_in(c->tasks, tasks, T * sizeof(tm_task), s)) != TM_OK) return rc;
+    if ((rc = copy_in(c->offsets, offsets, (G + 1) * sizeof(int32_t), s)) != TM_OK) return rc;
+    if ((rc = copy_in(c->devs, devs, G * sizeof(tm_device), s)) != TM_OK) return rc;
+    if (!c->stats.ensure(G * sizeof(tm_stats)) || !c->status.ensure(G * sizeof(int32_t)))
+        return TM_ENOMEM;
+    rc = tmgpu::overlap_exhaustive(c->tasks.as<tm_task>(), c->offsets.as<int32_t>(), offsets, G,
+                                   c->devs.as<tm_device>(), rate_num, rate_den,
+                                   c->stats.as<tm_stats>(), c->status.as<int32_t>(), s);
+    if (rc != TM_OK) return rc;
+    std::vector<tm_stats> out(G);
+    std::vector<int32_t> status(G);
+    TM_CUDA(cudaMemcpyAsync(out.data(), c->stats.p, G * sizeof(tm_stats), cudaMemcpyDeviceToHost, s));
+    TM_CUDA(cudaMemcpyAsync(status.data(), c->status.p, G * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    TM_CUDA(cudaStreamSynchronize(s));
+    if ((rc = first_error(status.data(), G)) != TM_OK) return rc;
+    std::memcpy(stats, out.data(), G * sizeof(tm_stats));
+    return TM_OK;
 }
 
 }  // extern "C"

@@ -230,6 +230,15 @@ cudaError_t launch_predict(const tm_task* d_tasks, const int32_t* d_offsets,
                            const tm_device* d_devs, int32_t* d_makespans,
                            int32_t* d_status, cudaStream_t stream);
 
+// Partial-overlap variant (overlap.cu).  rate: 1 <= num <= den <= 1024.
+int overlap_rate_ok(int32_t num, int32_t den);
+cudaError_t launch_overlap_predict(const tm_task* d_tasks, const int32_t* d_offsets, int G,
+                                   const int32_t* d_orders, const tm_device* d_devs, int32_t num,
+                                   int32_t den, int32_t* d_makespans, int32_t* d_status,
+                                   cudaStream_t s);
+int overlap_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int32_t* h_offsets,
+                       int G, const tm_device* d_devs, int32_t num, int32_t den, tm_stats* d_stats,
+                       int32_t* d_status, cudaStream_t s);
 cudaError_t launch_heuristic(const tm_task* d_tasks, const int32_t* d_offsets,
                              int G, const tm_device* d_devs,
                              int32_t* d_orders, int32_t* d_makespans,

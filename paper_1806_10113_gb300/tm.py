@@ -99,6 +99,12 @@ _SIGS = {
     "tm_server_counters": [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int64)],
     "tm_server_destroy": [_vp],
+    "tm_predict_overlap": [_vp, ctypes.c_int, _vp, _vp, _i32, _i32, _vp],
+    "tm_predict_overlap_batch": [_vp, _vp, ctypes.c_int, _vp, _vp, _i32, _i32, _vp],
+    "tm_predict_overlap_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _i32, _i32, _vp, _vp, _vp],
+    "tm_exhaustive_overlap_batch": [_vp, _vp, ctypes.c_int, _vp, _i32, _i32, _vp],
+    "tm_exhaustive_overlap_batch_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _i32, _i32, _vp, _vp,
+                                        _vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
@@ -555,3 +561,59 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- partial-overlap variant ------------------------------------------------------
+
+def tm_predict_overlap(tasks, order, dma_engines: int, rate_num: int, rate_den: int) -> int:
+    """Makespan of one order when concurrent HtD and DtH transfers each run at
+    rate_num / rate_den of full speed (see include/tm.h)."""
+    t = _tasks(tasks)
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    out = np.zeros(1, dtype=np.int32)
+    _check(lib().tm_predict_overlap(_p(t), t.shape[0], _p(o), _p(dev), int(rate_num),
+                                    int(rate_den), _p(out)), "tm_predict_overlap")
+    return int(out[0])
+
+
+def tm_predict_overlap_batch(tasks, offsets, orders, dma, rate_num: int, rate_den: int):
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(-1))
+    dev = _devs(dma, G)
+    out = np.zeros(max(G, 1), dtype=np.int32)
+    _check(lib().tm_predict_overlap_batch(_p(t), _p(off), G, _p(o), _p(dev), int(rate_num),
+                                          int(rate_den), _p(out)), "tm_predict_overlap_batch")
+    return out[:G]
+
+
+def tm_predict_overlap_batch_dev(d_tasks, d_offsets, G: int, d_orders, d_devs, rate_num: int,
+                                 rate_den: int, d_makespans, d_status=None, stream=None):
+    _check(lib().tm_predict_overlap_batch_dev(_dptr(d_tasks), _dptr(d_offsets), int(G),
+                                              _dptr(d_orders), _dptr(d_devs), int(rate_num),
+                                              int(rate_den), _dptr(d_makespans), _dptr(d_status),
+                                              _stream(stream)), "tm_predict_overlap_batch_dev")
+
+
+def tm_exhaustive_overlap_batch(tasks, offsets, dma, rate_num: int, rate_den: int) -> np.ndarray:
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    dev = _devs(dma, G)
+    st = np.zeros(max(G, 1), dtype=STATS_DTYPE)
+    _check(lib().tm_exhaustive_overlap_batch(_p(t), _p(off), G, _p(dev), int(rate_num),
+                                             int(rate_den), _p(st)), "tm_exhaustive_overlap_batch")
+    return st[:G]
+
+
+def tm_exhaustive_overlap_batch_dev(d_tasks, d_offsets, offsets, d_devs, rate_num: int,
+                                    rate_den: int, d_stats, d_status=None, stream=None):
+    """``offsets`` is the HOST copy of d_offsets."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    _check(lib().tm_exhaustive_overlap_batch_dev(_dptr(d_tasks), _dptr(d_offsets), _p(off),
+                                                 off.shape[0] - 1, _dptr(d_devs), int(rate_num),
+                                                 int(rate_den), _dptr(d_stats), _dptr(d_status),
+                                                 _stream(stream)),
+           "tm_exhaustive_overlap_batch_dev")

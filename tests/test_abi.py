@@ -127,3 +127,19 @@ def test_server_config_rejected_on_host(tm):
 def test_result_layout(tm):
     assert tm.RESULT_DTYPE.itemsize == 96
     assert tm.RESULT_DTYPE.fields["order"][1] == 32
+
+
+def test_overlap_rate_and_bound_rejected_on_host(tm):
+    t = [[1, 2, 3], [4, 5, 6]]
+    for num, den in ((0, 1), (3, 2), (1, 1025), (-1, 4)):
+        with pytest.raises(tm.TMError) as e:
+            tm.tm_predict_overlap(t, [0, 1], 2, num, den)
+        assert e.value.code == -1, (num, den)
+    # transfers stretched 4x pass INT32_MAX although the plain sum does not
+    big = [[2**28, 1, 2**28], [2**28, 1, 2**28]]
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_predict_overlap(big, [0, 1], 2, 1, 4)
+    assert e.value.code == -3
+    with pytest.raises(tm.TMError) as e:
+        tm.tm_exhaustive_overlap_batch(big, [0, 2], [2], 1, 4)
+    assert e.value.code == -3
