@@ -587,7 +587,7 @@ def run_beam12(args):
                 "h2d_bytes_per_step": int(test.tasks.nbytes + test.offsets.nbytes + test.dma.nbytes),
                 "d2h_bytes_per_step": int(4 * T + 4 * G)},
         "gpu_launches": 2 + 12 * 3 + 1,
-        "roofline": {"bound": "tensor", "kernel": "forward_kernel (ranker MLP, WMMA bf16)",
+        "roofline": {"bound": "tensor", "kernel": "forward_tc_kernel (ranker MLP, tcgen05 bf16, TMEM accumulator)",
                      "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": tflops / peak, "traffic": None,
                      "basis": f"{FLOPS_PER_RANKER_ROW} FLOP per row, {chunk} rows per launch, "

@@ -359,6 +359,12 @@ void tm_ranker_destroy(tm_ranker* ranker);
 int tm_ranker_get_params(const tm_ranker* ranker, float* h_params);
 int tm_ranker_set_params(tm_ranker* ranker, const float* h_params);
 
+/* Scoring (tm_ranker_forward_dev, the beam search) runs on the tcgen05
+ * tensor cores; every wait inside that kernel is bounded.  *count receives 1
+ * if such a wait has ever expired for this ranker (the affected scores are
+ * NaN), else 0.  Synchronous. */
+int tm_ranker_errors(const tm_ranker* ranker, int32_t* count);
+
 /* Training rows of a batch (host offsets): a group of n >= 2 tasks has
  * n - 1 states (positions p = 0 .. n - 2) with n - p candidate rows each,
  * n (n + 1) / 2 - 1 rows in all; n = 1 has none.  TM_EINVAL for bad

@@ -38,11 +38,12 @@ inline int32_t group_states(int n) { return n < 2 ? 0 : n - 1; }
 
 namespace {
 
+// Blocks of the tensor-core forward pass: one per SM (four 128-row tiles in
+// flight each).
 int forward_blocks(const tm_ranker* r, int64_t M)
 {
-    const int64_t slabs = (M + 15) / 16;
-    const int64_t want = (slabs + 7) / 8;   // 8 warps per block, one slab per warp
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * r->sms));   // 2 blocks per SM
+    const int64_t tiles = (M + 127) / 128;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, r->sms));
 }
 
 int on_device(const tm_ranker* r)
@@ -97,8 +98,8 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
             e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R, pos,
                               sc.bx.as<bf16_raw>(), s);
             if (e == cudaSuccess)
-                e = ranker_forward(sc.bx.as<bf16_raw>(), rows, r->Wb, r->P, sc.blog.as<float>(),
-                                   nullptr, 0, forward_blocks(r, rows), s);
+                e = ranker_forward_tc(sc.bx.as<bf16_raw>(), rows, r->Wimg, sc.blog.as<float>(),
+                                      r->d_err, forward_blocks(r, rows), s);
             if (e == cudaSuccess)
                 e = beam_select(off, d_tasks, sc.blog.as<float>(), cur, nxt, gc, B, R, pos, s);
             std::swap(cur, nxt);
@@ -123,7 +124,7 @@ int tm_ranker_create(uint64_t seed, tm_ranker** out)
     if (!r) return TM_ENOMEM;
     if (cudaGetDevice(&r->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess ||
-        tmgpu::ranker_configure() != cudaSuccess) {
+        tmgpu::ranker_configure() != cudaSuccess || tmgpu::ranker_tc_configure() != cudaSuccess) {
         delete r;
         return TM_ECUDA;
     }
@@ -131,6 +132,8 @@ int tm_ranker_create(uint64_t seed, tm_ranker** out)
     if (cudaMalloc(&r->P, pb) != cudaSuccess || cudaMalloc(&r->Mom, pb) != cudaSuccess ||
         cudaMalloc(&r->Vel, pb) != cudaSuccess || cudaMalloc(&r->G, pb) != cudaSuccess ||
         cudaMalloc(&r->loss, sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&r->Wimg, tmgpu::ranker_image_bytes()) != cudaSuccess ||
+        cudaMalloc(&r->d_err, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&r->Wb, tmgpu::kRankBf16 * sizeof(tmgpu::bf16_raw)) != cudaSuccess) {
         r->release();
         delete r;
@@ -139,7 +142,9 @@ int tm_ranker_create(uint64_t seed, tm_ranker** out)
     cudaError_t e = cudaMemset(r->Mom, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(r->Vel, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(r->G, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(r->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = tmgpu::ranker_init(r->P, r->Wb, seed, nullptr);
+    if (e == cudaSuccess) e = tmgpu::ranker_image(r->P, r->Wb, r->Wimg, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         r->release();
@@ -177,9 +182,22 @@ int tm_ranker_set_params(tm_ranker* r, const float* h_params)
     if (e == cudaSuccess) e = cudaMemset(r->Mom, 0, pb);
     if (e == cudaSuccess) e = cudaMemset(r->Vel, 0, pb);
     if (e == cudaSuccess) e = tmgpu::ranker_refresh(r->P, r->Wb, nullptr);
+    if (e == cudaSuccess) e = tmgpu::ranker_image(r->P, r->Wb, r->Wimg, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     r->adam_step = 0;
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_ranker_errors(const tm_ranker* r, int32_t* count)
+{
+    if (!r || !count) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&v, r->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TM_ECUDA;
+    *count = v;
+    return TM_OK;
 }
 
 int tm_ranker_rows_count(const int32_t* h_offsets, int G, int64_t* rows, int32_t* states)
@@ -225,8 +243,8 @@ int tm_ranker_forward_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows, float
     if (reinterpret_cast<uintptr_t>(d_X) % 16) return TM_EINVAL;   // rows are read 16 bytes at a time
     if (int rc = on_device(r)) return rc;
     if (rows == 0) return TM_OK;
-    cudaError_t e = tmgpu::ranker_forward(d_X, rows, r->Wb, r->P, d_logits, nullptr, 0,
-                                          forward_blocks(r, rows), (cudaStream_t)stream);
+    cudaError_t e = tmgpu::ranker_forward_tc(d_X, rows, r->Wimg, d_logits, r->d_err,
+                                             forward_blocks(r, rows), (cudaStream_t)stream);
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
@@ -270,6 +288,7 @@ int tm_ranker_adam_dev(tm_ranker* r, float lr, void* stream)
     r->adam_step += 1;
     cudaError_t e = tmgpu::ranker_adam(r->P, r->Mom, r->Vel, r->G, r->Wb, lr, r->adam_step,
                                        (cudaStream_t)stream);
+    if (e == cudaSuccess) e = tmgpu::ranker_image(r->P, r->Wb, r->Wimg, (cudaStream_t)stream);
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 

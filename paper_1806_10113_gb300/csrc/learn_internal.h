@@ -65,12 +65,15 @@ struct tm_ranker {
     float* Vel = nullptr;
     float* G = nullptr;              // gradient of the last tm_ranker_grad_dev
     float* loss = nullptr;
+    unsigned char* Wimg = nullptr;   // weight image of the tensor-core forward pass
+    int* d_err = nullptr;            // set by a forward pass whose bounded wait expired
     int adam_step = 0;
     tmgpu::Grow scan_rows, scan_states, logits, dlogit, act;   // training
     tmgpu::BeamScratch beam;                                    // tm_beam_batch_dev
     void release()
     {
-        for (void* q : {(void*)P, (void*)Wb, (void*)Mom, (void*)Vel, (void*)G, (void*)loss})
+        for (void* q : {(void*)P, (void*)Wb, (void*)Mom, (void*)Vel, (void*)G, (void*)loss,
+                        (void*)Wimg, (void*)d_err})
             if (q) cudaFree(q);
         for (tmgpu::Grow* b : {&scan_rows, &scan_states, &logits, &dlogit, &act}) b->release();
         beam.release();

@@ -58,4 +58,14 @@ cudaError_t ranker_backward(const bf16_raw* X, int64_t M, const int32_t* off,
 cudaError_t ranker_adam(float* P, float* Mom, float* Vel, const float* G, bf16_raw* Wb, float lr,
                         int step, cudaStream_t s);
 
+// ranker_tc.cu: the inference forward pass on tcgen05 tensor cores.  It
+// reads a weight image (ranker_image_bytes()) that ranker_image builds from
+// the parameters; rebuild it after every parameter change.  *err is set to 1
+// if a bounded wait of the kernel expired (its scores are then NaN).
+size_t ranker_image_bytes();
+cudaError_t ranker_image(const float* P, const bf16_raw* Wb, unsigned char* img, cudaStream_t s);
+cudaError_t ranker_tc_configure();
+cudaError_t ranker_forward_tc(const bf16_raw* X, int64_t M, const unsigned char* img,
+                              float* logits, int* err, int blocks, cudaStream_t s);
+
 }  // namespace tmgpu

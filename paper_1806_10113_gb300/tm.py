@@ -83,6 +83,7 @@ _SIGS = {
     "tm_ranker_destroy": [_vp],
     "tm_ranker_get_params": [_vp, _vp],
     "tm_ranker_set_params": [_vp, _vp],
+    "tm_ranker_errors": [_vp, ctypes.POINTER(ctypes.c_int32)],
     "tm_ranker_rows_count": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int32)],
     "tm_ranker_rows_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64,
@@ -433,6 +434,12 @@ class Ranker:
         if a.shape[0] != TM_RANKER_PARAMS:
             raise ValueError(f"expected {TM_RANKER_PARAMS} parameters, got {a.shape[0]}")
         _check(lib().tm_ranker_set_params(self._h, _p(a)), "tm_ranker_set_params")
+
+    def errors(self) -> int:
+        """1 if a bounded wait of the tensor-core scoring kernel ever expired."""
+        c = ctypes.c_int32(0)
+        _check(lib().tm_ranker_errors(self._h, ctypes.byref(c)), "tm_ranker_errors")
+        return int(c.value)
 
     def rows_dev(self, d_tasks, d_offsets, G: int, d_devs, rows: int, states: int, d_X,
                  d_state_off, d_target, d_orders=None, d_stats=None, d_status=None,

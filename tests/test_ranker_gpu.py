@@ -140,6 +140,27 @@ def test_forward_matches_oracle():
     assert np.median(err) <= 1e-3 * (np.abs(ref).max() + 1.0)
 
 
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 4101, 300_000])
+def test_forward_tile_edges_and_many_tiles(M):
+    # the tensor-core kernel works in 128-row tiles, several per CTA for large M
+    rng = np.random.default_rng(M)
+    theta = random_params(12).astype(np.float32)
+    r = tm.Ranker(seed=2)
+    r.set_params(theta)
+    xb = rng.normal(0, 1, (M, F)).astype(np.float32)
+    bits = float_to_bf16_bits(xb)
+    logits = torch.full((M,), float("nan"), dtype=torch.float32, device="cuda")
+    r.forward_dev(cuda(bits), M, logits)
+    torch.cuda.synchronize()
+    got = logits.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all() and r.errors() == 0
+    idx = np.unique(np.concatenate([np.arange(min(M, 300)), rng.integers(0, M, 1500),
+                                    np.arange(max(0, M - 130), M)]))
+    ref, _ = mlp.forward(theta.astype(np.float64), bf16_bits_to_float(bits[idx]), bf16=True)
+    err = np.abs(got[idx] - ref)
+    assert err.max() <= 1e-2 * (np.abs(ref).max() + 1.0), err.max()
+
+
 def test_get_params_roundtrip_and_init():
     r = tm.Ranker(seed=7)
     p = r.get_params()
