@@ -273,18 +273,28 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
     const bool leader = row == 0;                           // issues the group's MMAs
     int64_t tile = (int64_t)blockIdx.x * kGroups + grp;
     const int64_t step = (int64_t)gridDim.x * kGroups;
-    for (; ok && tile < tiles; tile += step) {
-        const int64_t r0 = tile * kTile;
-        // features of this thread's row -> activation tile (K = 32 layout)
-        uint4 v[4] = {};
-        if (r0 + row < M) {
-            const uint4* src = reinterpret_cast<const uint4*>(X + (size_t)(r0 + row) * kF);
+    // this thread's row of features: loaded one tile ahead, so that the
+    // global-memory latency hides behind the current tile's layers
+    auto load_row = [&](int64_t t, uint4 (&v)[4]) {
+        const int64_t r = t * kTile + row;
+        if (t < tiles && r < M) {
+            const uint4* src = reinterpret_cast<const uint4*>(X + (size_t)r * kF);
 #pragma unroll
             for (int q = 0; q < 4; ++q) v[q] = src[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = make_uint4(0, 0, 0, 0);
         }
+    };
+    uint4 v[4];
+    load_row(tile, v);
+    for (; ok && tile < tiles; tile += step) {
+        const int64_t r0 = tile * kTile;
+        // features -> activation tile (K = 32 layout)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(act_p + core_off(row, 8 * q, kF)) = v[q];
+        load_row(tile + step, v);
         fence_async_smem();
         tc_fence_before();
         wg_sync(grp);
@@ -308,12 +318,18 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                 uint32_t r[32];
                 tc_ld32(t_row + (uint32_t)(32 * c), r);
                 tc_wait_ld();
+                float bv[32];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 b4v = reinterpret_cast<const float4*>(bias + 32 * c)[q];
+                    bv[4 * q] = b4v.x; bv[4 * q + 1] = b4v.y; bv[4 * q + 2] = b4v.z; bv[4 * q + 3] = b4v.w;
+                }
                 if (layer < 2) {
                     uint32_t packed[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float lo = fmaxf(__uint_as_float(r[2 * j]) + bias[32 * c + 2 * j], 0.0f);
-                        const float hi = fmaxf(__uint_as_float(r[2 * j + 1]) + bias[32 * c + 2 * j + 1], 0.0f);
+                        const float lo = fmaxf(__uint_as_float(r[2 * j]) + bv[2 * j], 0.0f);
+                        const float hi = fmaxf(__uint_as_float(r[2 * j + 1]) + bv[2 * j + 1], 0.0f);
                         const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
                         packed[j] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
@@ -325,9 +341,15 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                                        packed[4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float h = fmaxf(__uint_as_float(r[j]) + bias[32 * c + j], 0.0f);
-                        logit += __bfloat162float(__float2bfloat16_rn(h)) * w4[32 * c + j];
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 wq = reinterpret_cast<const float4*>(w4 + 32 * c)[q];
+                        const float wv[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = 4 * q + e;
+                            const float h = fmaxf(__uint_as_float(r[j]) + bv[j], 0.0f);
+                            logit += __bfloat162float(__float2bfloat16_rn(h)) * wv[e];
+                        }
                     }
                 }
             }
