@@ -13,8 +13,8 @@
 // the features of "append the slot-th unused task", R = nmax - i.  The
 // ranker scores the rows; a block per group turns scores into log-softmax
 // over each beam's candidates, adds the beam's log-probability, keeps the
-// best B candidates (bitonic sort in shared memory; ties: lower beam, then
-// lower slot) and applies them.
+// best B candidates (bitonic sort in shared memory of the B x R keys; ties:
+// lower beam, then lower slot) and applies them.
 #include <cuda_bf16.h>
 
 #include "rank_features.cuh"
@@ -94,9 +94,16 @@ __global__ void beam_features_kernel(const int32_t* __restrict__ offsets,
     } else {
         for (int q = 0; q < kFeat; ++q) f[q] = 0.0f;
     }
-    __nv_bfloat16* x = X + row * kFeat;
+    // one 64-byte row: four 16-byte stores
+    uint32_t w[kFeat / 2];
 #pragma unroll
-    for (int q = 0; q < kFeat; ++q) x[q] = __float2bfloat16_rn(f[q]);
+    for (int q = 0; q < kFeat / 2; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    uint4* x = reinterpret_cast<uint4*>(X + row * kFeat);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
 __device__ __forceinline__ uint32_t orderable(float v)
@@ -120,8 +127,8 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
     __shared__ float lse[64];
     __shared__ unsigned long long key[kMaxCand];
     const int cands = n - pos;
-    int nk = 16;
-    while (nk < B * 16) nk <<= 1;   // keys sorted: a power of two >= B * 16
+    int nk = 32;
+    while (nk < B * R) nk <<= 1;    // keys sorted: a power of two >= B * R
     // log-sum-exp of each live beam's candidate logits
     for (int b = tid; b < B; b += blockDim.x) {
         const BeamState s = cur[(size_t)g * B + b];
@@ -135,7 +142,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
     }
     __syncthreads();
     for (int i = tid; i < nk; i += blockDim.x) {
-        const int b = i / 16, c = i % 16;
+        const int b = i / R, c = i - (i / R) * R;
         unsigned long long k = 0;
         if (b < B && c < cands && cur[(size_t)g * B + b].alive) {
             const float score = cur[(size_t)g * B + b].logp +
@@ -170,7 +177,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
             s.logp = 0.0f;
         } else {
             const int i = (int)(0xFFFFu - (uint32_t)(k & 0xFFFFu));
-            const int pb = i / 16, c = i % 16;
+            const int pb = i / R, c = i - (i / R) * R;
             const BeamState p = cur[(size_t)g * B + pb];
             const int j = slot_task(p.used, n, c);
             const tm_task t = tasks[off + j];
