@@ -89,10 +89,9 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
                                                 int32_t* __restrict__ ms_out,
                                                 int32_t* __restrict__ status)
 {
-    int32_t hs = 0, dinit = 0;
-    int err = check_group(tasks + off, n, dma, TM_MAX_TASKS, &hs, &dinit);
-    if (err != 0) {
-        if (lane == 0 && status) status[g] = err;
+    // the input check of check_group, one task per lane
+    if (n < 1 || n > TM_MAX_TASKS || (dma != 1 && dma != 2)) {
+        if (lane == 0 && status) status[g] = TM_EINVAL;
         return;
     }
     int32_t H = 0, K = 0, D = 0;
@@ -100,6 +99,20 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
         tm_task t = tasks[off + lane];
         H = t.htd; K = t.k; D = t.dth;
     }
+    long long tot = (long long)H + K + D, hsum = H;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(kFull, tot, o);
+        hsum += __shfl_xor_sync(kFull, hsum, o);
+    }
+    const int err = __ballot_sync(kFull, H < 0 || K < 0 || D < 0) ? TM_ENEG
+                    : tot > INT32_MAX                              ? TM_EOVERFLOW
+                                                                   : 0;
+    if (err != 0) {
+        if (lane == 0 && status) status[g] = err;
+        return;
+    }
+    const int32_t hs = (int32_t)hsum, dinit = dma == 1 ? hs : 0;
     unsigned rt = (n >= 32) ? kFull : ((1u << n) - 1u);   // remaining tasks
     HeurState st{0, 0, dinit, 0, kNegC, 0, -1};
     auto take = [&](int j) {
