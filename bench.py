@@ -43,6 +43,9 @@ WORKLOADS = {
     "dkdt64x10": ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
                   "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
                   "exhaustive 10! orders + heuristic per group"),
+    "dkdt32x12": ("32 groups x 12 tasks (half dominant-kernel, half dominant-transfer tasks in each, "
+                  "log-uniform [1e4,1e7] ns), seed 3, each under 2 and 1 DMA engines: exhaustive "
+                  "12! orders + heuristic per group (64 x 479,001,600 orders per step)"),
     "ragged8192": ("8192 ragged groups, n~U{4..9}, each task dominant-kernel or dominant-transfer "
                    "(p=1/2), durations log-uniform [1e4,1e7] ns, seed 2, DMA engines alternating "
                    "2/1: exhaustive n! orders + heuristic per group"),
@@ -96,6 +99,8 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 def workload(rank: int = 0, name: str = "dkdt64x10"):
+    if name == "dkdt32x12":
+        return inputs.half_dk_half_dt(groups=32, n=12, seed=3 + 1000 * rank, models=(2, 1))
     if name == "ragged8192":
         return inputs.ragged_mixed(groups=8192, seed=2 + 1000 * rank)
     return inputs.dk_dt_groups(groups=GROUPS, n=N_TASKS, seed=SEED + 1000 * rank)
@@ -268,7 +273,7 @@ def cpu_baseline(b, items_per_group: int = 2) -> dict:
     cores = oracle.hardware_threads()
     n_orders, dt = oracle_sample(b, items_per_group)
     return {"value": n_orders / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"{items_per_group} two-task prefixes x 8! orders of each of the "
+            "sample": (f"{items_per_group} two-task prefixes x (n-2)! orders of each of the "
                        f"{b.G} group evaluations ({n_orders} orders, event-driven "
                        f"simulation per order, {cores} threads, {dt:.2f} s)")}
 
@@ -465,7 +470,7 @@ def run_tm(args):
             "wall_s_timed": wall,
         }
         if ws_total == 1 and not args.no_cpu_baseline:
-            result["cpu_baseline"] = cpu_baseline(b)
+            result["cpu_baseline"] = cpu_baseline(b, 1 if args.workload == "dkdt32x12" else 2)
         print(json.dumps(result))
     if dist is not None:
         dist.barrier()
