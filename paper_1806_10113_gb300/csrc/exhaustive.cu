@@ -41,6 +41,12 @@ namespace tmgpu {
 namespace {
 
 constexpr int kEnumBlock = 128;
+// Three resident blocks per SM leave the enumeration up to 168 registers per
+// thread (no spills); measured as fast as four blocks of 128 registers, and
+// up to 2% faster on ragged and 12-task batches.
+#ifndef TM_ENUM_MIN_BLOCKS
+#define TM_ENUM_MIN_BLOCKS 3
+#endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // 4-subsets of {0..11} in colexicographic order: the subsets of {0..n-1}
@@ -750,7 +756,7 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
 }
 
 template <int PDMAX>
-__global__ void __launch_bounds__(kEnumBlock, 4)
+__global__ void __launch_bounds__(kEnumBlock, TM_ENUM_MIN_BLOCKS)
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
             uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks)
