@@ -10,7 +10,8 @@
 //
 // Step i (the i-th position): every live beam b of group g proposes each of
 // its unused tasks; row ((g * B + b) * R + slot) of the feature matrix holds
-// the features of "append the slot-th unused task", R = nmax - i.  The
+// the features of "append the slot-th unused task", R = nmax - i (written by
+// the init kernel for i = 0 and by the previous selection after that).  The
 // ranker scores the rows; a block per group turns scores into log-softmax
 // over each beam's candidates, adds the beam's log-probability, keeps the
 // best B candidates (bitonic sort in shared memory of the B x R keys; ties:
@@ -46,10 +47,33 @@ __device__ __forceinline__ int slot_task(uint32_t used, int n, int slot)
     return __ffs(free_mask) - 1;
 }
 
+// Candidate row (g, b, slot) of a step with R rows per beam: the features
+// of appending the slot-th unplaced task to beam state s, as one 64-byte row
+// (four 16-byte stores).
+__device__ __forceinline__ void write_row(__nv_bfloat16* __restrict__ X, int64_t row,
+                                          const tm_task* __restrict__ gtasks, int n,
+                                          const BeamState& s, int dma, float scale, int slot)
+{
+    float f[kFeat];
+    rank_features(gtasks, n, s.used, s.h, s.k, s.d, dma, scale, slot_task(s.used, n, slot), f);
+    uint32_t w[kFeat / 2];
+#pragma unroll
+    for (int q = 0; q < kFeat / 2; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    uint4* x = reinterpret_cast<uint4*>(X + row * kFeat);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+// Initial beams (only beam 0 live, empty prefix) and the candidate rows of
+// position 0 (R rows per beam; rows of dead beams are never read).
 __global__ void beam_init_kernel(const int32_t* __restrict__ offsets,
                                  const int32_t* __restrict__ status, const tm_task* __restrict__ tasks,
-                                 const tm_device* __restrict__ devs, int G, int B,
-                                 BeamState* __restrict__ st, float* __restrict__ scale)
+                                 const tm_device* __restrict__ devs, int G, int B, int R,
+                                 BeamState* __restrict__ st, float* __restrict__ scale,
+                                 __nv_bfloat16* __restrict__ X)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= G * B) return;
@@ -68,12 +92,18 @@ __global__ void beam_init_kernel(const int32_t* __restrict__ offsets,
             total += (int64_t)tasks[off + i].htd + tasks[off + i].k + tasks[off + i].dth;
         }
         if (devs[g].dma_engines == 1) s.d = (int32_t)hs;   // one transfer queue
-        scale[g] = total > 0 ? (float)n / (float)total : 0.0f;
+        const float sc = total > 0 ? (float)n / (float)total : 0.0f;
+        scale[g] = sc;
+        if (s.alive)
+            for (int slot = 0; slot < n; ++slot)
+                write_row(X, (int64_t)t * R + slot, tasks + off, n, s, devs[g].dma_engines, sc, slot);
     }
     st[t] = s;
 }
 
-// Feature rows of step i.  One thread per (g, b, slot).
+// Candidate rows of position pos from the current beams, one thread per
+// (g, b, slot): used for large batches, where spreading the rows over the
+// whole GPU beats writing them inside the per-group selection blocks.
 __global__ void beam_features_kernel(const int32_t* __restrict__ offsets,
                                      const tm_task* __restrict__ tasks,
                                      const tm_device* __restrict__ devs,
@@ -87,23 +117,8 @@ __global__ void beam_features_kernel(const int32_t* __restrict__ offsets,
     const int g = gb / B;
     const int off = offsets[g], n = offsets[g + 1] - off;
     const BeamState s = st[gb];
-    float f[kFeat];
-    if (s.alive && pos < n && slot < n - pos) {
-        const int j = slot_task(s.used, n, slot);
-        rank_features(tasks + off, n, s.used, s.h, s.k, s.d, devs[g].dma_engines, scale[g], j, f);
-    } else {
-        for (int q = 0; q < kFeat; ++q) f[q] = 0.0f;
-    }
-    // one 64-byte row: four 16-byte stores
-    uint32_t w[kFeat / 2];
-#pragma unroll
-    for (int q = 0; q < kFeat / 2; ++q) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
-        w[q] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-    uint4* x = reinterpret_cast<uint4*>(X + row * kFeat);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    if (s.alive && pos < n && slot < n - pos)
+        write_row(X, row, tasks + off, n, s, devs[g].dma_engines, scale[g], slot);
 }
 
 __device__ __forceinline__ uint32_t orderable(float v)
@@ -112,10 +127,17 @@ __device__ __forceinline__ uint32_t orderable(float v)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// With WRITE_NEXT it also writes the candidate rows of position pos + 1
+// (R - 1 rows per beam) from the new beams, so that each position costs two
+// launches: the scores and this selection (small batches, where launches
+// dominate).
+template <bool WRITE_NEXT>
 __global__ void __launch_bounds__(kSelectThreads)
 beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
+                   const tm_device* __restrict__ devs, const float* __restrict__ scale,
                    const float* __restrict__ logits, const BeamState* __restrict__ cur,
-                   BeamState* __restrict__ nxt, int B, int R, int pos)
+                   BeamState* __restrict__ nxt, int B, int R, int pos,
+                   __nv_bfloat16* __restrict__ X)
 {
     const int g = blockIdx.x;
     const int off = offsets[g], n = offsets[g + 1] - off;
@@ -126,6 +148,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
     }
     __shared__ float lse[64];
     __shared__ unsigned long long key[kMaxCand];
+    __shared__ BeamState ns[64];
     const int cands = n - pos;
     int nk = 32;
     while (nk < B * R) nk <<= 1;    // keys sorted: a power of two >= B * R
@@ -189,6 +212,18 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
             s.alive = 1;
         }
         nxt[(size_t)g * B + b] = s;
+        ns[b] = s;
+    }
+    // candidate rows of the next position
+    const int R1 = R - 1, left = n - pos - 1;
+    if (!WRITE_NEXT || R1 <= 0 || left <= 0) return;
+    __syncthreads();
+    const int dma = devs[g].dma_engines;
+    const float sc = scale[g];
+    for (int r = tid; r < B * R1; r += blockDim.x) {
+        const int b = r / R1, slot = r - (r / R1) * R1;
+        if (slot < left && ns[b].alive)
+            write_row(X, ((int64_t)g * B + b) * R1 + slot, tasks + off, n, ns[b], dma, sc, slot);
     }
 }
 
@@ -363,11 +398,13 @@ __global__ void rows_kernel(const tm_task* __restrict__ tasks, const int32_t* __
 size_t beam_state_bytes(int G, int B) { return (size_t)G * B * sizeof(BeamState); }
 
 cudaError_t beam_init(const int32_t* offsets, const int32_t* status, const tm_task* tasks,
-                      const tm_device* devs, int G, int B, void* st, float* scale, cudaStream_t s)
+                      const tm_device* devs, int G, int B, int R, void* st, float* scale,
+                      bf16_raw* X, cudaStream_t s)
 {
     const int threads = G * B;
-    beam_init_kernel<<<(threads + 255) / 256, 256, 0, s>>>(offsets, status, tasks, devs, G, B,
-                                                           static_cast<BeamState*>(st), scale);
+    beam_init_kernel<<<(threads + 255) / 256, 256, 0, s>>>(offsets, status, tasks, devs, G, B, R,
+                                                           static_cast<BeamState*>(st), scale,
+                                                           reinterpret_cast<__nv_bfloat16*>(X));
     return cudaGetLastError();
 }
 
@@ -382,12 +419,19 @@ cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm
     return cudaGetLastError();
 }
 
-cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const float* logits,
-                        const void* cur, void* nxt, int G, int B, int R, int pos, cudaStream_t s)
+cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
+                        const float* scale, const float* logits, const void* cur, void* nxt, int G,
+                        int B, int R, int pos, bf16_raw* X, cudaStream_t s)
 {
-    beam_select_kernel<<<G, kSelectThreads, 0, s>>>(offsets, tasks, logits,
-                                                    static_cast<const BeamState*>(cur),
-                                                    static_cast<BeamState*>(nxt), B, R, pos);
+    // X == nullptr: the caller writes the next position's rows itself
+    if (X)
+        beam_select_kernel<true><<<G, kSelectThreads, 0, s>>>(
+            offsets, tasks, devs, scale, logits, static_cast<const BeamState*>(cur),
+            static_cast<BeamState*>(nxt), B, R, pos, reinterpret_cast<__nv_bfloat16*>(X));
+    else
+        beam_select_kernel<false><<<G, kSelectThreads, 0, s>>>(
+            offsets, tasks, devs, scale, logits, static_cast<const BeamState*>(cur),
+            static_cast<BeamState*>(nxt), B, R, pos, nullptr);
     return cudaGetLastError();
 }
 

@@ -12,12 +12,14 @@ namespace tmgpu {
 // beam.cu
 size_t beam_state_bytes(int G, int B);
 cudaError_t beam_init(const int32_t* offsets, const int32_t* status, const tm_task* tasks,
-                      const tm_device* devs, int G, int B, void* st, float* scale, cudaStream_t s);
+                      const tm_device* devs, int G, int B, int R, void* st, float* scale,
+                      bf16_raw* X, cudaStream_t s);
 cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
                           const float* scale, const void* st, int G, int B, int R, int pos,
                           bf16_raw* X, cudaStream_t s);
-cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const float* logits,
-                        const void* cur, void* nxt, int G, int B, int R, int pos, cudaStream_t s);
+cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
+                        const float* scale, const float* logits, const void* cur, void* nxt, int G,
+                        int B, int R, int pos, bf16_raw* X, cudaStream_t s);
 cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const void* st, int G,
                         int B, const int32_t* heur_ms, int32_t* orders, int32_t* ms,
                         int32_t* beam_won, cudaStream_t s);
@@ -91,17 +93,23 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
         const int32_t* off = d_offsets + g0;
         void* cur = sc.st[0].p;
         void* nxt = sc.st[1].p;
-        e = beam_init(off, status + g0, d_tasks, d_devs + g0, gc, B, cur, sc.scale.as<float>(), s);
+        e = beam_init(off, status + g0, d_tasks, d_devs + g0, gc, B, nm, cur, sc.scale.as<float>(),
+                      sc.bx.as<bf16_raw>(), s);
+        // small batches: the selection writes the next rows (two launches per
+        // position); large ones: a separate row kernel spreads them over the GPU
+        const bool fused = (int64_t)gc * B * nm <= kBeamFusedRows;
         for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
             const int R = nm - pos;
             const int64_t rows = (int64_t)gc * B * R;
-            e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R, pos,
-                              sc.bx.as<bf16_raw>(), s);
+            if (!fused && pos > 0)
+                e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R,
+                                  pos, sc.bx.as<bf16_raw>(), s);
             if (e == cudaSuccess)
                 e = ranker_forward_tc(sc.bx.as<bf16_raw>(), rows, r->Wimg, sc.blog.as<float>(),
                                       r->d_err, forward_blocks(r, rows), s);
             if (e == cudaSuccess)
-                e = beam_select(off, d_tasks, sc.blog.as<float>(), cur, nxt, gc, B, R, pos, s);
+                e = beam_select(off, d_tasks, d_devs + g0, sc.scale.as<float>(), sc.blog.as<float>(),
+                                cur, nxt, gc, B, R, pos, fused ? sc.bx.as<bf16_raw>() : nullptr, s);
             std::swap(cur, nxt);
         }
         if (e == cudaSuccess)

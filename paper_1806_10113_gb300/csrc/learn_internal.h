@@ -44,6 +44,10 @@ struct BeamScratch {
 // Rows of one beam step are processed in chunks of groups so that the
 // feature matrix stays below this many rows.
 constexpr int64_t kBeamRowsPerChunk = int64_t(1) << 22;
+// Batches with at most this many first-position rows let the selection
+// kernel write the next position's rows (fewer launches); larger ones use a
+// separate row kernel (more parallel).
+constexpr int64_t kBeamFusedRows = int64_t(1) << 19;
 
 // Beam search of G groups (see tm_beam_batch_dev).  d_offsets / h_offsets
 // hold G + 1 task offsets (h_offsets need not start at 0; only differences

@@ -262,6 +262,19 @@ def test_beam_orders_valid_and_exact(width):
             assert won[g] == 1 and ms[g] < h_ms
 
 
+def test_beam_large_batch_equals_small_batches():
+    # 800 groups of 12 tasks at width 64 (614k first-position rows) take the
+    # separate row kernel; 25 of them alone take the fused selection path
+    b = inputs.training_groups(800, 12, 12, seed=9)
+    r = tm.Ranker(seed=8)
+    big = run_beam(b, r, 64)
+    sub = inputs.make_batch([b.group(g) for g in range(25)], b.dma[:25])
+    small = run_beam(sub, r, 64)
+    T = int(sub.offsets[-1])
+    assert np.array_equal(big[0][:T], small[0]) and np.array_equal(big[1][:25], small[1])
+    assert np.array_equal(big[3][:25], small[3]) and (big[2] == 0).all()
+
+
 def test_beam_is_exhaustive_when_wide_enough():
     # n <= 4 and width 24 >= n!: every partial order survives every step
     rng = np.random.default_rng(14)
