@@ -35,16 +35,17 @@ constexpr int kOvlMaxRate = 1024;
 constexpr int kOvlBlock = 128;
 constexpr uint32_t kRanksPerThread = 64;
 
-// Exact ceil(x / v) for x < 2^62 and 1 <= v <= 1024: one 64 x 64-bit
-// multiply-high by floor((2^64 - 1) / v) (division by invariant integers,
-// Granlund and Montgomery, PLDI 1994), whose quotient is at most two below
-// floor(x / v), then corrected by the exact remainder.
+// Exact ceil(x / v) for 1 <= v <= 1024: a multiply-high by floor((2^B - 1) / v)
+// for B-bit x (division by invariant integers, Granlund and Montgomery, PLDI
+// 1994), whose quotient is at most two below floor(x / v), then corrected by
+// the exact remainder.
 struct Div {
-    unsigned long long v, m;
+    unsigned long long v, m;   // m for 64-bit numerators (x < 2^62)
+    uint32_t m32;              // m for 32-bit numerators (x < 2^31)
 };
 __host__ __device__ inline Div make_div(unsigned long long v)
 {
-    return Div{v, v <= 1 ? 0ull : (~0ull) / v};
+    return Div{v, v <= 1 ? 0ull : (~0ull) / v, v <= 1 ? 0u : 0xFFFFFFFFu / (uint32_t)v};
 }
 __device__ __forceinline__ long long ceil_div(long long x, const Div& d)
 {
@@ -56,37 +57,60 @@ __device__ __forceinline__ long long ceil_div(long long x, const Div& d)
     if (r >= d.v) { q += 1; r -= d.v; }
     return (long long)(q + (r != 0ull));
 }
+__device__ __forceinline__ int32_t ceil_div(int32_t x, const Div& d)
+{
+    if (d.v <= 1) return x;
+    const uint32_t v = (uint32_t)d.v, ux = (uint32_t)x;
+    uint32_t q = __umulhi(ux, d.m32);
+    uint32_t r = ux - q * v;
+    if (r >= v) { q += 1; r -= v; }
+    if (r >= v) { q += 1; r -= v; }
+    return (int32_t)(q + (r != 0u));
+}
 
 // Total time of one order (tasks in `tbl`, order as nibbles, position 0
-// lowest) on two DMA engines under the partial-overlap rule.
-__device__ long long overlap_makespan(const int4* __restrict__ tbl, int n, uint64_t order,
-                                      const Div& slow, const Div& full)
+// lowest) on two DMA engines under the partial-overlap rule.  W is the type
+// of times and work left: int32_t when every transfer's work plus one rate
+// step stays below 2^31 (checked per group), else 64-bit.
+template <typename W>
+__device__ W overlap_makespan(const int4* __restrict__ tbl, int n, uint64_t order, const Div& slow,
+                              const Div& full)
 {
-    const long long rs = (long long)slow.v, rf = (long long)full.v;
+    const W rs = (W)slow.v, rf = (W)full.v;
     int ih = 0, ik = 0, id = 0;          // next position each queue starts
     bool hb = false, kb = false, db = false;
-    long long hl = 0, kl = 0, dl = 0;    // work left: transfers in units, kernel in ns
-    long long T = 0;
+    W hl = 0, kl = 0, dl = 0;            // work left: transfers in units, kernel in ns
+    W T = 0;
     for (;;) {
-        if (!hb && ih < n) { hb = true; hl = (long long)tbl[nib_get(order, ih)].x * rf; }
+        if (!hb && ih < n) { hb = true; hl = (W)tbl[nib_get(order, ih)].x * rf; }
         // positions below ih (ik) have finished their HtD (kernel)
         if (!kb && ik < ih) { kb = true; kl = tbl[nib_get(order, ik)].y; }
-        if (!db && id < ik) { db = true; dl = (long long)tbl[nib_get(order, id)].z * rf; }
+        if (!db && id < ik) { db = true; dl = (W)tbl[nib_get(order, id)].z * rf; }
         if (!hb && !kb && !db) break;
         const bool both = hb && db;
         const Div& v = both ? slow : full;
-        const long long rate = both ? rs : rf;
-        long long next = LLONG_MAX;
-        if (hb) next = min(next, T + ceil_div(hl, v));
-        if (kb) next = min(next, T + kl);
-        if (db) next = min(next, T + ceil_div(dl, v));
-        const long long dt = next - T;
+        const W rate = both ? rs : rf;
+        W next = sizeof(W) == 4 ? (W)INT32_MAX : (W)LLONG_MAX;
+        if (hb) next = min(next, (W)(T + ceil_div(hl, v)));
+        if (kb) next = min(next, (W)(T + kl));
+        if (db) next = min(next, (W)(T + ceil_div(dl, v)));
+        const W dt = next - T;
         T = next;
         if (hb) { hl -= rate * dt; if (hl <= 0) { hb = false; ++ih; } }
         if (kb) { kl -= dt; if (kl <= 0) { kb = false; ++ik; } }
         if (db) { dl -= rate * dt; if (dl <= 0) { db = false; ++id; } }
     }
     return T;
+}
+
+// Whether the 32-bit loop is exact for a group: every transfer's work
+// (duration x den) plus one step of the fastest rate below 2^31.  (Times
+// stay below the group's bound, itself below 2^31.)
+__device__ __forceinline__ bool fits32(const tm_task* tasks, int n, int32_t den)
+{
+    long long mx = 0;
+    for (int i = 0; i < n; ++i) mx = max(mx, (long long)max(tasks[i].htd, tasks[i].dth));
+    return mx * den + den <= INT32_MAX;
 }
 
 // Plain model (one DMA engine, or full rate): the closed-form recurrence.
@@ -146,7 +170,8 @@ __global__ void overlap_predict_kernel(const tm_task* __restrict__ tasks,
     for (int i = 0; i < n; ++i) tb[i] = make_int4(tasks[off + i].htd, tasks[off + i].k, tasks[off + i].dth, 0);
     long long ms;
     if (dma == 1 || num == den) ms = plain_makespan(tb, n, order, dinit);
-    else ms = overlap_makespan(tb, n, order, make_div(num), make_div(den));
+    else if (fits32(tasks + off, n, den)) ms = overlap_makespan<int32_t>(tb, n, order, make_div(num), make_div(den));
+    else ms = overlap_makespan<long long>(tb, n, order, make_div(num), make_div(den));
     out[g] = (int32_t)ms;
     if (status) status[g] = 0;
 }
@@ -155,6 +180,7 @@ __global__ void overlap_predict_kernel(const tm_task* __restrict__ tasks,
 
 struct OvlInfo {
     int32_t off, n, dinit, status;
+    int32_t w32, pad0, pad1, pad2;   // w32: the 32-bit loop is exact for this group
 };
 
 __global__ void ovl_prep_kernel(const tm_task* __restrict__ tasks,
@@ -175,6 +201,8 @@ __global__ void ovl_prep_kernel(const tm_task* __restrict__ tasks,
     oi.n = n;
     oi.dinit = devs[g].dma_engines == 1 ? dinit : -1;   // -1: the overlap loop
     oi.status = st;
+    oi.w32 = st == 0 && fits32(tasks + off, n, den) ? 1 : 0;
+    oi.pad0 = oi.pad1 = oi.pad2 = 0;
     if (st == 0)
         for (int i = 0; i < n; ++i)
             tbl[off + i] = make_int4(tasks[off + i].htd, tasks[off + i].k, tasks[off + i].dth, 0);
@@ -270,7 +298,8 @@ ovl_enum_kernel(const unsigned long long* __restrict__ base, int G,
         for (; x < gend; ++x, ++rank) {
             const long long ms = (oi.dinit >= 0 || num == den)
                                      ? plain_makespan(t, oi.n, order, max(oi.dinit, 0))
-                                     : overlap_makespan(t, oi.n, order, slow, full);
+                                 : oi.w32 ? (long long)overlap_makespan<int32_t>(t, oi.n, order, slow, full)
+                                          : overlap_makespan<long long>(t, oi.n, order, slow, full);
             const int32_t m = (int32_t)ms;
             a.sum += (unsigned long long)(uint32_t)m;
             if (m < a.best) { a.best = m; a.best_rank = rank; }       // ranks rise: first kept

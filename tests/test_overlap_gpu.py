@@ -116,3 +116,19 @@ def test_exhaustive_dev_sampled_n10():
             m = oracle.predict_overlap(t, o, 2, 2, 3)
             assert got[g]["best"] <= m <= got[g]["worst"]
         assert got[g]["best"] * 3628800 <= got[g]["sum"] <= got[g]["worst"] * 3628800
+
+
+def test_64bit_work_path():
+    # durations of 3..5 ms at rate 1000/1024: a transfer's work (duration x
+    # 1024 units) passes 2^31, so these groups take the 64-bit event loop
+    b = inputs.random_groups(46, [5, 6, 7, 3], lo=3_000_000, hi=5_000_000)
+    got = tm.stats_to_dicts(tm.tm_exhaustive_overlap_batch(b.tasks, b.offsets, b.dma, 1000, 1024),
+                            b.sizes())
+    for g in range(b.G):
+        assert_stats(got[g], oracle.exhaustive_overlap(b.group(g), int(b.dma[g]), 1000, 1024), g)
+    rng = np.random.default_rng(11)
+    orders = np.concatenate([rng.permutation(n) for n in b.sizes()]).astype(np.int32)
+    ms = tm.tm_predict_overlap_batch(b.tasks, b.offsets, orders, b.dma, 1000, 1024)
+    for g in range(b.G):
+        o = orders[b.offsets[g]:b.offsets[g + 1]]
+        assert ms[g] == oracle.predict_overlap(b.group(g), o, int(b.dma[g]), 1000, 1024)
