@@ -99,10 +99,30 @@ struct DevBuf {
     void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
 };
 
+// Page-locked host staging, grown on demand (contents not kept).
+struct PinBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes)
+    {
+        if (bytes <= cap) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes, 4096);
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) { p = nullptr; return false; }
+        cap = want;
+        return true;
+    }
+    void release() { if (p) cudaFreeHost(p); p = nullptr; cap = 0; }
+};
+
 struct Context {
     int device = -1;
     cudaStream_t stream = nullptr;
     DevBuf tasks, offsets, devs, orders, out, stats, status;
+    DevBuf blk_in, blk_out;          // packed inputs / outputs of the exhaustive host call
+    PinBuf pin_in, pin_out;
     tm_plan* plan = nullptr;
     std::vector<int32_t> plan_offsets;
     unsigned plan_epoch = 0;
@@ -111,7 +131,10 @@ struct Context {
         if (plan) tm_plan_destroy(plan);
         plan = nullptr;
         plan_offsets.clear();
-        for (DevBuf* b : {&tasks, &offsets, &devs, &orders, &out, &stats, &status}) b->release();
+        for (DevBuf* b : {&tasks, &offsets, &devs, &orders, &out, &stats, &status, &blk_in, &blk_out})
+            b->release();
+        pin_in.release();
+        pin_out.release();
         if (stream) cudaStreamDestroy(stream);
         stream = nullptr;
     }
@@ -504,37 +527,41 @@ int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const t
     }
     const int T = offsets[G];
     cudaStream_t s = c->stream;
-    if ((rc = copy_in(c->tasks, tasks, T * sizeof(tm_task), s)) != TM_OK) return rc;
-    if ((rc = copy_in(c->devs, devs, G * sizeof(tm_device), s)) != TM_OK) return rc;
-    if (!c->stats.ensure(G * sizeof(tm_stats)) || !c->status.ensure(G * sizeof(int32_t)) ||
-        !c->orders.ensure(T * sizeof(int32_t)) || !c->out.ensure(G * sizeof(int32_t)))
+    // one packed H2D copy (tasks, device models) and one packed D2H copy
+    // (stats, status, makespans, orders), both through page-locked staging
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t i_devs = al((size_t)T * sizeof(tm_task)), in_bytes = i_devs + (size_t)G * 4;
+    const size_t o_status = al((size_t)G * sizeof(tm_stats)), o_ms = o_status + al((size_t)G * 4),
+                 o_orders = o_ms + al((size_t)G * 4), out_bytes = o_orders + (size_t)T * 4;
+    if (!c->blk_in.ensure(in_bytes) || !c->blk_out.ensure(out_bytes) ||
+        !c->pin_in.ensure(in_bytes) || !c->pin_out.ensure(out_bytes))
         return TM_ENOMEM;
+    unsigned char* hin = static_cast<unsigned char*>(c->pin_in.p);
+    std::memcpy(hin, tasks, (size_t)T * sizeof(tm_task));
+    std::memcpy(hin + i_devs, devs, (size_t)G * 4);
+    TM_CUDA(cudaMemcpyAsync(c->blk_in.p, hin, in_bytes, cudaMemcpyHostToDevice, s));
+    unsigned char* din = c->blk_in.as<unsigned char>();
+    unsigned char* dout = c->blk_out.as<unsigned char>();
+    const tm_task* d_tasks = reinterpret_cast<const tm_task*>(din);
+    const tm_device* d_devs = reinterpret_cast<const tm_device*>(din + i_devs);
+    tm_stats* d_stats = reinterpret_cast<tm_stats*>(dout);
+    int32_t* d_status = reinterpret_cast<int32_t*>(dout + o_status);
+    int32_t* d_ms = reinterpret_cast<int32_t*>(dout + o_ms);
+    int32_t* d_orders = reinterpret_cast<int32_t*>(dout + o_orders);
     if (orders_out)
-        rc = tm_schedule_batch_dev(c->plan, c->tasks.as<tm_task>(), c->devs.as<tm_device>(),
-                                   c->stats.as<tm_stats>(), c->orders.as<int32_t>(),
-                                   c->out.as<int32_t>(), c->status.as<int32_t>(), s);
+        rc = tm_schedule_batch_dev(c->plan, d_tasks, d_devs, d_stats, d_orders, d_ms, d_status, s);
     else
-        rc = tm_exhaustive_batch_dev(c->plan, c->tasks.as<tm_task>(), c->devs.as<tm_device>(),
-                                     c->stats.as<tm_stats>(), c->status.as<int32_t>(), s);
+        rc = tm_exhaustive_batch_dev(c->plan, d_tasks, d_devs, d_stats, d_status, s);
     if (rc != TM_OK) return rc;
-    std::vector<tm_stats> out(G);
-    std::vector<int32_t> status(G), orders(orders_out ? T : 0), ms(orders_out ? G : 0);
-    TM_CUDA(cudaMemcpyAsync(out.data(), c->stats.p, G * sizeof(tm_stats), cudaMemcpyDeviceToHost,
-                            s));
-    TM_CUDA(cudaMemcpyAsync(status.data(), c->status.p, G * sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, s));
-    if (orders_out) {
-        TM_CUDA(cudaMemcpyAsync(orders.data(), c->orders.p, T * sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, s));
-        TM_CUDA(cudaMemcpyAsync(ms.data(), c->out.p, G * sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, s));
-    }
+    const size_t copy_bytes = orders_out ? out_bytes : o_ms;
+    TM_CUDA(cudaMemcpyAsync(c->pin_out.p, dout, copy_bytes, cudaMemcpyDeviceToHost, s));
     TM_CUDA(cudaStreamSynchronize(s));
-    if ((rc = first_error(status.data(), G)) != TM_OK) return rc;
-    std::memcpy(stats, out.data(), G * sizeof(tm_stats));
+    const unsigned char* hout = static_cast<const unsigned char*>(c->pin_out.p);
+    if ((rc = first_error(reinterpret_cast<const int32_t*>(hout + o_status), G)) != TM_OK) return rc;
+    std::memcpy(stats, hout, (size_t)G * sizeof(tm_stats));
     if (orders_out) {
-        std::memcpy(orders_out, orders.data(), T * sizeof(int32_t));
-        if (makespans_out) std::memcpy(makespans_out, ms.data(), G * sizeof(int32_t));
+        std::memcpy(orders_out, hout + o_orders, (size_t)T * sizeof(int32_t));
+        if (makespans_out) std::memcpy(makespans_out, hout + o_ms, (size_t)G * sizeof(int32_t));
     }
     return TM_OK;
 }
