@@ -228,12 +228,13 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 // ---- prep: validation, padded task table, suffix tables -------------------
 
 // One block per group (128 threads, or 512 when the batch has groups with
-// many 4-subsets).  Warp 0 loads and validates the group (lane i holds task
-// i) and writes its GroupInfo and padded task table (and finishes groups of
-// n <= 3 outright); then the block's threads stride over the (4-subset,
-// order) pairs of the group and tabulate alpha / beta / gamma.  When the
-// heuristic is requested, blocks G.. of the same launch run it, one warp per
-// group, beside the table blocks.
+// many 4-subsets; a warp per group measured slower: its largest groups'
+// tables then run on 32 threads).  Warp 0 loads and validates the group
+// (lane i holds task i) and writes its GroupInfo and padded task table (and
+// finishes groups of n <= 3 outright); then the block's threads stride over
+// the group's (4-subset, order) pairs and tabulate alpha / beta / gamma.
+// When the heuristic is requested, blocks G.. of the same launch run it, one
+// warp per group.
 constexpr int kPrepMaxThreads = 512;
 
 struct PrepArgs {
@@ -251,79 +252,66 @@ struct PrepArgs {
     uint32_t* next;               // dynamic chunk counter to zero, or null
 };
 
-__global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
+// Validation, GroupInfo, padded task table (and n <= 3 groups finished
+// outright) for group g, by one full warp (lane i holds task i); the tasks
+// also land in s_task.  Returns the group's status and HtD sum.
+__device__ __forceinline__ int prep_group(const PrepArgs& a, int g, int lane,
+                                          int4* __restrict__ s_task, int32_t* hs_out)
 {
-    const int kPrepThreads = blockDim.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const GroupPlan* __restrict__ gp = a.gp;
-    if (blockIdx.x >= (unsigned)a.G) {
-        // blocks past the groups run the heuristic, a warp per group, so that
-        // no table block waits for a heuristic warp
-        const int hg = (blockIdx.x - a.G) * (kPrepThreads / 32) + warp;
-        if (hg < a.G) {
-            const int hoff = gp[hg].off;
-            heur::heuristic_group(a.tasks, hoff, gp[hg + 1].off - hoff, a.devs[hg].dma_engines, hg,
-                                  lane, a.orders, a.makespans, nullptr);
-        }
-        return;
-    }
-    const int g = blockIdx.x;
     const int off = gp[g].off;
     const int n = gp[g + 1].off - off;
     const int dma = a.devs[g].dma_engines;
-    __shared__ int4 s_task[TM_MAX_EXHAUSTIVE];
-    __shared__ int s_status, s_hs;
-
-    if (a.next && g == 0 && tid == 0) *a.next = 0;
-    if (warp == 0) {
-        const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
-        tm_task t = mine ? a.tasks[off + lane] : tm_task{0, 0, 0};
-        const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
-        unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
+    const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
+    tm_task t = mine ? a.tasks[off + lane] : tm_task{0, 0, 0};
+    const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
+    unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
-        // with no negative duration and tot <= INT32_MAX the HtD sum fits
-        const int32_t hs = (int32_t)__reduce_add_sync(kFull, mine ? (uint32_t)t.htd : 0u);
-        int status = 0;
-        if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
-        else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
-        else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
-        if (mine) {
-            s_task[lane] = make_int4(t.htd, t.k, t.dth, 0);
-            if (status == 0) a.tbl[off + lane] = s_task[lane];
-        }
-        if (lane == 0) {
-            GroupInfo gi;
-            gi.off = off;
-            gi.n = n;
-            gi.hs = hs;
-            gi.dinit = dma == 1 ? hs : 0;
-            gi.status = status;
-            gi.sum32 = tot * 24u < (1ull << 32) ? 1u : 0u;
-            gi.pad0 = gi.pad1 = 0;
-            a.info[g] = gi;
-            if (status != 0 && a.status) a.status[g] = status;
-            s_status = status;
-            s_hs = hs;
-        }
-        if (status == 0 && n <= 3) {       // at most 6 orders: finish here
-            __syncwarp();
-            small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
-            if (lane == 0 && a.status) a.status[g] = 0;
-        }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+    // with no negative duration and tot <= INT32_MAX the HtD sum fits
+    const int32_t hs = (int32_t)__reduce_add_sync(kFull, mine ? (uint32_t)t.htd : 0u);
+    int status = 0;
+    if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
+    else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
+    else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
+    if (mine) {
+        s_task[lane] = make_int4(t.htd, t.k, t.dth, 0);
+        if (status == 0) a.tbl[off + lane] = s_task[lane];
     }
-    const int workers = kPrepThreads;
-    __syncthreads();
-    if (s_status != 0 || n < 4) return;
+    if (lane == 0) {
+        GroupInfo gi;
+        gi.off = off;
+        gi.n = n;
+        gi.hs = hs;
+        gi.dinit = dma == 1 ? hs : 0;
+        gi.status = status;
+        gi.sum32 = tot * 24u < (1ull << 32) ? 1u : 0u;
+        gi.pad0 = gi.pad1 = 0;
+        a.info[g] = gi;
+        if (status != 0 && a.status) a.status[g] = status;
+    }
+    if (status == 0 && n <= 3) {       // at most 6 orders: finish here
+        __syncwarp();
+        small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
+        if (lane == 0 && a.status) a.status[g] = 0;
+    }
+    *hs_out = hs;
+    return status;
+}
 
+// The suffix tables of group g (n >= 4): the (4-subset, order) pairs
+// first, first + stride, ...; tasks from s_task.
+__device__ __forceinline__ void prep_tables(const PrepArgs& a, int g, int n, int32_t hs,
+                                            const int4* __restrict__ s_task, uint32_t first,
+                                            uint32_t stride)
+{
     // beta: the makespan when only the K-engine time (= 0) enters S;
     // gamma: when only the HtD-engine time (= hs - sum of S's HtD) enters S.
     // A very negative start removes the other engines from the max-plus paths.
     const int64_t NEG = -(int64_t(1) << 40);
-    const int32_t hs = s_hs;
-    SuffixTab* out = a.sub + gp[g].sub_base;
+    SuffixTab* out = a.sub + a.gp[g].sub_base;
     const uint32_t pairs = choose4(n) * 24u;
-    for (uint32_t pj = tid; pj < pairs; pj += workers) {
+    for (uint32_t pj = first; pj < pairs; pj += stride) {
         const uint32_t s = pj / 24, j = pj - s * 24;
         const uint32_t mask = c_subsets.m[s];
         int4 t4[4];
@@ -359,6 +347,39 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
             out[s].pad0 = out[s].pad1 = 0;
         }
     }
+}
+
+// Heuristic warp hg (blocks or warps after the table work), if requested.
+__device__ __forceinline__ void prep_heuristic(const PrepArgs& a, int hg, int lane)
+{
+    if (!a.orders || hg >= a.G) return;
+    const int hoff = a.gp[hg].off;
+    heur::heuristic_group(a.tasks, hoff, a.gp[hg + 1].off - hoff, a.devs[hg].dma_engines, hg, lane,
+                          a.orders, a.makespans, nullptr);
+}
+
+// Block per group (groups with many 4-subsets).  Blocks G.. run the
+// heuristic, a warp per group, so that no table block waits for one.
+__global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x >= (unsigned)a.G) {
+        prep_heuristic(a, (blockIdx.x - a.G) * (blockDim.x / 32) + warp, lane);
+        return;
+    }
+    const int g = blockIdx.x;
+    __shared__ int4 s_task[TM_MAX_EXHAUSTIVE];
+    __shared__ int s_status, s_hs;
+    if (a.next && g == 0 && tid == 0) *a.next = 0;
+    if (warp == 0) {
+        int32_t hs;
+        const int st = prep_group(a, g, lane, s_task, &hs);
+        if (lane == 0) { s_status = st; s_hs = hs; }
+    }
+    __syncthreads();
+    const int n = a.gp[g + 1].off - a.gp[g].off;
+    if (s_status != 0 || n < 4) return;
+    prep_tables(a, g, n, s_hs, s_task, tid, blockDim.x);
 }
 
 // ---- enumeration ----------------------------------------------------------
@@ -866,7 +887,8 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.orders = d_orders;
     pa.makespans = d_makespans;
     pa.next = (p.chunks_per_thread > 1 && p.total_items > 0) ? p.d_next : nullptr;
-    // many (subset, order) pairs per group (n >= 9: >= 3,024): a bigger block
+    // a block per group: 512 threads when the batch's groups have many
+    // (subset, order) pairs (n >= 9: >= 3,024), else 128
     const int prep_threads = p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128;
     const int heur_blocks = d_orders ? (p.G + prep_threads / 32 - 1) / (prep_threads / 32) : 0;
     prep_kernel<<<p.G + heur_blocks, prep_threads, 0, stream>>>(pa);
