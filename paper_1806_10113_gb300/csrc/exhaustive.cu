@@ -299,53 +299,65 @@ __device__ __forceinline__ int prep_group(const PrepArgs& a, int g, int lane,
     return status;
 }
 
-// The suffix tables of group g (n >= 4): the (4-subset, order) pairs
-// first, first + stride, ...; tasks from s_task.
+// The suffix tables of group g (n >= 4), one 4-subset S per thread: S =
+// first, first + stride, ...; tasks from s_task.  The 24 orders of S are
+// walked depth-first in lexicographic order (prefix steps shared), and the
+// 208-byte table is written with 16-byte stores.
+//   beta[j]:  the order's makespan when only the K engine (free at 0) enters
+//             S: HtD and DtH start unconstrained, so the first task's kernel
+//             starts at 0 and its DtH right after it;
+//   gamma[j]: when only the HtD engine enters S, free at hS = hs - (S's HtD
+//             sum): the first task's kernel and DtH follow its HtD directly.
+// Every value is a path length within the group, so int32 holds it.
 __device__ __forceinline__ void prep_tables(const PrepArgs& a, int g, int n, int32_t hs,
                                             const int4* __restrict__ s_task, uint32_t first,
                                             uint32_t stride)
 {
-    // beta: the makespan when only the K-engine time (= 0) enters S;
-    // gamma: when only the HtD-engine time (= hs - sum of S's HtD) enters S.
-    // A very negative start removes the other engines from the max-plus paths.
-    const int64_t NEG = -(int64_t(1) << 40);
     SuffixTab* out = a.sub + a.gp[g].sub_base;
-    const uint32_t pairs = choose4(n) * 24u;
-    for (uint32_t pj = first; pj < pairs; pj += stride) {
-        const uint32_t s = pj / 24, j = pj - s * 24;
-        const uint32_t mask = c_subsets.m[s];
-        int4 t4[4];
+    const uint32_t subsets = choose4(n);
+    for (uint32_t sidx = first; sidx < subsets; sidx += stride) {
+        const uint32_t mask = c_subsets.m[sidx];
+        int4 t[4];
         for (int q = 0, m = (int)mask; q < 4; ++q) {
-            t4[q] = s_task[__ffs(m) - 1];
+            t[q] = s_task[__ffs(m) - 1];
             m &= m - 1;
         }
-        // order j of S in lexicographic order: Lehmer digits 6, 2, 1
-        const int dg[3] = {(int)j / 6, ((int)j % 6) / 2, (int)j % 2};
-        int slots = 0x3210, order[4];
+        const int32_t hS = hs - t[0].x - t[1].x - t[2].x - t[3].x;
+        int32_t beta[24], gamma[24];
+        int j = 0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int c = dg[q];
-            order[q] = (slots >> (4 * c)) & 0xF;
-            const int low = slots & ((1 << (4 * c)) - 1);
-            slots = low | ((slots >> (4 * c + 4)) << (4 * c));
-        }
-        order[3] = slots & 0xF;
-        int64_t hS = (int64_t)hs - t4[0].x - t4[1].x - t4[2].x - t4[3].x;
-        int64_t bh = NEG, bk = 0, bd = NEG, gh = hS, gk = NEG, gd = NEG;
+        for (int p0 = 0; p0 < 4; ++p0) {
+            const int4 A = t[p0];
+            const int32_t bk1 = A.y, bd1 = A.y + A.z;
+            const int32_t gh1 = hS + A.x, gk1 = gh1 + A.y, gd1 = gk1 + A.z;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x = order[q];
-            const int4 t = x == 0 ? t4[0] : x == 1 ? t4[1] : x == 2 ? t4[2] : t4[3];
-            bh += t.x; bk = max(bk, bh) + t.y; bd = max(bd, bk) + t.z;
-            gh += t.x; gk = max(gk, gh) + t.y; gd = max(gd, gk) + t.z;
+            for (int p1 = 0; p1 < 4; ++p1) {
+                if (p1 == p0) continue;
+                const int4 B = t[p1];
+                const int32_t bk2 = bk1 + B.y, bd2 = max(bd1, bk2) + B.z;
+                const int32_t gh2 = gh1 + B.x, gk2 = max(gk1, gh2) + B.y, gd2 = max(gd1, gk2) + B.z;
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    if (p2 == p0 || p2 == p1) continue;
+                    const int p3 = 6 - p0 - p1 - p2;
+                    const int4 C = t[p2], D = t[p3];
+                    const int32_t bk3 = bk2 + C.y, bd3 = max(bd2, bk3) + C.z;
+                    const int32_t bk4 = bk3 + D.y, bd4 = max(bd3, bk4) + D.z;
+                    const int32_t gh3 = gh2 + C.x, gk3 = max(gk2, gh3) + C.y, gd3 = max(gd2, gk3) + C.z;
+                    const int32_t gh4 = gh3 + D.x, gk4 = max(gk3, gh4) + D.y, gd4 = max(gd3, gk4) + D.z;
+                    beta[j] = bd4;
+                    gamma[j] = gd4;
+                    ++j;
+                }
+            }
         }
-        out[s].beta[j] = (int32_t)bd;
-        out[s].gamma[j] = (int32_t)gd;
-        if (j == 0) {
-            out[s].alpha = t4[0].z + t4[1].z + t4[2].z + t4[3].z;
-            out[s].mask = mask;
-            out[s].pad0 = out[s].pad1 = 0;
+        int4* dst = reinterpret_cast<int4*>(out + sidx);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            dst[q] = make_int4(beta[4 * q], beta[4 * q + 1], beta[4 * q + 2], beta[4 * q + 3]);
+            dst[6 + q] = make_int4(gamma[4 * q], gamma[4 * q + 1], gamma[4 * q + 2], gamma[4 * q + 3]);
         }
+        dst[12] = make_int4(t[0].z + t[1].z + t[2].z + t[3].z, (int)mask, 0, 0);
     }
 }
 
