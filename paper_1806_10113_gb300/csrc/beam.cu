@@ -36,7 +36,7 @@ static_assert(sizeof(BeamState) == 32, "beam state layout");
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kSelectThreads = 512;
+
 constexpr int kMaxCand = 64 * 16;   // beam width <= 64, tasks <= 16
 
 __device__ __forceinline__ int slot_task(uint32_t used, int n, int slot)
@@ -131,8 +131,10 @@ __device__ __forceinline__ uint32_t orderable(float v)
 // (R - 1 rows per beam) from the new beams, so that each position costs two
 // launches: the scores and this selection (small batches, where launches
 // dominate).
-template <bool WRITE_NEXT>
-__global__ void __launch_bounds__(kSelectThreads)
+// NT threads per block hold the up to kMaxCand sort keys, kMaxCand / NT
+// each (key i in thread i % NT).
+template <bool WRITE_NEXT, int NT>
+__global__ void __launch_bounds__(NT)
 beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
                    const tm_device* __restrict__ devs, const float* __restrict__ scale,
                    const float* __restrict__ logits, const BeamState* __restrict__ cur,
@@ -147,7 +149,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         return;
     }
     __shared__ float lse[64];
-    __shared__ unsigned long long key[kMaxCand];
+    __shared__ unsigned long long buf[2][kMaxCand];
     __shared__ BeamState ns[64];
     const int cands = n - pos;
     int nk = 32;
@@ -164,34 +166,57 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         lse[b] = s.alive ? mx + logf(z) : 0.0f;
     }
     __syncthreads();
-    for (int i = tid; i < nk; i += blockDim.x) {
+    constexpr int KPT = kMaxCand / NT;       // keys per thread
+    unsigned long long key[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        const int i = tid + q * NT;
         const int b = i / R, c = i - (i / R) * R;
-        unsigned long long k = 0;
-        if (b < B && c < cands && cur[(size_t)g * B + b].alive) {
+        key[q] = 0;
+        if (i < nk && b < B && c < cands && cur[(size_t)g * B + b].alive) {
             const float score = cur[(size_t)g * B + b].logp +
                                 (logits[((size_t)g * B + b) * R + c] - lse[b]);
-            k = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
+            key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
         }
-        key[i] = k;
     }
-    __syncthreads();
-    // bitonic sort, descending
+    // bitonic sort, descending: partners in the same thread (j >= NT) in
+    // registers, within a warp (j < 32) by shuffles, else through shared
+    // memory (two buffers, one barrier per stage)
+    int flip = 0;
     for (int kk = 2; kk <= nk; kk <<= 1) {
         for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < nk; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = key[i], c = key[ixj];
-                    const bool desc = (i & kk) == 0;
-                    if (desc ? (a < c) : (a > c)) { key[i] = c; key[ixj] = a; }
-                }
+            unsigned long long other[KPT];
+            if (j >= NT) {
+                // nk <= kMaxCand = 2 NT here: the partner is the thread's other key
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) other[q] = key[KPT - 1 - q];
+            } else if (j >= 32) {
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) buf[flip][tid + q * NT] = key[q];
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) other[q] = buf[flip][(tid + q * NT) ^ j];
+                flip ^= 1;
+            } else {
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) other[q] = __shfl_xor_sync(0xFFFFFFFFu, key[q], j);
             }
-            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < KPT; ++q) {
+                const int i = tid + q * NT;
+                const bool desc = (i & kk) == 0, lower = (i & j) == 0;
+                key[q] = (lower == desc) ? (key[q] > other[q] ? key[q] : other[q])
+                                         : (key[q] < other[q] ? key[q] : other[q]);
+            }
         }
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) buf[0][tid + q * NT] = key[q];
+    __syncthreads();
     for (int b = tid; b < B; b += blockDim.x) {
         BeamState s;
-        const unsigned long long k = key[b];
+        const unsigned long long k = buf[0][b];
         if (k == 0) {
             s.alive = 0;
             s.h = s.k = s.d = 0;
@@ -423,15 +448,19 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
                         const float* scale, const float* logits, const void* cur, void* nxt, int G,
                         int B, int R, int pos, bf16_raw* X, cudaStream_t s)
 {
-    // X == nullptr: the caller writes the next position's rows itself
-    if (X)
-        beam_select_kernel<true><<<G, kSelectThreads, 0, s>>>(
-            offsets, tasks, devs, scale, logits, static_cast<const BeamState*>(cur),
-            static_cast<BeamState*>(nxt), B, R, pos, reinterpret_cast<__nv_bfloat16*>(X));
-    else
-        beam_select_kernel<false><<<G, kSelectThreads, 0, s>>>(
-            offsets, tasks, devs, scale, logits, static_cast<const BeamState*>(cur),
-            static_cast<BeamState*>(nxt), B, R, pos, nullptr);
+    // X == nullptr: the caller writes the next position's rows itself.
+    // Large batches: 512 threads per group (more blocks per SM); small ones:
+    // 1024 (one key per thread, lower latency).
+    const BeamState* c = static_cast<const BeamState*>(cur);
+    BeamState* nx = static_cast<BeamState*>(nxt);
+    __nv_bfloat16* x = reinterpret_cast<__nv_bfloat16*>(X);
+    if (G > 1024) {
+        if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, x);
+        else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, nullptr);
+    } else {
+        if (X) beam_select_kernel<true, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, x);
+        else beam_select_kernel<false, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, nullptr);
+    }
     return cudaGetLastError();
 }
 

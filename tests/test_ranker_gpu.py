@@ -263,9 +263,10 @@ def test_beam_orders_valid_and_exact(width):
 
 
 def test_beam_large_batch_equals_small_batches():
-    # 800 groups of 12 tasks at width 64 (614k first-position rows) take the
-    # separate row kernel; 25 of them alone take the fused selection path
-    b = inputs.training_groups(800, 12, 12, seed=9)
+    # 1100 groups of 12 tasks at width 64 (845k first-position rows) take the
+    # separate row kernel and the 512-thread selection; 25 of them alone take
+    # the fused, 1024-thread selection
+    b = inputs.training_groups(1100, 12, 12, seed=9)
     r = tm.Ranker(seed=8)
     big = run_beam(b, r, 64)
     sub = inputs.make_batch([b.group(g) for g in range(25)], b.dma[:25])
