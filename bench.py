@@ -43,6 +43,9 @@ WORKLOADS = {
     "dkdt64x10": ("64 groups x 10 tasks (32 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
                   "32 dominant-transfer: reverse), seed 1, each under 1 and 2 DMA engines: "
                   "exhaustive 10! orders + heuristic per group"),
+    "single6": ("1 group x 6 tasks, durations U[50k,2M] ns, seed 0, two DMA engines: exhaustive 720 "
+                "orders + heuristic in one host-pointer call (tm_schedule_batch), one group per "
+                "call (latency)"),
     "dkdt32x12": ("32 groups x 12 tasks (half dominant-kernel, half dominant-transfer tasks in each, "
                   "log-uniform [1e4,1e7] ns), seed 3, each under 2 and 1 DMA engines: exhaustive "
                   "12! orders + heuristic per group (64 x 479,001,600 orders per step)"),
@@ -842,6 +845,51 @@ def run_heuristic(args):
     return 0
 
 
+def run_single(args):
+    """Latency of one small group through the host-pointer calls (the
+    paper's own use: one group, scheduled when it is submitted)."""
+    import torch
+    from paper_1806_10113_gb300 import tm
+    import oracle
+    torch.cuda.set_device(0)
+    b = inputs.single_group_uniform(n=6, seed=0)
+    # both searches in one call (the host-pointer tm_schedule_batch)
+    for _ in range(max(args.warmup, 10)):
+        tm.tm_schedule_batch(b.tasks, b.offsets, b.dma)
+    K = min(args.steps, 2000)
+    lat = []
+    for _ in range(K):
+        t0 = time.perf_counter()
+        st, order, ms = tm.tm_schedule_batch(b.tasks, b.offsets, b.dma)
+        lat.append(time.perf_counter() - t0)
+    ref = oracle.exhaustive(b.tasks, 2)
+    if int(st[0]["best"]) != ref["best"] or ([int(x) for x in order], int(ms[0])) != \
+            oracle.heuristic(b.tasks, 2):
+        raise RuntimeError("mismatch with the oracle")
+    t0 = time.perf_counter()
+    for _ in range(200):
+        oracle.exhaustive(b.tasks, 2)
+        oracle.heuristic(b.tasks, 2)
+    cpu_s = (time.perf_counter() - t0) / 200
+    lat_us = np.asarray(lat) * 1e6
+    out = {
+        "metric": "schedule latency of one 6-task group (exhaustive 720 orders + heuristic)",
+        "value": float(np.median(lat_us)), "unit": "us", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": float(np.median(lat_us)) / 1000,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOADS["single6"]},
+        "p99_us": float(np.quantile(lat_us, 0.99)),
+        "e2e": {"value": float(np.median(lat_us)), "unit": "us",
+                "h2d_bytes_per_step": int(2 * b.tasks.nbytes + 8),
+                "d2h_bytes_per_step": int(72 + 4 * 6 + 8)},
+        "gpu_launches": 3,
+        "cpu_baseline": {"value": cpu_s * 1e6, "unit": "us", "cores": 1, "kind": "oracle",
+                         "sample": "the same group, oracle exhaustive + heuristic, 200 calls"},
+    }
+    print(json.dumps(out))
+    return 0
+
+
 def measured_peak(key: str):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -882,6 +930,8 @@ def main(argv=None):
         return run_overlap(args)
     if args.workload == "heuristic1m":
         return run_heuristic(args)
+    if args.workload == "single6":
+        return run_single(args)
     return run_tm(args)
 
 
