@@ -444,6 +444,7 @@ def run_tm(args):
         achieved = alg_ops / enum_avg_s / 1e12
         stepwise_achieved = STEPWISE_OPS_PER_ORDER * n_orders / enum_avg_s / 1e12
         traffic = profiled_traffic()
+        rates = tm.tm_measure_int32_rates()
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_total, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / K,
@@ -468,7 +469,11 @@ def run_tm(args):
                          "ops_basis": "max-plus suffix decomposition (see method_ops_per_order)",
                          "stepwise_ops_per_order": round(STEPWISE_OPS_PER_ORDER, 3),
                          "stepwise_frac": stepwise_achieved / INT32_PEAK_TOPS,
-                         "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
+                         "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)",
+                         "measured_int32_tops": {k: v / 1e12 for k, v in rates.items()},
+                         "measured_basis": "independent int32 max / add / max-then-add chains "
+                                           "on every SM (tm_measure_int32_rates), after the "
+                                           "timed region"},
             "clocks": clocks,
             "wall_s_timed": wall,
         }

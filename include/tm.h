@@ -511,6 +511,17 @@ void tm_server_destroy(tm_server* server);
 
 /* ---- misc ---------------------------------------------------------------- */
 
+/* Measured int32 issue rates of this device, in operations per second:
+ * independent chains of int32 maxima (max_per_s), additions (add_per_s) and
+ * max-then-add recurrence steps k = max(k, h) + K counted as two operations
+ * (max_add_per_s), every SM busy.  These are the operations the exhaustive
+ * search's inner loop is made of (the FIFO recurrence of the model,
+ * Sec. 4.1), so they bound it from above.  Runs 12 short kernels (about
+ * 10 ms in all) on the legacy default stream and synchronises.  TM_EINVAL
+ * for a NULL pointer, TM_ECUDA / TM_ENOMEM on CUDA failures. */
+int tm_measure_int32_rates(double* max_per_s, double* add_per_s, double* max_add_per_s);
+
+
 const char* tm_strerror(int code);
 
 /* Library version, e.g. "tm 0.1 sm_103a". */

@@ -106,6 +106,7 @@ _SIGS = {
     "tm_exhaustive_overlap_batch": [_vp, _vp, ctypes.c_int, _vp, _i32, _i32, _vp],
     "tm_exhaustive_overlap_batch_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _i32, _i32, _vp, _vp,
                                         _vp],
+    "tm_measure_int32_rates": [_vp, _vp, _vp],
     "tm_strerror": [ctypes.c_int],
     "tm_version": [],
 }
@@ -136,6 +137,13 @@ def strerror(code: int) -> str:
 
 def version() -> str:
     return lib().tm_version().decode()
+
+
+def tm_measure_int32_rates() -> dict:
+    """Measured int32 max, add and max-then-add issue rates (operations/s)."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _check(lib().tm_measure_int32_rates(*[ctypes.byref(x) for x in v]), "tm_measure_int32_rates")
+    return {"max": v[0].value, "add": v[1].value, "max_add": v[2].value}
 
 
 def _check(rc: int, where: str):
