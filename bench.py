@@ -427,9 +427,9 @@ def run_tm(args):
     d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
     from paper_1806_10113_gb300 import autotune
     if args.tuning:
-        vals = [int(x) for x in args.tuning.split(",")] + [0, 0]
+        vals = [int(x) for x in args.tuning.split(",")] + [0, 0, 0]
         tuning = dict(zip(("pdmax", "fuse_finalize", "blocks_per_sm", "item_cost",
-                           "chunks_per_thread"), vals[:5]))
+                           "chunks_per_thread", "unroll"), vals[:6]))
     else:
         tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
     tm.tm_set_default_tuning(**tuning)          # also for the host-pointer (e2e) calls
@@ -994,7 +994,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dkdt64x10")
     ap.add_argument("--graph", action="store_true", help="replay each step as one CUDA graph")
     ap.add_argument("--tuning", default="",
-                    help="pdmax,fuse_finalize,blocks_per_sm[,item_cost[,chunks_per_thread]] "
+                    help="pdmax,fuse_finalize,blocks_per_sm[,item_cost[,chunks_per_thread[,unroll]]] "
                          "(skips the autotuner)")
     ap.add_argument("--groups", type=int, default=0, help="beam12: test groups (default 2048)")
     ap.add_argument("--train-groups", type=int, default=2_000_000)

@@ -173,13 +173,18 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  the cost; 2..64: the cost is cut into that many chunks per
  *                  thread, which warps take from a counter as they finish
  *                  (dynamic balance, for batches whose orders cost unevenly;
- *                  needs fuse_finalize != 1); 0: default 1 */
+ *                  needs fuse_finalize != 1); 0: default 1
+ *   unroll         1: the depth-first walk's level with three prefix tasks
+ *                  left runs as straight-line code (faster on batches of one
+ *                  group size); 2: as a loop (less code: faster on batches
+ *                  that mix group sizes); 0: default 2 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;
     int32_t blocks_per_sm;
     int32_t item_cost;
     int32_t chunks_per_thread;
+    int32_t unroll;
 } tm_tuning;
 
 int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tuning,

@@ -2,7 +2,7 @@
 
 Picks the tm_tuning (prefix depth per work item, fused or separate
 finalize, resident blocks per SM, per-item cost weight, static or dynamic
-work split) that runs a given batch fastest, by
+work split, straight-line or looped walk level) that runs a given batch fastest, by
 timing each candidate on the device with CUDA events (L2 flushed between
 runs), and caches the choice in a JSON file keyed by the batch's shape (the
 number of groups of each size), so later plans for the same shape reuse it
@@ -27,6 +27,7 @@ CANDIDATES = {
     "blocks_per_sm": (0, 3),
     "item_cost": (4096, 16384, 65536),
     "chunks_per_thread": (1, 3, 6, 12),
+    "unroll": (1, 2),
 }
 _lock = threading.Lock()
 

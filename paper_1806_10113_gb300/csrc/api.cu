@@ -149,7 +149,7 @@ struct Context {
 thread_local std::unique_ptr<Context> t_ctx;
 
 std::mutex g_tune_mu;
-tm_tuning g_default_tuning{0, 0, 0, 0, 0};
+tm_tuning g_default_tuning{0, 0, 0, 0, 0, 0};
 unsigned g_tuning_epoch = 0;   // bumped on every change; cached plans compare it
 
 int context(Context** out)
@@ -195,7 +195,7 @@ bool tuning_invalid(const tm_tuning& t)
     return (t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
            t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 ||
            t.item_cost > (1 << 20) || t.chunks_per_thread < 0 || t.chunks_per_thread > 64 ||
-           (t.fuse_finalize == 1 && t.chunks_per_thread != 1);
+           (t.fuse_finalize == 1 && t.chunks_per_thread != 1) || t.unroll < 0 || t.unroll > 2;
 }
 
 void free_plan(Plan& p)
@@ -244,6 +244,7 @@ int build_plan(const int32_t* h_offsets, int G, const tm_tuning& tune, Plan& p)
     if (rc != TM_OK) return rc;
     TM_CUDA(cudaGetDevice(&p.device));
     p.chunks_per_thread = tune.chunks_per_thread == 0 ? 1 : tune.chunks_per_thread;
+    p.unroll = tune.unroll == 0 ? 2 : tune.unroll;
     tmgpu::exhaustive_partition(p, p.device, tune.blocks_per_sm);
     std::vector<uint32_t> target;
     fused_tables(p, gp, target);
@@ -297,7 +298,7 @@ int tm_plan_create_tuned(const int32_t* h_offsets, int G, const tm_tuning* tunin
                          tm_plan** plan_out)
 {
     if (!plan_out) return TM_EINVAL;
-    tm_tuning tune{0, 0, 0, 0, 0};
+    tm_tuning tune{0, 0, 0, 0, 0, 0};
     if (tuning) tune = *tuning;
     std::unique_ptr<tm_plan> plan(new (std::nothrow) tm_plan());
     if (!plan) return TM_ENOMEM;
@@ -319,7 +320,7 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out)
 
 int tm_set_default_tuning(const tm_tuning* tuning)
 {
-    tm_tuning t{0, 0, 0, 0, 0};
+    tm_tuning t{0, 0, 0, 0, 0, 0};
     if (tuning) t = *tuning;
     if (tuning_invalid(t)) return TM_EINVAL;
     std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -572,8 +572,11 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
 
 // Depth-first walk over the D remaining prefix tasks (ascending in `rem`):
 // their orders in lexicographic order, so `walked` counts prefixes in rank
-// order.
-template <int D, bool SUM32>
+// order.  UNROLL: the level with three tasks left runs as straight-line code
+// (its six prefixes in one block, which the compiler can interleave); else
+// as a loop (less code: better when a batch mixes group sizes and so runs
+// many walk depths and both sum widths at once).
+template <int D, bool SUM32, bool UNROLL>
 __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict__ tbl,
                                     const Sfx& S, Acc& a)
 {
@@ -589,27 +592,33 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
         Eng s10 = step(step(st, t1.x, t1.y, t1.z), t0.x, t0.y, t0.z);
         leaves<SUM32>(s01.k, s01.d, S, a);
         leaves<SUM32>(s10.k, s10.d, S, a);
+    } else if constexpr (D == 3 && UNROLL) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int4 t = tbl[nib_get(rem, c)];
+            dfs<2, SUM32, UNROLL>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
+        }
     } else {
 #pragma unroll 1
         for (int c = 0; c < D; ++c) {
             int4 t = tbl[nib_get(rem, c)];
-            dfs<D - 1, SUM32>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
+            dfs<D - 1, SUM32, UNROLL>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
         }
     }
 }
 
-template <int PDMAX, bool SUM32>
+template <int PDMAX, bool SUM32, bool UNROLL>
 __device__ __forceinline__ void walk_prefixes(int pd, Eng st, uint64_t rem,
                                               const int4* __restrict__ tbl, const Sfx& S, Acc& a)
 {
     switch (pd) {
-    case 0: dfs<0, SUM32>(st, rem, tbl, S, a); break;
-    case 1: dfs<1, SUM32>(st, rem, tbl, S, a); break;
-    case 2: dfs<2, SUM32>(st, rem, tbl, S, a); break;
+    case 0: dfs<0, SUM32, UNROLL>(st, rem, tbl, S, a); break;
+    case 1: dfs<1, SUM32, UNROLL>(st, rem, tbl, S, a); break;
+    case 2: dfs<2, SUM32, UNROLL>(st, rem, tbl, S, a); break;
     default:
-        if constexpr (PDMAX >= 3) { if (pd == 3) dfs<3, SUM32>(st, rem, tbl, S, a); }
-        if constexpr (PDMAX >= 4) { if (pd == 4) dfs<4, SUM32>(st, rem, tbl, S, a); }
-        if constexpr (PDMAX >= 5) { if (pd == 5) dfs<5, SUM32>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 3) { if (pd == 3) dfs<3, SUM32, UNROLL>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 4) { if (pd == 4) dfs<4, SUM32, UNROLL>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 5) { if (pd == 5) dfs<5, SUM32, UNROLL>(st, rem, tbl, S, a); }
         break;
     }
 }
@@ -689,7 +698,7 @@ __device__ __noinline__ uint32_t item_rank(uint32_t at, int32_t v, uint32_t hd, 
 // The items whose first cost unit lies in [x0, x1), in order: walk them,
 // settle each against the thread's running best / worst, and report to the
 // group accumulators when the group changes and at the end.
-template <int PDMAX>
+template <int PDMAX, bool UNROLL>
 __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
                                            const GroupInfo* __restrict__ info,
                                            const int4* __restrict__ tbl,
@@ -767,8 +776,8 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
         uint32_t placed;
         Eng st = run_head(hd, f, P, gi.dinit, rem, placed, gt);
         a.start_item();
-        if (gi.sum32) walk_prefixes<PDMAX, true>(pd, st, rem, gt, S, a);
-        else walk_prefixes<PDMAX, false>(pd, st, rem, gt, S, a);
+        if (gi.sum32) walk_prefixes<PDMAX, true, UNROLL>(pd, st, rem, gt, S, a);
+        else walk_prefixes<PDMAX, false, UNROLL>(pd, st, rem, gt, S, a);
         // Settle the item against the running best / worst: every lane of a
         // warp gets here together, so this rank work does not diverge.  A
         // tie can only lower the rank if the item's first order ranks below
@@ -788,7 +797,7 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
     flush_final(a, sink, g);
 }
 
-template <int PDMAX>
+template <int PDMAX, bool UNROLL>
 __global__ void __launch_bounds__(kEnumBlock, TM_ENUM_MIN_BLOCKS)
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
@@ -796,7 +805,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
 {
     if (!next) {   // static split: one range per thread
         const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        enum_range<PDMAX>(gp, info, tbl, sub, G, t * per_thread, (t + 1) * per_thread, item_cost,
+        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, t * per_thread, (t + 1) * per_thread, item_cost,
                           sink);
         return;
     }
@@ -808,7 +817,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
         c0 = __shfl_sync(kFull, c0, 0);
         if (c0 >= nchunks) break;
         const uint64_t c = (uint64_t)c0 + lane;
-        enum_range<PDMAX>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
+        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
                           sink);
         __syncwarp();
     }
@@ -828,26 +837,33 @@ __global__ void finalize_kernel(const GroupInfo* __restrict__ info, const int4* 
     if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, tbl, acc, stats, status);
 }
 
-template <int PDMAX>
+template <int PDMAX, bool UNROLL>
 cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
 {
     uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
     const bool dyn = p.chunks_per_thread > 1;
-    enum_kernel<PDMAX><<<blocks, kEnumBlock, 0, stream>>>(
+    enum_kernel<PDMAX, UNROLL><<<blocks, kEnumBlock, 0, stream>>>(
         p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
         sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u);
     return cudaGetLastError();
 }
 
-int resident_threads(int pdmax, int device, int blocks_per_sm)
+template <int PDMAX, bool UNROLL>
+cudaError_t enum_occupancy(int* per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, enum_kernel<PDMAX, UNROLL>,
+                                                         kEnumBlock, 0);
+}
+
+int resident_threads(int pdmax, bool unroll, int device, int blocks_per_sm)
 {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaErrorInvalidValue;
     switch (pdmax) {
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enum_kernel<3>, kEnumBlock, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enum_kernel<4>, kEnumBlock, 0); break;
-    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enum_kernel<5>, kEnumBlock, 0); break;
+    case 3: e = unroll ? enum_occupancy<3, true>(&per_sm) : enum_occupancy<3, false>(&per_sm); break;
+    case 4: e = unroll ? enum_occupancy<4, true>(&per_sm) : enum_occupancy<4, false>(&per_sm); break;
+    case 5: e = unroll ? enum_occupancy<5, true>(&per_sm) : enum_occupancy<5, false>(&per_sm); break;
     default: break;
     }
     if (e != cudaSuccess || sms <= 0 || per_sm <= 0) return 152 * 512;
@@ -859,7 +875,7 @@ int resident_threads(int pdmax, int device, int blocks_per_sm)
 
 void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
 {
-    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, device, blocks_per_sm),
+    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, p.unroll == 1, device, blocks_per_sm),
                                           std::max<uint64_t>(p.total_items, 1));
     p.leaves_per_thread = std::max<uint64_t>(1, (p.total_leaves + threads - 1) / threads);
     p.threads = (uint32_t)((p.total_leaves + p.leaves_per_thread - 1) / p.leaves_per_thread);
@@ -917,10 +933,11 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
         if (p.ev_before &&
             (e = cudaEventRecordWithFlags(p.ev_before, stream, rec_flags)) != cudaSuccess)
             return e;
+        const bool unroll = p.unroll == 1;
         switch (p.pdmax) {
-        case 3: e = launch_enum<3>(p, sink, stream); break;
-        case 4: e = launch_enum<4>(p, sink, stream); break;
-        case 5: e = launch_enum<5>(p, sink, stream); break;
+        case 3: e = unroll ? launch_enum<3, true>(p, sink, stream) : launch_enum<3, false>(p, sink, stream); break;
+        case 4: e = unroll ? launch_enum<4, true>(p, sink, stream) : launch_enum<4, false>(p, sink, stream); break;
+        case 5: e = unroll ? launch_enum<5, true>(p, sink, stream) : launch_enum<5, false>(p, sink, stream); break;
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;

@@ -90,6 +90,7 @@ struct Plan {
     // (zeroed by the prep kernel), so threads that meet cheap orders take
     // more work.
     int chunks_per_thread = 1;
+    int unroll = 2;                       // 1: straight-line walk level (tm_tuning)
     uint64_t chunk = 0;                   // cost units per chunk (dynamic)
     uint32_t nchunks = 0;
     GroupPlan* d_gp = nullptr;            // [G + 1]

@@ -303,16 +303,17 @@ def tm_heuristic_batch_dev(d_tasks, d_offsets, G: int, d_devs, d_orders_out,
 
 class Tuning(ctypes.Structure):
     """tm_tuning: pdmax (3..5), fuse_finalize (1 fused, 2 separate), blocks_per_sm,
-    item_cost, chunks_per_thread (1 static split, 2..64 dynamic); 0 = default."""
+    item_cost, chunks_per_thread (1 static split, 2..64 dynamic), unroll (1
+    straight-line walk level, 2 loop); 0 = default."""
     _fields_ = [("pdmax", ctypes.c_int32), ("fuse_finalize", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("item_cost", ctypes.c_int32),
-                ("chunks_per_thread", ctypes.c_int32)]
+                ("chunks_per_thread", ctypes.c_int32), ("unroll", ctypes.c_int32)]
 
 
 def tm_set_default_tuning(pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0,
-                          item_cost: int = 0, chunks_per_thread: int = 0):
+                          item_cost: int = 0, chunks_per_thread: int = 0, unroll: int = 0):
     """Tuning for plans made by tm_plan_create and the host-pointer calls."""
-    t = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost, chunks_per_thread)
+    t = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost, chunks_per_thread, unroll)
     _check(lib().tm_set_default_tuning(ctypes.byref(t)), "tm_set_default_tuning")
 
 
@@ -320,11 +321,12 @@ class Plan:
     """Owns a tm_plan (exhaustive search over a fixed set of group sizes)."""
 
     def __init__(self, offsets, pdmax: int = 0, fuse_finalize: int = 0, blocks_per_sm: int = 0,
-                 item_cost: int = 0, chunks_per_thread: int = 0):
+                 item_cost: int = 0, chunks_per_thread: int = 0, unroll: int = 0):
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
         self.G = off.shape[0] - 1
         self.offsets = off
-        self.tuning = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost, chunks_per_thread)
+        self.tuning = Tuning(pdmax, fuse_finalize, blocks_per_sm, item_cost, chunks_per_thread,
+                             unroll)
         h = ctypes.c_void_p()
         _check(lib().tm_plan_create_tuned(_p(off), self.G, ctypes.byref(self.tuning),
                                           ctypes.byref(h)), "tm_plan_create_tuned")

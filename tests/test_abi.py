@@ -115,6 +115,18 @@ def test_plan_rejects_sizes_without_gpu(tm):
     assert e.value.code == -4
 
 
+def test_tuning_layout_and_rejection_on_host(tm):
+    import ctypes
+    assert ctypes.sizeof(tm.Tuning) == 24
+    for kw in ({"pdmax": 6}, {"pdmax": 2}, {"fuse_finalize": 3}, {"chunks_per_thread": 65},
+               {"fuse_finalize": 1, "chunks_per_thread": 2}, {"unroll": 3}, {"unroll": -1},
+               {"item_cost": (1 << 20) + 1}):
+        with pytest.raises(tm.TMError) as e:
+            tm.tm_set_default_tuning(**kw)
+        assert e.value.code == -1, kw
+    tm.tm_set_default_tuning()            # back to the library's defaults
+
+
 def test_server_config_rejected_on_host(tm):
     # argument checks run before any CUDA call
     for kw in ({"exact_max_n": 13}, {"exact_max_n": -1}, {"lanes": 9},

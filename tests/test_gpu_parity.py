@@ -268,7 +268,10 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
                                     dict(pdmax=3, blocks_per_sm=1), dict(item_cost=1),
                                     dict(pdmax=4, item_cost=5000), dict(chunks_per_thread=1),
                                     dict(pdmax=3, chunks_per_thread=64),
-                                    dict(chunks_per_thread=2, item_cost=1, blocks_per_sm=1)])
+                                    dict(chunks_per_thread=2, item_cost=1, blocks_per_sm=1),
+                                    dict(unroll=1), dict(pdmax=3, unroll=1),
+                                    dict(pdmax=5, unroll=1, chunks_per_thread=3),
+                                    dict(pdmax=4, unroll=2, item_cost=1)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
@@ -277,8 +280,10 @@ def test_every_tuning_gives_identical_results(tm, tuning):
     sizes = [rng.randint(1, 11) for _ in range(30)] + [4, 5, 9, 11]
     b = inputs.random_groups(23, sizes, hi=rng.choice([50, 4_000_000]))
     tie = inputs.random_groups(24, [9, 10, 8], lo=0, hi=3)        # many ties
-    b = inputs.make_batch([b.group(g) for g in range(b.G)] + [tie.group(g) for g in range(tie.G)],
-                          list(b.dma) + list(tie.dma))
+    big = inputs.random_groups(25, [9, 8], hi=60_000_000)        # 24 makespans overflow 32 bits
+    parts = (b, tie, big)
+    b = inputs.make_batch([p.group(g) for p in parts for g in range(p.G)],
+                          [int(x) for p in parts for x in p.dma])
     d_tasks = torch.from_numpy(b.tasks).to(dev)
     d_dma = torch.from_numpy(b.dma).to(dev)
     outs = []
