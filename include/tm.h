@@ -175,9 +175,10 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  (dynamic balance, for batches whose orders cost unevenly;
  *                  needs fuse_finalize != 1); 0: default 1
  *   unroll         1: the depth-first walk's level with three prefix tasks
- *                  left runs as straight-line code (faster on batches of one
- *                  group size); 2: as a loop (less code: faster on batches
- *                  that mix group sizes); 0: default 2 */
+ *                  left runs as straight-line code, and the orders' sum
+ *                  shares the FMA pipe (faster on batches of one group
+ *                  size); 2: as a loop (less code: faster on batches that
+ *                  mix group sizes); 0: default 2 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;

@@ -441,6 +441,7 @@ struct Sink {
     int32_t* status;
     const uint32_t* target;
     uint32_t* done;
+    uint32_t one;   // always 1 (the leaves' multiply-add sum)
 };
 
 __device__ __forceinline__ void flush(const Acc& a, unsigned long long* acc, int g)
@@ -511,6 +512,7 @@ __device__ __forceinline__ void flush_final(Acc& a, const Sink& k, int g)
 struct Sfx {
     int32_t b[24], c[24];
     int32_t alpha, bmax, cmax;
+    uint32_t one;   // 1, read from a kernel parameter (see leaves)
 };
 
 // Lexicographic rank of the first order that starts with the P tasks in
@@ -540,8 +542,14 @@ __device__ __forceinline__ int first_completion(int32_t k, int32_t d, int32_t v,
     return j;
 }
 
-// All 24 orders of S after a prefix with engine times (k, d).
-template <bool SUM32>
+// All 24 orders of S after a prefix with engine times (k, d).  FMA_SUM:
+// the 32-bit sum takes 18 of the 24 makespans as multiply-adds by S.one,
+// which the compiler cannot fold to plain adds, so they issue on the FMA
+// pipe; the maxima, the minima and the other six terms (three-input adds)
+// stay on the ALU pipe.  That balance pays where the walk's straight-line
+// level keeps the ALU pipe busy (5% on uniform batches) and costs 2% in the
+// looped walk, so the two go together.
+template <bool SUM32, bool FMA_SUM>
 __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& a)
 {
     const int32_t c0 = d + S.alpha;
@@ -553,8 +561,15 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
     for (int i = 0; i < 8; ++i) t8[i] = min3i(m[3 * i], m[3 * i + 1], m[3 * i + 2]);
     const int32_t pmin = min3i(min3i(t8[0], t8[1], t8[2]), min3i(t8[3], t8[4], t8[5]),
                                min(t8[6], t8[7]));
-    if (SUM32) {
+    if (SUM32 && FMA_SUM) {
         // the group's duration sum bounds every makespan, and 24 of them fit
+        uint32_t q[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 18; ++j) q[j & 3] = (uint32_t)m[j] * S.one + q[j & 3];
+        const uint32_t t0 = (uint32_t)m[18] + (uint32_t)m[19] + (uint32_t)m[20];
+        const uint32_t t1 = (uint32_t)m[21] + (uint32_t)m[22] + (uint32_t)m[23];
+        a.sum += ((q[0] + q[1]) + (q[2] + q[3])) + (t0 + t1);
+    } else if (SUM32) {
         uint32_t s8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -581,17 +596,17 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
                                     const Sfx& S, Acc& a)
 {
     if constexpr (D == 0) {
-        leaves<SUM32>(st.k, st.d, S, a);
+        leaves<SUM32, UNROLL>(st.k, st.d, S, a);
     } else if constexpr (D == 1) {
         int4 t = tbl[nib_get(rem, 0)];
         Eng s1 = step(st, t.x, t.y, t.z);
-        leaves<SUM32>(s1.k, s1.d, S, a);
+        leaves<SUM32, UNROLL>(s1.k, s1.d, S, a);
     } else if constexpr (D == 2) {
         int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)];
         Eng s01 = step(step(st, t0.x, t0.y, t0.z), t1.x, t1.y, t1.z);
         Eng s10 = step(step(st, t1.x, t1.y, t1.z), t0.x, t0.y, t0.z);
-        leaves<SUM32>(s01.k, s01.d, S, a);
-        leaves<SUM32>(s10.k, s10.d, S, a);
+        leaves<SUM32, UNROLL>(s01.k, s01.d, S, a);
+        leaves<SUM32, UNROLL>(s10.k, s10.d, S, a);
     } else if constexpr (D == 3 && UNROLL) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -714,6 +729,7 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
     Acc a;
     a.reset();
     Sfx S;
+    S.one = sink.one;
     GroupInfo gi;
     const int4* gt = tbl;
     uint32_t gbase = 0, gend = 0, heads = 1, cur = kFull;
@@ -923,7 +939,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
-        Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done};
+        Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done, 1u};
         // Under stream capture, an external record becomes an event-record
         // node of the graph (a plain record would only order the capture).
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
