@@ -585,6 +585,16 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
     a.walked += 1;
 }
 
+// The last two prefix positions, holding tasks x < y: orders (x, y), (y, x).
+template <bool SUM32, bool FMA_SUM>
+__device__ __forceinline__ void last_two(Eng st, int4 x, int4 y, const Sfx& S, Acc& a)
+{
+    const Eng sxy = step(step(st, x.x, x.y, x.z), y.x, y.y, y.z);
+    const Eng syx = step(step(st, y.x, y.y, y.z), x.x, x.y, x.z);
+    leaves<SUM32, FMA_SUM>(sxy.k, sxy.d, S, a);
+    leaves<SUM32, FMA_SUM>(syx.k, syx.d, S, a);
+}
+
 // Depth-first walk over the D remaining prefix tasks (ascending in `rem`):
 // their orders in lexicographic order, so `walked` counts prefixes in rank
 // order.  UNROLL: the level with three tasks left runs as straight-line code
@@ -602,17 +612,14 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
         Eng s1 = step(st, t.x, t.y, t.z);
         leaves<SUM32, UNROLL>(s1.k, s1.d, S, a);
     } else if constexpr (D == 2) {
-        int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)];
-        Eng s01 = step(step(st, t0.x, t0.y, t0.z), t1.x, t1.y, t1.z);
-        Eng s10 = step(step(st, t1.x, t1.y, t1.z), t0.x, t0.y, t0.z);
-        leaves<SUM32, UNROLL>(s01.k, s01.d, S, a);
-        leaves<SUM32, UNROLL>(s10.k, s10.d, S, a);
+        last_two<SUM32, UNROLL>(st, tbl[nib_get(rem, 0)], tbl[nib_get(rem, 1)], S, a);
     } else if constexpr (D == 3 && UNROLL) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int4 t = tbl[nib_get(rem, c)];
-            dfs<2, SUM32, UNROLL>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
-        }
+        // the three tasks' rows loaded once; their six orders in
+        // lexicographic order (the list is ascending)
+        const int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)], t2 = tbl[nib_get(rem, 2)];
+        last_two<SUM32, UNROLL>(step(st, t0.x, t0.y, t0.z), t1, t2, S, a);
+        last_two<SUM32, UNROLL>(step(st, t1.x, t1.y, t1.z), t0, t2, S, a);
+        last_two<SUM32, UNROLL>(step(st, t2.x, t2.y, t2.z), t0, t1, S, a);
     } else {
 #pragma unroll 1
         for (int c = 0; c < D; ++c) {
