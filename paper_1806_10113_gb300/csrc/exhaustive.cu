@@ -142,6 +142,7 @@ __device__ __noinline__ void finalize_group_warp(int g, const GroupInfo& gi,
     const int lane = threadIdx.x & 31;
     unsigned long long* A = acc + (size_t)kAccStride * g;
     unsigned long long mk = 0, xk = 0, sum = 0;
+    const int4 row = lane < gi.n ? tbl[gi.off + lane] : make_int4(0, 0, 0, 0);
     if (lane == 0) {
         mk = __ldcg(A);
         xk = __ldcg(A + 1);
@@ -158,10 +159,12 @@ __device__ __noinline__ void finalize_group_warp(int g, const GroupInfo& gi,
     const uint64_t nf = factorial_u64(n);
     uint8_t order[16];
     for (int i = 0; i < 16; ++i) order[i] = 0xFF;
-    bool good = brank < nf && wrank < nf;
-    if (lane < 2 && good)
-        good = makespan_of_rank(tbl + gi.off, n, gi.dinit, lane == 0 ? brank : wrank, order) ==
-               (lane == 0 ? best : worst);
+    bool good = brank < nf && wrank < nf;   // the same on every lane
+    if (good) {
+        const uint32_t r = lane == 0 ? brank : lane == 1 ? wrank : 0u;
+        const int32_t ms = makespan_of_rank_warp(row, n, gi.dinit, r, order);
+        if (lane < 2) good = ms == (lane == 0 ? best : worst);
+    }
     const bool ok = __all_sync(kFull, good);
     uint32_t packed[4];
 #pragma unroll

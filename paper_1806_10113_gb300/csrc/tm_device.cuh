@@ -124,4 +124,27 @@ __device__ inline int32_t makespan_of_rank(const int4* tbl, int n, int32_t dinit
     return s.d;
 }
 
+// The same for a whole warp, each lane with its own rank, taking the task
+// rows from the lanes instead of memory: lane j holds task j's row
+// (j < n).  n must be the same on every lane and every lane must call.
+__device__ inline int32_t makespan_of_rank_warp(int4 row, int n, int32_t dinit, uint32_t rank,
+                                                uint8_t* order_out)
+{
+    uint64_t list = nib_identity(n);
+    Eng s{0, 0, dinit};
+    for (int i = 0; i < n; ++i) {
+        const int k = n - 1 - i;
+        const uint32_t c = min(div_fact(rank, k), (uint32_t)k);
+        rank -= c * (uint32_t)factorial_u64(k);
+        const int e = nib_get(list, (int)c);
+        list = nib_remove(list, (int)c);
+        if (order_out) order_out[i] = (uint8_t)e;
+        const int32_t h = __shfl_sync(0xFFFFFFFFu, row.x, e);
+        const int32_t kk = __shfl_sync(0xFFFFFFFFu, row.y, e);
+        const int32_t dd = __shfl_sync(0xFFFFFFFFu, row.z, e);
+        s = step(s, h, kk, dd);
+    }
+    return s.d;
+}
+
 }  // namespace tmgpu
