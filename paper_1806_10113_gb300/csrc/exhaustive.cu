@@ -175,7 +175,7 @@ __device__ __noinline__ void finalize_group_warp(int g, const GroupInfo& gi,
     }
     if (lane != 0) return;
     if (!ok) {  // the reduction disagrees with a re-evaluation: never expected
-        if (status) status[g] = TM_ECUDA;
+        if (status) status[gi.user] = TM_ECUDA;
         return;
     }
     tm_stats st;
@@ -189,8 +189,8 @@ __device__ __noinline__ void finalize_group_warp(int g, const GroupInfo& gi,
         st.best_order[i] = order[i];
         st.worst_order[i] = (uint8_t)(packed[i / 4] >> (8 * (i % 4)));
     }
-    stats[g] = st;
-    if (status) status[g] = 0;
+    stats[gi.user] = st;
+    if (status) status[gi.user] = 0;
 }
 
 // Turns a group's three reduction words into tm_stats (one thread) and
@@ -221,11 +221,11 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
     ok = ok && makespan_of_rank(t, n, gi.dinit, (uint32_t)st.worst_rank, st.worst_order) ==
                    st.worst;
     if (!ok) {
-        if (status) status[g] = TM_ECUDA;
+        if (status) status[gi.user] = TM_ECUDA;
         return;
     }
-    stats[g] = st;
-    if (status) status[g] = 0;
+    stats[gi.user] = st;
+    if (status) status[gi.user] = 0;
 }
 
 // ---- prep: validation, padded task table, suffix tables -------------------
@@ -256,17 +256,18 @@ struct PrepArgs {
 };
 
 // Validation, GroupInfo, padded task table (and n <= 3 groups finished
-// outright) for group g, by one full warp (lane i holds task i); the tasks
-// also land in s_task.  Returns the group's status and HtD sum.
-__device__ __forceinline__ int prep_group(const PrepArgs& a, int g, int lane,
+// outright) for the group at work position w, by one full warp (lane i
+// holds task i); the tasks also land in s_task.  Returns the group's status
+// and HtD sum.
+__device__ __forceinline__ int prep_group(const PrepArgs& a, int w, int lane,
                                           int4* __restrict__ s_task, int32_t* hs_out)
 {
     const GroupPlan* __restrict__ gp = a.gp;
-    const int off = gp[g].off;
-    const int n = gp[g + 1].off - off;
-    const int dma = a.devs[g].dma_engines;
+    const int off = gp[w].off, uoff = gp[w].uoff, user = gp[w].group;
+    const int n = gp[w + 1].off - off;
+    const int dma = a.devs[user].dma_engines;
     const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
-    tm_task t = mine ? a.tasks[off + lane] : tm_task{0, 0, 0};
+    tm_task t = mine ? a.tasks[uoff + lane] : tm_task{0, 0, 0};
     const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
     unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
 #pragma unroll
@@ -289,14 +290,15 @@ __device__ __forceinline__ int prep_group(const PrepArgs& a, int g, int lane,
         gi.dinit = dma == 1 ? hs : 0;
         gi.status = status;
         gi.sum32 = tot * 24u < (1ull << 32) ? 1u : 0u;
-        gi.pad0 = gi.pad1 = 0;
-        a.info[g] = gi;
-        if (status != 0 && a.status) a.status[g] = status;
+        gi.user = user;
+        gi.pad1 = 0;
+        a.info[w] = gi;
+        if (status != 0 && a.status) a.status[user] = status;
     }
     if (status == 0 && n <= 3) {       // at most 6 orders: finish here
         __syncwarp();
-        small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + g);
-        if (lane == 0 && a.status) a.status[g] = 0;
+        small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + user);
+        if (lane == 0 && a.status) a.status[user] = 0;
     }
     *hs_out = hs;
     return status;
@@ -364,13 +366,14 @@ __device__ __forceinline__ void prep_tables(const PrepArgs& a, int g, int n, int
     }
 }
 
-// Heuristic warp hg (blocks or warps after the table work), if requested.
-__device__ __forceinline__ void prep_heuristic(const PrepArgs& a, int hg, int lane)
+// Heuristic warp for the group at work position w (blocks after the table
+// work), if requested.
+__device__ __forceinline__ void prep_heuristic(const PrepArgs& a, int w, int lane)
 {
-    if (!a.orders || hg >= a.G) return;
-    const int hoff = a.gp[hg].off;
-    heur::heuristic_group(a.tasks, hoff, a.gp[hg + 1].off - hoff, a.devs[hg].dma_engines, hg, lane,
-                          a.orders, a.makespans, nullptr);
+    if (!a.orders || w >= a.G) return;
+    const int user = a.gp[w].group;
+    heur::heuristic_group(a.tasks, a.gp[w].uoff, a.gp[w + 1].off - a.gp[w].off,
+                          a.devs[user].dma_engines, user, lane, a.orders, a.makespans, nullptr);
 }
 
 // Block per group (groups with many 4-subsets).  Blocks G.. run the

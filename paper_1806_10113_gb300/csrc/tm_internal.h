@@ -40,11 +40,18 @@ struct GroupInfo {
     int32_t hs;       // sum of HtD of the group
     int32_t status;   // 0 or a tm_status code
     uint32_t sum32;   // 1 if 24 makespans of this group always fit in 32 bits
-    int32_t pad0, pad1;
+    int32_t user;     // the caller's index of the group (outputs go there)
+    int32_t pad1;
 };
 
 // Per-group work layout computed on the host from the group sizes alone.
-// Entry G holds the totals.
+// Groups are laid out in WORK ORDER: by size, largest first, stable (so a
+// batch of one size keeps the caller's order).  The threads and warps that
+// run at one time then mostly hold groups of one size and walk one code
+// path, which keeps the instruction cache warm on mixed batches.  Every
+// per-group array of the plan (GroupInfo, the padded task table, suffix
+// tables, reduction words) is in work order; inputs are read and outputs
+// written at the caller's index.  Entry G holds the totals.
 struct GroupPlan {
     uint64_t cost_base;   // first cost unit of the group: each work item of a
                           // group with n >= 4 costs its orders plus a fixed
@@ -52,7 +59,9 @@ struct GroupPlan {
     uint32_t item_base;   // first work item
     uint32_t unit_base;   // first thread of the prep / suffix-table kernel
     uint32_t sub_base;    // first suffix-table entry
-    int32_t off;          // first task
+    int32_t off;          // first task in the plan's task table (work order)
+    int32_t uoff;         // first task in the caller's task array
+    int32_t group;        // the caller's index of the group
 };
 
 // The last four positions of an order hold a 4-task set S.  Because the
@@ -120,16 +129,32 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
                           GroupPlan* gp, Plan* totals)
 {
     if (!offsets || G < 0 || offsets[0] != 0 || pdmax < 2 || pdmax > 5) return TM_EINVAL;
-    uint64_t cost = 0, items = 0, units = 0, subs = 0;
+    // work order: a counting sort by size, largest first, stable
+    uint32_t start[TM_MAX_EXHAUSTIVE + 1] = {};
     for (int g = 0; g < G; ++g) {
-        int n = offsets[g + 1] - offsets[g];
+        const int n = offsets[g + 1] - offsets[g];
         if (n < 1) return TM_EINVAL;
         if (n > TM_MAX_EXHAUSTIVE) return TM_ETOOBIG;
-        gp[g].cost_base = cost;
-        gp[g].item_base = (uint32_t)items;
-        gp[g].unit_base = (uint32_t)units;
-        gp[g].sub_base = (uint32_t)subs;
-        gp[g].off = offsets[g];
+        ++start[n];
+    }
+    for (uint32_t nn = TM_MAX_EXHAUSTIVE, at = 0; nn >= 1; --nn) {
+        const uint32_t c = start[nn];
+        start[nn] = at;
+        at += c;
+    }
+    for (int g = 0; g < G; ++g) gp[start[offsets[g + 1] - offsets[g]]++].group = g;
+    uint64_t cost = 0, items = 0, units = 0, subs = 0;
+    int32_t toff = 0;
+    for (int w = 0; w < G; ++w) {
+        const int g = gp[w].group;
+        const int n = offsets[g + 1] - offsets[g];
+        gp[w].cost_base = cost;
+        gp[w].item_base = (uint32_t)items;
+        gp[w].unit_base = (uint32_t)units;
+        gp[w].sub_base = (uint32_t)subs;
+        gp[w].off = toff;
+        gp[w].uoff = offsets[g];
+        toff += n;
         uint32_t c4 = choose4(n);
         units += c4 > 0 ? c4 : 1;
         subs += c4;
@@ -146,6 +171,8 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
     gp[G].unit_base = (uint32_t)units;
     gp[G].sub_base = (uint32_t)subs;
     gp[G].off = offsets[G];
+    gp[G].uoff = offsets[G];
+    gp[G].group = G;
     totals->G = G;
     totals->T = offsets[G];
     totals->pdmax = pdmax;
