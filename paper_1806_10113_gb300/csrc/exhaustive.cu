@@ -232,12 +232,14 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 
 // One block per group (128 threads, or 512 when the batch has groups with
 // many 4-subsets; a warp per group measured slower: its largest groups'
-// tables then run on 32 threads).  Warp 0 loads and validates the group
-// (lane i holds task i) and writes its GroupInfo and padded task table (and
-// finishes groups of n <= 3 outright); then the block's threads stride over
-// the group's (4-subset, order) pairs and tabulate alpha / beta / gamma.
-// When the heuristic is requested, blocks G.. of the same launch run it, one
-// warp per group.
+// tables then run on 32 threads).  Every warp loads the group itself (lane
+// i holds task i), so no warp waits at a block barrier: warp 0 validates it
+// and writes its GroupInfo and padded task table (and finishes groups of
+// n <= 3 outright) while all warps stride over the group's 4-subsets and
+// tabulate alpha / beta / gamma, taking the subset's tasks from the lanes
+// by shuffle.  A group that fails validation gets tables too, which
+// nothing reads.  When the heuristic is requested, blocks G.. of the same
+// launch run it, one warp per group.
 constexpr int kPrepMaxThreads = 512;
 
 struct PrepArgs {
@@ -256,18 +258,13 @@ struct PrepArgs {
 };
 
 // Validation, GroupInfo, padded task table (and n <= 3 groups finished
-// outright) for the group at work position w, by one full warp (lane i
-// holds task i); the tasks also land in s_task.  Returns the group's status
-// and HtD sum.
-__device__ __forceinline__ int prep_group(const PrepArgs& a, int w, int lane,
-                                          int4* __restrict__ s_task, int32_t* hs_out)
+// outright) for the group at work position w, by one full warp: lane i
+// holds task i in t (lanes >= n hold zeros).
+__device__ __forceinline__ void prep_group(const PrepArgs& a, int w, int lane, int off, int n,
+                                           int user, const tm_task& t)
 {
-    const GroupPlan* __restrict__ gp = a.gp;
-    const int off = gp[w].off, uoff = gp[w].uoff, user = gp[w].group;
-    const int n = gp[w + 1].off - off;
     const int dma = a.devs[user].dma_engines;
-    const bool mine = lane < n && lane < TM_MAX_EXHAUSTIVE;
-    tm_task t = mine ? a.tasks[uoff + lane] : tm_task{0, 0, 0};
+    const bool mine = lane < n;
     const bool neg = mine && (t.htd < 0 || t.k < 0 || t.dth < 0);
     unsigned long long tot = mine ? (unsigned long long)((int64_t)t.htd + t.k + t.dth) : 0ull;
 #pragma unroll
@@ -278,10 +275,7 @@ __device__ __forceinline__ int prep_group(const PrepArgs& a, int w, int lane,
     if (n < 1 || n > TM_MAX_EXHAUSTIVE || (dma != 1 && dma != 2)) status = TM_EINVAL;
     else if (__ballot_sync(kFull, neg)) status = TM_ENEG;
     else if (tot > (unsigned long long)INT32_MAX) status = TM_EOVERFLOW;
-    if (mine) {
-        s_task[lane] = make_int4(t.htd, t.k, t.dth, 0);
-        if (status == 0) a.tbl[off + lane] = s_task[lane];
-    }
+    if (mine && status == 0) a.tbl[off + lane] = make_int4(t.htd, t.k, t.dth, 0);
     if (lane == 0) {
         GroupInfo gi;
         gi.off = off;
@@ -300,35 +294,40 @@ __device__ __forceinline__ int prep_group(const PrepArgs& a, int w, int lane,
         small_group_stats(a.tbl + off, n, dma == 1 ? hs : 0, lane, a.stats + user);
         if (lane == 0 && a.status) a.status[user] = 0;
     }
-    *hs_out = hs;
-    return status;
 }
 
-// The suffix tables of group g (n >= 4), one 4-subset S per thread: S =
-// first, first + stride, ...; tasks from s_task.  The 24 orders of S are
-// walked depth-first in lexicographic order (prefix steps shared), and the
-// 208-byte table is written with 16-byte stores.
+// The suffix tables of the group at work position w (n >= 4) by one warp:
+// 4-subsets S = first + lane, first + lane + stride, ...; lane i holds task
+// i in `row`, hs is the group's HtD sum.  The 24 orders of S are walked
+// depth-first in lexicographic order (prefix steps shared) and the 208-byte
+// table goes out in 16-byte stores as it fills.
 //   beta[j]:  the order's makespan when only the K engine (free at 0) enters
 //             S: HtD and DtH start unconstrained, so the first task's kernel
 //             starts at 0 and its DtH right after it;
 //   gamma[j]: when only the HtD engine enters S, free at hS = hs - (S's HtD
 //             sum): the first task's kernel and DtH follow its HtD directly.
 // Every value is a path length within the group, so int32 holds it.
-__device__ __forceinline__ void prep_tables(const PrepArgs& a, int g, int n, int32_t hs,
-                                            const int4* __restrict__ s_task, uint32_t first,
-                                            uint32_t stride)
+__device__ __forceinline__ void prep_tables(const PrepArgs& a, int w, int n, int32_t hs,
+                                            int4 row, int lane, uint32_t first, uint32_t stride)
 {
-    SuffixTab* out = a.sub + a.gp[g].sub_base;
+    SuffixTab* out = a.sub + a.gp[w].sub_base;
     const uint32_t subsets = choose4(n);
-    for (uint32_t sidx = first; sidx < subsets; sidx += stride) {
-        const uint32_t mask = c_subsets.m[sidx];
+    for (uint32_t base = first; base < subsets; base += stride) {   // the same on every lane
+        const uint32_t sidx = base + (uint32_t)lane;
+        const bool live = sidx < subsets;
+        const uint32_t mask = live ? c_subsets.m[sidx] : 0xFu;
         int4 t[4];
+#pragma unroll
         for (int q = 0, m = (int)mask; q < 4; ++q) {
-            t[q] = s_task[__ffs(m) - 1];
+            const int e = __ffs(m) - 1;
+            t[q] = make_int4(__shfl_sync(kFull, row.x, e), __shfl_sync(kFull, row.y, e),
+                             __shfl_sync(kFull, row.z, e), 0);
             m &= m - 1;
         }
+        if (!live) continue;
         const int32_t hS = hs - t[0].x - t[1].x - t[2].x - t[3].x;
-        int32_t beta[24], gamma[24];
+        int4* dst = reinterpret_cast<int4*>(out + sidx);
+        int32_t bq[4], gq[4];
         int j = 0;
 #pragma unroll
         for (int p0 = 0; p0 < 4; ++p0) {
@@ -350,17 +349,15 @@ __device__ __forceinline__ void prep_tables(const PrepArgs& a, int g, int n, int
                     const int32_t bk4 = bk3 + D.y, bd4 = max(bd3, bk4) + D.z;
                     const int32_t gh3 = gh2 + C.x, gk3 = max(gk2, gh3) + C.y, gd3 = max(gd2, gk3) + C.z;
                     const int32_t gh4 = gh3 + D.x, gk4 = max(gk3, gh4) + D.y, gd4 = max(gd3, gk4) + D.z;
-                    beta[j] = bd4;
-                    gamma[j] = gd4;
+                    bq[j & 3] = bd4;
+                    gq[j & 3] = gd4;
+                    if ((j & 3) == 3) {
+                        dst[j >> 2] = make_int4(bq[0], bq[1], bq[2], bq[3]);
+                        dst[6 + (j >> 2)] = make_int4(gq[0], gq[1], gq[2], gq[3]);
+                    }
                     ++j;
                 }
             }
-        }
-        int4* dst = reinterpret_cast<int4*>(out + sidx);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            dst[q] = make_int4(beta[4 * q], beta[4 * q + 1], beta[4 * q + 2], beta[4 * q + 3]);
-            dst[6 + q] = make_int4(gamma[4 * q], gamma[4 * q + 1], gamma[4 * q + 2], gamma[4 * q + 3]);
         }
         dst[12] = make_int4(t[0].z + t[1].z + t[2].z + t[3].z, (int)mask, 0, 0);
     }
@@ -385,19 +382,17 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
         prep_heuristic(a, (blockIdx.x - a.G) * (blockDim.x / 32) + warp, lane);
         return;
     }
-    const int g = blockIdx.x;
-    __shared__ int4 s_task[TM_MAX_EXHAUSTIVE];
-    __shared__ int s_status, s_hs;
-    if (a.next && g == 0 && tid == 0) *a.next = 0;
-    if (warp == 0) {
-        int32_t hs;
-        const int st = prep_group(a, g, lane, s_task, &hs);
-        if (lane == 0) { s_status = st; s_hs = hs; }
-    }
-    __syncthreads();
-    const int n = a.gp[g + 1].off - a.gp[g].off;
-    if (s_status != 0 || n < 4) return;
-    prep_tables(a, g, n, s_hs, s_task, tid, blockDim.x);
+    const int w = blockIdx.x;
+    if (a.next && w == 0 && tid == 0) *a.next = 0;
+    const GroupPlan* __restrict__ gp = a.gp;
+    const int off = gp[w].off, uoff = gp[w].uoff, user = gp[w].group;
+    const int n = gp[w + 1].off - off;     // 1..TM_MAX_EXHAUSTIVE: the plan checked it
+    const tm_task t = lane < n ? a.tasks[uoff + lane] : tm_task{0, 0, 0};
+    if (warp == 0) prep_group(a, w, lane, off, n, user, t);
+    if (n < 4) return;
+    const int32_t hs = (int32_t)__reduce_add_sync(kFull, lane < n ? (uint32_t)t.htd : 0u);
+    prep_tables(a, w, n, hs, make_int4(t.htd, t.k, t.dth, 0), lane, (uint32_t)warp * 32u,
+                blockDim.x);
 }
 
 // ---- enumeration ----------------------------------------------------------
