@@ -850,15 +850,22 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
 // ---- finalize ---------------------------------------------------------------
 
 // Separate finalize (when the plan has no completion counters): one warp
-// per group of n >= 4 tasks; the prep kernel handled the others.
-__global__ void finalize_kernel(const GroupInfo* __restrict__ info, const int4* __restrict__ tbl,
-                                int G, unsigned long long* __restrict__ acc,
-                                tm_stats* __restrict__ stats, int32_t* __restrict__ status)
+// per group of n >= 4 tasks in blocks [0, fin_blocks); the prep kernel
+// handled the others.  Blocks fin_blocks.. run the heuristic, a warp per
+// group, when the launch carries it (a.orders set): it needs nothing from
+// the enumeration, and here it runs beside the finalize warps instead of
+// delaying the enumeration's start.
+__global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc, int fin_blocks)
 {
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x >= (unsigned)fin_blocks) {
+        prep_heuristic(a, (blockIdx.x - fin_blocks) * (blockDim.x / 32) + (threadIdx.x >> 5), lane);
+        return;
+    }
     const int g = (int)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (g >= G) return;
-    const GroupInfo gi = info[g];
-    if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, tbl, acc, stats, status);
+    if (g >= a.G) return;
+    const GroupInfo gi = a.info[g];
+    if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, a.tbl, acc, a.stats, a.status);
 }
 
 template <int PDMAX, bool UNROLL>
@@ -942,8 +949,13 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     // a block per group: 512 threads when the batch's groups have many
     // (subset, order) pairs (n >= 9: >= 3,024), else 128
     const int prep_threads = p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128;
-    const int heur_blocks = d_orders ? (p.G + prep_threads / 32 - 1) / (prep_threads / 32) : 0;
-    prep_kernel<<<p.G + heur_blocks, prep_threads, 0, stream>>>(pa);
+    // the heuristic runs in the finalize launch when there is one, else here
+    const bool heur_late = d_orders && p.total_items > 0 && !p.d_done;
+    PrepArgs pp = pa;
+    if (heur_late) pp.orders = pp.makespans = nullptr;
+    const int heur_blocks =
+        pp.orders ? (p.G + prep_threads / 32 - 1) / (prep_threads / 32) : 0;
+    prep_kernel<<<p.G + heur_blocks, prep_threads, 0, stream>>>(pp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
@@ -969,8 +981,9 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
             (e = cudaEventRecordWithFlags(p.ev_after, stream, rec_flags)) != cudaSuccess)
             return e;
         if (!p.d_done) {
-            finalize_kernel<<<(p.G * 32 + 255) / 256, 256, 0, stream>>>(p.d_info, p.d_tbl, p.G,
-                                                                        p.d_acc, d_stats, d_status);
+            const int fin_blocks = (p.G * 32 + 255) / 256;
+            const int late = heur_late ? (p.G + 7) / 8 : 0;
+            finalize_kernel<<<fin_blocks + late, 256, 0, stream>>>(pa, p.d_acc, fin_blocks);
             e = cudaGetLastError();
         }
     }
