@@ -124,6 +124,7 @@ def test_tuning_layout_and_rejection_on_host(tm):
         with pytest.raises(tm.TMError) as e:
             tm.tm_set_default_tuning(**kw)
         assert e.value.code == -1, kw
+    tm.tm_set_default_tuning(fuse_finalize=1)   # chunks_per_thread 0 means 1: allowed
     tm.tm_set_default_tuning()            # back to the library's defaults
 
 

@@ -234,6 +234,38 @@ def test_schedule_batch_matches_oracle_on_ragged_groups(tm):
     assert st2.tobytes() == st.tobytes() and (orders2 == orders).all()
 
 
+@pytest.mark.parametrize("sizes,tuning", [
+    ([6, 2, 9, 1, 5, 3, 8, 4], dict(fuse_finalize=2)),     # heuristic beside the finalize warps
+    ([6, 2, 9, 1, 5, 3, 8, 4], dict(fuse_finalize=1)),     # no finalize launch: heuristic in prep
+    ([3, 1, 2, 3, 2], dict(fuse_finalize=2)),              # no group of 4+: no enumeration at all
+])
+def test_heuristic_and_search_in_every_launch_layout(tm, sizes, tuning):
+    """The heuristic's warps run in the finalize launch, or in the prep
+    launch when there is no finalize launch; groups are laid out by size.
+    Every output must land at the caller's index either way."""
+    import torch
+    dev = torch.device("cuda")
+    b = inputs.random_groups(61, sizes, hi=4_000_000)
+    plan = tm.Plan(b.offsets, **tuning)
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(b.G * 72, dtype=torch.uint8, device=dev)
+    d_orders = torch.full((b.tasks.shape[0],), -1, dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(b.G, dtype=torch.int32, device=dev)
+    d_status = torch.full((b.G,), 99, dtype=torch.int32, device=dev)
+    tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status)
+    torch.cuda.synchronize()
+    assert (d_status.cpu().numpy() == 0).all()
+    got = tm.stats_to_dicts(d_stats.cpu().numpy().view(tm.STATS_DTYPE), b.sizes())
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(got[g], ref[g], g)
+    assert (d_orders.cpu().numpy() == ref_orders).all()
+    assert (d_ms.cpu().numpy().astype(np.int64) == ref_ms).all()
+    plan.close()
+
+
 def test_schedule_batch_dev_reports_invalid_groups(tm):
     import torch
     dev = torch.device("cuda")
