@@ -100,29 +100,30 @@ struct DevBuf {
 };
 
 // Page-locked host staging, grown on demand (contents not kept).
+// Page-locked host memory mapped into the device's address space: kernels
+// read and write it in place through `d` (over NVLink-C2C on GB300).
 struct PinBuf {
     void* p = nullptr;
+    void* d = nullptr;
     size_t cap = 0;
     bool ensure(size_t bytes)
     {
         if (bytes <= cap) return true;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
+        release();
         const size_t want = std::max<size_t>(bytes, 4096);
-        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) { p = nullptr; return false; }
+        if (cudaHostAlloc(&p, want, cudaHostAllocMapped) != cudaSuccess) { p = nullptr; return false; }
+        if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) { release(); return false; }
         cap = want;
         return true;
     }
-    void release() { if (p) cudaFreeHost(p); p = nullptr; cap = 0; }
+    void release() { if (p) cudaFreeHost(p); p = nullptr; d = nullptr; cap = 0; }
 };
 
 struct Context {
     int device = -1;
     cudaStream_t stream = nullptr;
     DevBuf tasks, offsets, devs, orders, out, stats, status;
-    DevBuf blk_in, blk_out;          // packed inputs / outputs of the exhaustive host call
-    PinBuf pin_in, pin_out;
+    PinBuf pin_in, pin_out;          // mapped inputs / outputs of the exhaustive host call
     tm_plan* plan = nullptr;
     std::vector<int32_t> plan_offsets;
     unsigned plan_epoch = 0;
@@ -131,7 +132,7 @@ struct Context {
         if (plan) tm_plan_destroy(plan);
         plan = nullptr;
         plan_offsets.clear();
-        for (DevBuf* b : {&tasks, &offsets, &devs, &orders, &out, &stats, &status, &blk_in, &blk_out})
+        for (DevBuf* b : {&tasks, &offsets, &devs, &orders, &out, &stats, &status})
             b->release();
         pin_in.release();
         pin_out.release();
@@ -528,21 +529,20 @@ int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const t
     }
     const int T = offsets[G];
     cudaStream_t s = c->stream;
-    // one packed H2D copy (tasks, device models) and one packed D2H copy
-    // (stats, status, makespans, orders), both through page-locked staging
+    // Inputs (tasks, device models) and outputs (stats, status, makespans,
+    // orders) live in one mapped page-locked block each: the prep kernel
+    // reads the inputs in place and the finalize kernel writes the results
+    // in place, so the call issues no copy at all.
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t i_devs = al((size_t)T * sizeof(tm_task)), in_bytes = i_devs + (size_t)G * 4;
     const size_t o_status = al((size_t)G * sizeof(tm_stats)), o_ms = o_status + al((size_t)G * 4),
                  o_orders = o_ms + al((size_t)G * 4), out_bytes = o_orders + (size_t)T * 4;
-    if (!c->blk_in.ensure(in_bytes) || !c->blk_out.ensure(out_bytes) ||
-        !c->pin_in.ensure(in_bytes) || !c->pin_out.ensure(out_bytes))
-        return TM_ENOMEM;
+    if (!c->pin_in.ensure(in_bytes) || !c->pin_out.ensure(out_bytes)) return TM_ENOMEM;
     unsigned char* hin = static_cast<unsigned char*>(c->pin_in.p);
     std::memcpy(hin, tasks, (size_t)T * sizeof(tm_task));
     std::memcpy(hin + i_devs, devs, (size_t)G * 4);
-    TM_CUDA(cudaMemcpyAsync(c->blk_in.p, hin, in_bytes, cudaMemcpyHostToDevice, s));
-    unsigned char* din = c->blk_in.as<unsigned char>();
-    unsigned char* dout = c->blk_out.as<unsigned char>();
+    unsigned char* din = static_cast<unsigned char*>(c->pin_in.d);
+    unsigned char* dout = static_cast<unsigned char*>(c->pin_out.d);
     const tm_task* d_tasks = reinterpret_cast<const tm_task*>(din);
     const tm_device* d_devs = reinterpret_cast<const tm_device*>(din + i_devs);
     tm_stats* d_stats = reinterpret_cast<tm_stats*>(dout);
@@ -554,8 +554,6 @@ int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const t
     else
         rc = tm_exhaustive_batch_dev(c->plan, d_tasks, d_devs, d_stats, d_status, s);
     if (rc != TM_OK) return rc;
-    const size_t copy_bytes = orders_out ? out_bytes : o_ms;
-    TM_CUDA(cudaMemcpyAsync(c->pin_out.p, dout, copy_bytes, cudaMemcpyDeviceToHost, s));
     TM_CUDA(cudaStreamSynchronize(s));
     const unsigned char* hout = static_cast<const unsigned char*>(c->pin_out.p);
     if ((rc = first_error(reinterpret_cast<const int32_t*>(hout + o_status), G)) != TM_OK) return rc;
