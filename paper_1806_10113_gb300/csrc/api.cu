@@ -213,19 +213,21 @@ void free_plan(Plan& p)
 
 // Host-side table of the fused finalize: per group the number of
 // enumeration threads whose item range touches it (thread t covers the items
-// whose cost range starts in [t W, (t + 1) W)).
+// whose cost range starts in its static_range).
 void fused_tables(const Plan& p, const std::vector<tmgpu::GroupPlan>& gp,
                   std::vector<uint32_t>& target)
 {
     target.assign(std::max(p.G, 1), 0);
-    const uint64_t W = p.leaves_per_thread, total = gp[p.G].cost_base;
+    const uint64_t total = gp[p.G].cost_base;
     int g = 0;
     for (uint64_t t = 0; t < p.threads; ++t) {
-        const uint64_t x0 = t * W;
+        uint64_t x0, x1;
+        tmgpu::static_range(t, p.leaves_per_thread, p.split_c, p.split_warps, p.split_hi,
+                            p.split_klo, &x0, &x1);
         if (x0 >= total) break;
         const uint32_t i0 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, p.item_cost, x0);
         const uint32_t i1 = tmgpu::plan_first_item(gp.data(), p.G, p.pdmax, p.item_cost,
-                                                   std::min(x0 + W, total));
+                                                   std::min(x1, total));
         if (i0 >= i1) continue;
         while (gp[g + 1].item_base <= i0) ++g;        // the group holding item i0
         for (int h = g; h < p.G && gp[h].item_base < i1; ++h)

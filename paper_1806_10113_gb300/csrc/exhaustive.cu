@@ -825,12 +825,14 @@ template <int PDMAX, bool UNROLL>
 __global__ void __launch_bounds__(kEnumBlock, TM_ENUM_MIN_BLOCKS)
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
-            uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks)
+            uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks,
+            uint64_t split_c, uint32_t split_warps, uint32_t split_hi, uint32_t split_klo)
 {
     if (!next) {   // static split: one range per thread
         const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, t * per_thread, (t + 1) * per_thread, item_cost,
-                          sink);
+        uint64_t x0, x1;
+        static_range(t, per_thread, split_c, split_warps, split_hi, split_klo, &x0, &x1);
+        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, x0, x1, item_cost, sink);
         return;
     }
     // dynamic: each warp takes 32 consecutive chunks at a time, one per lane
@@ -875,7 +877,8 @@ cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
     const bool dyn = p.chunks_per_thread > 1;
     enum_kernel<PDMAX, UNROLL><<<blocks, kEnumBlock, 0, stream>>>(
         p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
-        sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u);
+        sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u, dyn ? 0ull : p.split_c,
+        p.split_warps, p.split_hi, p.split_klo);
     return cudaGetLastError();
 }
 
@@ -910,6 +913,20 @@ void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
                                           std::max<uint64_t>(p.total_items, 1));
     p.leaves_per_thread = std::max<uint64_t>(1, (p.total_leaves + threads - 1) / threads);
     p.threads = (uint32_t)((p.total_leaves + p.leaves_per_thread - 1) / p.leaves_per_thread);
+    p.split_c = 0;
+    p.split_warps = p.split_hi = p.split_klo = 0;
+    if (p.chunks_per_thread == 1 && p.total_items > 0 && p.uniform_n >= 4) {
+        const uint64_t I = p.total_items, c = p.total_leaves / I;   // every item costs c
+        uint64_t warps = (threads + 31) / 32;
+        const uint64_t klo = I / (32 * warps);
+        if (klo == 0) warps = (I + 31) / 32;                // one item per lane at most
+        const uint64_t hi = (I - 32 * warps * klo + 31) / 32;   // warps with klo + 1
+        p.split_c = c;
+        p.split_warps = (uint32_t)warps;
+        p.split_hi = (uint32_t)hi;
+        p.split_klo = (uint32_t)klo;
+        p.threads = (uint32_t)(32 * warps);
+    }
     if (p.chunks_per_thread > 1) {
         p.chunk = std::max<uint64_t>(1, p.leaves_per_thread / (uint64_t)p.chunks_per_thread);
         const uint64_t nch = (p.total_leaves + p.chunk - 1) / p.chunk;

@@ -90,6 +90,7 @@ struct Plan {
     uint32_t item_cost = 256;     // per-item overhead, in orders
     uint32_t total_units = 0;     // prep / suffix-table threads
     uint32_t total_subs = 0;      // suffix-table entries
+    int uniform_n = 0;            // the group size when every group has it, else 0
     uint32_t threads = 0;         // enumeration threads
     uint64_t leaves_per_thread = 0;
     int launches = 0;
@@ -100,6 +101,13 @@ struct Plan {
     // more work.
     int chunks_per_thread = 1;
     int unroll = 2;                       // 1: straight-line walk level (tm_tuning)
+    // Static split of a batch of one group size (all work items cost the
+    // same, split_c): whole warps take klo or klo + 1 items per lane, the
+    // split_hi heavier warps spread evenly over the split_warps warps, so no
+    // lane of a warp waits for another's extra item and every SM holds the
+    // same mix.  split_c == 0: contiguous cost ranges of leaves_per_thread.
+    uint64_t split_c = 0;
+    uint32_t split_warps = 0, split_hi = 0, split_klo = 0;
     uint64_t chunk = 0;                   // cost units per chunk (dynamic)
     uint32_t nchunks = 0;
     GroupPlan* d_gp = nullptr;            // [G + 1]
@@ -181,6 +189,9 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
     totals->total_leaves = cost;
     totals->total_units = (uint32_t)units;
     totals->total_subs = (uint32_t)subs;
+    totals->uniform_n = 0;
+    for (int nn = 1; nn <= TM_MAX_EXHAUSTIVE && G > 0; ++nn)
+        if (start[nn] - (nn < TM_MAX_EXHAUSTIVE ? start[nn + 1] : 0u) == (uint32_t)G) totals->uniform_n = nn;
     return TM_OK;
 }
 
@@ -239,6 +250,24 @@ __host__ __device__ inline uint32_t plan_first_item(const GroupPlan* gp, int G, 
     const uint64_t q = (x - gp[lo].cost_base + lpi - 1) / lpi;
     const uint64_t i = gp[lo].item_base + q;
     return (uint32_t)(i < gp[lo + 1].item_base ? i : gp[lo + 1].item_base);
+}
+
+// Cost units [x0, x1) of static-split enumeration thread t.
+__host__ __device__ inline void static_range(uint64_t t, uint64_t per_thread, uint64_t split_c,
+                                             uint32_t split_warps, uint32_t split_hi,
+                                             uint32_t split_klo, uint64_t* x0, uint64_t* x1)
+{
+    if (split_c == 0) {
+        *x0 = t * per_thread;
+        *x1 = (t + 1) * per_thread;
+        return;
+    }
+    const uint64_t w = t >> 5, lane = t & 31;
+    const uint64_t hi_before = w * split_hi / split_warps;
+    const uint64_t k = split_klo + (((w + 1) * split_hi / split_warps > hi_before) ? 1u : 0u);
+    const uint64_t first = 32 * (split_klo * w + hi_before) + lane * k;
+    *x0 = first * split_c;
+    *x1 = (first + k) * split_c;
 }
 
 // Launchers (return cudaError_t of the launch).  With d_orders non-null the
