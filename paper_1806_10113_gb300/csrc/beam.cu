@@ -154,23 +154,38 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
     const int cands = n - pos;
     int nk = 32;
     while (nk < B * R) nk <<= 1;    // keys sorted: a power of two >= B * R
-    // log-sum-exp of each live beam's candidate logits
+    // log-sum-exp of each live beam's candidate logits: all of a beam's
+    // logits are loaded at once (one memory latency, not one per
+    // candidate), then reduced in candidate order
     for (int b = tid; b < B; b += blockDim.x) {
         const BeamState s = cur[(size_t)g * B + b];
         float mx = -INFINITY, z = 0.0f;
         if (s.alive) {
             const float* lg = logits + ((size_t)g * B + b) * R;
-            for (int c = 0; c < cands; ++c) mx = fmaxf(mx, lg[c]);
-            for (int c = 0; c < cands; ++c) z += expf(lg[c] - mx);
+            float v[TM_MAX_TASKS];
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c) v[c] = c < cands ? lg[c] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c)
+                if (c < cands) mx = fmaxf(mx, v[c]);
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c)
+                if (c < cands) z += expf(v[c] - mx);
         }
         lse[b] = s.alive ? mx + logf(z) : 0.0f;
     }
     __syncthreads();
     constexpr int KPT = kMaxCand / NT;       // keys per thread
+    // key i of thread tid, slot q: with two keys per thread, warp w holds
+    // keys 64 w .. 64 w + 63 (lane l: 64 w + l and 64 w + 32 + l), so that
+    // each warp can sort its 64 alone; with one, key tid
+    auto key_index = [&](int q) {
+        return KPT == 2 ? 64 * (tid >> 5) + 32 * q + (tid & 31) : tid + q * NT;
+    };
     unsigned long long key[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-        const int i = tid + q * NT;
+        const int i = key_index(q);
         const int b = i / R, c = i - (i / R) * R;
         key[q] = 0;
         if (i < nk && b < B && c < cands && cur[(size_t)g * B + b].alive) {
@@ -179,6 +194,59 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
             key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
         }
     }
+    if constexpr (KPT == 2) {
+        // Top 64 by sorted runs and merges: each warp sorts its 64 keys
+        // (bitonic, descending; the partner at distance 32 is the lane's
+        // other key, nearer ones by shuffle), then runs merge pairwise in
+        // four rounds: the upper run of a pair is read reversed from shared
+        // memory, the element-wise maximum of the two is a bitonic sequence
+        // holding the pair's best 64, and a half-cleaner cascade sorts it.
+        // Keys are distinct (the candidate index is in their low bits), so
+        // the best 64 come out exactly as a full sort would order them.
+        const int lane = tid & 31, w = tid >> 5;
+        auto cx = [&](unsigned long long& a, unsigned long long o, bool keep_max) {
+            a = keep_max ? (a > o ? a : o) : (a < o ? a : o);
+        };
+        const bool any = __any_sync(0xFFFFFFFFu, (key[0] | key[1]) != 0ull);
+        for (int kk = 2; any && kk <= 64; kk <<= 1) {   // a run of empty keys is sorted
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                if (j == 32) {   // kk == 64: element l against element 32 + l
+                    const unsigned long long a = key[0], b = key[1];
+                    key[0] = a > b ? a : b;
+                    key[1] = a > b ? b : a;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, key[q], j);
+                        const int e = 32 * q + lane;
+                        cx(key[q], o, ((e & j) == 0) == ((e & kk) == 0));
+                    }
+                }
+            }
+        }
+        unsigned long long (*run)[64] = reinterpret_cast<unsigned long long (*)[64]>(buf[0]);
+        for (int step = 1; step < NT / 32; step <<= 1) {
+            const bool upper = (w & (2 * step - 1)) == step, merger = (w & (2 * step - 1)) == 0;
+            if (upper) { run[w][lane] = key[0]; run[w][32 + lane] = key[1]; }
+            __syncthreads();
+            if (merger) {
+                // element e against the partner's element 63 - e
+                cx(key[0], run[w + step][63 - lane], true);
+                cx(key[1], run[w + step][31 - lane], true);
+                const unsigned long long a = key[0], b = key[1];   // distance 32
+                key[0] = a > b ? a : b;
+                key[1] = a > b ? b : a;
+                for (int j = 16; j > 0; j >>= 1) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        cx(key[q], __shfl_xor_sync(0xFFFFFFFFu, key[q], j), (lane & j) == 0);
+                }
+            }
+            __syncthreads();
+        }
+        if (w == 0) { run[0][lane] = key[0]; run[0][32 + lane] = key[1]; }
+        __syncthreads();
+    } else {
     // bitonic sort, descending: partners in the same thread (j >= NT) in
     // registers, within a warp (j < 32) by shuffles, else through shared
     // memory (two buffers, one barrier per stage)
@@ -214,6 +282,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
 #pragma unroll
     for (int q = 0; q < KPT; ++q) buf[0][tid + q * NT] = key[q];
     __syncthreads();
+    }
     for (int b = tid; b < B; b += blockDim.x) {
         BeamState s;
         const unsigned long long k = buf[0][b];
