@@ -14,8 +14,8 @@
 // the init kernel for i = 0 and by the previous selection after that).  The
 // ranker scores the rows; a block per group turns scores into log-softmax
 // over each beam's candidates, adds the beam's log-probability, keeps the
-// best B candidates (bitonic sort in shared memory of the B x R keys; ties:
-// lower beam, then lower slot) and applies them.
+// best B candidates (the best 64 of the B x R keys by warp-sorted runs and
+// pairwise merges; ties: lower beam, then lower slot) and applies them.
 #include <cuda_bf16.h>
 
 #include "rank_features.cuh"
@@ -131,8 +131,7 @@ __device__ __forceinline__ uint32_t orderable(float v)
 // (R - 1 rows per beam) from the new beams, so that each position costs two
 // launches: the scores and this selection (small batches, where launches
 // dominate).
-// NT threads per block hold the up to kMaxCand sort keys, kMaxCand / NT
-// each (key i in thread i % NT).
+// NT (512 or 1024) threads per block; the first 512 hold the keys.
 template <bool WRITE_NEXT, int NT>
 __global__ void __launch_bounds__(NT)
 beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
@@ -149,7 +148,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         return;
     }
     __shared__ float lse[64];
-    __shared__ unsigned long long buf[2][kMaxCand];
+    __shared__ unsigned long long buf[kMaxCand];
     __shared__ BeamState ns[64];
     const int cands = n - pos;
     int nk = 32;
@@ -175,117 +174,78 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         lse[b] = s.alive ? mx + logf(z) : 0.0f;
     }
     __syncthreads();
-    constexpr int KPT = kMaxCand / NT;       // keys per thread
-    // key i of thread tid, slot q: with two keys per thread, warp w holds
-    // keys 64 w .. 64 w + 63 (lane l: 64 w + l and 64 w + 32 + l), so that
-    // each warp can sort its 64 alone; with one, key tid
-    auto key_index = [&](int q) {
-        return KPT == 2 ? 64 * (tid >> 5) + 32 * q + (tid & 31) : tid + q * NT;
-    };
-    unsigned long long key[KPT];
+    // The B x R <= kMaxCand candidate keys sit two per lane in warps
+    // 0 .. 15 (warp w: keys 64 w .. 64 w + 63, lane l holding 64 w + l and
+    // 64 w + 32 + l), so that each of those warps can sort its 64 alone.
+    static_assert(NT >= 512 && kMaxCand == 1024, "16 warps of 64 keys");
+    const int lane = tid & 31, w = tid >> 5;
+    unsigned long long key[2] = {0ull, 0ull};
+    if (w < 16) {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-        const int i = key_index(q);
-        const int b = i / R, c = i - (i / R) * R;
-        key[q] = 0;
-        if (i < nk && b < B && c < cands && cur[(size_t)g * B + b].alive) {
-            const float score = cur[(size_t)g * B + b].logp +
-                                (logits[((size_t)g * B + b) * R + c] - lse[b]);
-            key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
-        }
-    }
-    if constexpr (KPT == 2) {
-        // Top 64 by sorted runs and merges: each warp sorts its 64 keys
-        // (bitonic, descending; the partner at distance 32 is the lane's
-        // other key, nearer ones by shuffle), then runs merge pairwise in
-        // four rounds: the upper run of a pair is read reversed from shared
-        // memory, the element-wise maximum of the two is a bitonic sequence
-        // holding the pair's best 64, and a half-cleaner cascade sorts it.
-        // Keys are distinct (the candidate index is in their low bits), so
-        // the best 64 come out exactly as a full sort would order them.
-        const int lane = tid & 31, w = tid >> 5;
-        auto cx = [&](unsigned long long& a, unsigned long long o, bool keep_max) {
-            a = keep_max ? (a > o ? a : o) : (a < o ? a : o);
-        };
-        const bool any = __any_sync(0xFFFFFFFFu, (key[0] | key[1]) != 0ull);
-        for (int kk = 2; any && kk <= 64; kk <<= 1) {   // a run of empty keys is sorted
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                if (j == 32) {   // kk == 64: element l against element 32 + l
-                    const unsigned long long a = key[0], b = key[1];
-                    key[0] = a > b ? a : b;
-                    key[1] = a > b ? b : a;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, key[q], j);
-                        const int e = 32 * q + lane;
-                        cx(key[q], o, ((e & j) == 0) == ((e & kk) == 0));
-                    }
-                }
+        for (int q = 0; q < 2; ++q) {
+            const int i = 64 * w + 32 * q + lane;
+            const int b = i / R, c = i - (i / R) * R;
+            if (i < nk && b < B && c < cands && cur[(size_t)g * B + b].alive) {
+                const float score = cur[(size_t)g * B + b].logp +
+                                    (logits[((size_t)g * B + b) * R + c] - lse[b]);
+                key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
             }
         }
-        unsigned long long (*run)[64] = reinterpret_cast<unsigned long long (*)[64]>(buf[0]);
-        for (int step = 1; step < NT / 32; step <<= 1) {
-            const bool upper = (w & (2 * step - 1)) == step, merger = (w & (2 * step - 1)) == 0;
-            if (upper) { run[w][lane] = key[0]; run[w][32 + lane] = key[1]; }
-            __syncthreads();
-            if (merger) {
-                // element e against the partner's element 63 - e
-                cx(key[0], run[w + step][63 - lane], true);
-                cx(key[1], run[w + step][31 - lane], true);
-                const unsigned long long a = key[0], b = key[1];   // distance 32
+    }
+    // Top 64 by sorted runs and merges: each warp sorts its 64 keys
+    // (bitonic, descending; the partner at distance 32 is the lane's other
+    // key, nearer ones by shuffle), then runs merge pairwise in four rounds:
+    // the upper run of a pair is read reversed from shared memory, the
+    // element-wise maximum of the two is a bitonic sequence holding the
+    // pair's best 64, and a half-cleaner cascade sorts it.  Keys are
+    // distinct (the candidate index is in their low bits), so the best 64
+    // come out exactly as a full sort would order them.
+    auto cx = [&](unsigned long long& a, unsigned long long o, bool keep_max) {
+        a = keep_max ? (a > o ? a : o) : (a < o ? a : o);
+    };
+    const bool any = __any_sync(0xFFFFFFFFu, (key[0] | key[1]) != 0ull);
+    for (int kk = 2; w < 16 && any && kk <= 64; kk <<= 1) {   // a run of empty keys is sorted
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j == 32) {   // kk == 64: element l against element 32 + l
+                const unsigned long long a = key[0], b = key[1];
                 key[0] = a > b ? a : b;
                 key[1] = a > b ? b : a;
-                for (int j = 16; j > 0; j >>= 1) {
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-                        cx(key[q], __shfl_xor_sync(0xFFFFFFFFu, key[q], j), (lane & j) == 0);
-                }
-            }
-            __syncthreads();
-        }
-        if (w == 0) { run[0][lane] = key[0]; run[0][32 + lane] = key[1]; }
-        __syncthreads();
-    } else {
-    // bitonic sort, descending: partners in the same thread (j >= NT) in
-    // registers, within a warp (j < 32) by shuffles, else through shared
-    // memory (two buffers, one barrier per stage)
-    int flip = 0;
-    for (int kk = 2; kk <= nk; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            unsigned long long other[KPT];
-            if (j >= NT) {
-                // nk <= kMaxCand = 2 NT here: the partner is the thread's other key
-#pragma unroll
-                for (int q = 0; q < KPT; ++q) other[q] = key[KPT - 1 - q];
-            } else if (j >= 32) {
-#pragma unroll
-                for (int q = 0; q < KPT; ++q) buf[flip][tid + q * NT] = key[q];
-                __syncthreads();
-#pragma unroll
-                for (int q = 0; q < KPT; ++q) other[q] = buf[flip][(tid + q * NT) ^ j];
-                flip ^= 1;
             } else {
 #pragma unroll
-                for (int q = 0; q < KPT; ++q) other[q] = __shfl_xor_sync(0xFFFFFFFFu, key[q], j);
-            }
-#pragma unroll
-            for (int q = 0; q < KPT; ++q) {
-                const int i = tid + q * NT;
-                const bool desc = (i & kk) == 0, lower = (i & j) == 0;
-                key[q] = (lower == desc) ? (key[q] > other[q] ? key[q] : other[q])
-                                         : (key[q] < other[q] ? key[q] : other[q]);
+                for (int q = 0; q < 2; ++q) {
+                    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, key[q], j);
+                    const int e = 32 * q + lane;
+                    cx(key[q], o, ((e & j) == 0) == ((e & kk) == 0));
+                }
             }
         }
     }
-    __syncthreads();
+    unsigned long long (*run)[64] = reinterpret_cast<unsigned long long (*)[64]>(buf);
+    for (int span = 1; span < 16; span <<= 1) {
+        const bool upper = w < 16 && (w & (2 * span - 1)) == span;
+        const bool merger = w < 16 && (w & (2 * span - 1)) == 0;
+        if (upper) { run[w][lane] = key[0]; run[w][32 + lane] = key[1]; }
+        __syncthreads();
+        if (merger) {
+            // element e against the partner's element 63 - e
+            cx(key[0], run[w + span][63 - lane], true);
+            cx(key[1], run[w + span][31 - lane], true);
+            const unsigned long long a = key[0], b = key[1];   // distance 32
+            key[0] = a > b ? a : b;
+            key[1] = a > b ? b : a;
+            for (int j = 16; j > 0; j >>= 1) {
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) buf[0][tid + q * NT] = key[q];
-    __syncthreads();
+                for (int q = 0; q < 2; ++q)
+                    cx(key[q], __shfl_xor_sync(0xFFFFFFFFu, key[q], j), (lane & j) == 0);
+            }
+        }
+        __syncthreads();
     }
+    if (w == 0) { run[0][lane] = key[0]; run[0][32 + lane] = key[1]; }
+    __syncthreads();
     for (int b = tid; b < B; b += blockDim.x) {
         BeamState s;
-        const unsigned long long k = buf[0][b];
+        const unsigned long long k = run[0][b];
         if (k == 0) {
             s.alive = 0;
             s.h = s.k = s.d = 0;
@@ -519,7 +479,7 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
 {
     // X == nullptr: the caller writes the next position's rows itself.
     // Large batches: 512 threads per group (more blocks per SM); small ones:
-    // 1024 (one key per thread, lower latency).
+    // 1024 (more threads for the log-softmax and the next position's rows).
     const BeamState* c = static_cast<const BeamState*>(cur);
     BeamState* nx = static_cast<BeamState*>(nxt);
     __nv_bfloat16* x = reinterpret_cast<__nv_bfloat16*>(X);
