@@ -103,6 +103,55 @@ __device__ W overlap_makespan(const int4* __restrict__ tbl, int n, uint64_t orde
     return T;
 }
 
+// The event loop's state at the instant the HtD queue turns to position p,
+// before any command starts at that instant: everything up to then depends
+// only on the tasks at positions < p, so every order that shares them can
+// resume from it.  q packs ik | id << 8 | kernel busy << 16 | DtH busy << 17.
+template <typename W>
+struct OvlSnap {
+    W T, kl, dl;
+    uint32_t q;
+};
+
+// overlap_makespan resumed from snap[from] (snap[0] is the empty start);
+// on the way it stores the snapshots of positions from + 1 .. n - 1.
+template <typename W>
+__device__ W overlap_makespan_from(const int4* __restrict__ tbl, int n, uint64_t order,
+                                   const Div& slow, const Div& full, OvlSnap<W>* snap, int from)
+{
+    const W rs = (W)slow.v, rf = (W)full.v;
+    const OvlSnap<W> s0 = snap[from];
+    int ih = from, ik = (int)(s0.q & 0xFFu), id = (int)((s0.q >> 8) & 0xFFu);
+    bool hb = false, kb = ((s0.q >> 16) & 1u) != 0u, db = ((s0.q >> 17) & 1u) != 0u;
+    W hl = 0, kl = s0.kl, dl = s0.dl;
+    W T = s0.T;
+    for (;;) {
+        if (!hb && ih < n) {
+            if (ih > from)
+                snap[ih] = OvlSnap<W>{T, kl, dl, (uint32_t)ik | ((uint32_t)id << 8) |
+                                                     ((uint32_t)kb << 16) | ((uint32_t)db << 17)};
+            hb = true;
+            hl = (W)tbl[nib_get(order, ih)].x * rf;
+        }
+        if (!kb && ik < ih) { kb = true; kl = tbl[nib_get(order, ik)].y; }
+        if (!db && id < ik) { db = true; dl = (W)tbl[nib_get(order, id)].z * rf; }
+        if (!hb && !kb && !db) break;
+        const bool both = hb && db;
+        const Div& v = both ? slow : full;
+        const W rate = both ? rs : rf;
+        W next = sizeof(W) == 4 ? (W)INT32_MAX : (W)LLONG_MAX;
+        if (hb) next = min(next, (W)(T + ceil_div(hl, v)));
+        if (kb) next = min(next, (W)(T + kl));
+        if (db) next = min(next, (W)(T + ceil_div(dl, v)));
+        const W dt = next - T;
+        T = next;
+        if (hb) { hl -= rate * dt; if (hl <= 0) { hb = false; ++ih; } }
+        if (kb) { kl -= dt; if (kl <= 0) { kb = false; ++ik; } }
+        if (db) { dl -= rate * dt; if (dl <= 0) { db = false; ++id; } }
+    }
+    return T;
+}
+
 // Whether the 32-bit loop is exact for a group: every transfer's work
 // (duration x den) plus one step of the fastest rate below 2^31.  (Times
 // stay below the group's bound, itself below 2^31.)
@@ -266,6 +315,45 @@ __device__ __forceinline__ void ovl_flush(const OvlAcc& a, unsigned long long* _
     atomicAdd(&A[2], a.sum);
 }
 
+__device__ __forceinline__ void ovl_take(OvlAcc& a, int32_t m, uint32_t rank)
+{
+    a.sum += (unsigned long long)(uint32_t)m;
+    if (m < a.best) { a.best = m; a.best_rank = rank; }       // ranks rise: first kept
+    if (m > a.worst) { a.worst = m; a.worst_rank = rank; }
+}
+
+// `count` consecutive orders from `order` (rank `rank`) under the plain
+// model (one DMA engine, or full rate).
+__device__ void ovl_run_plain(const int4* __restrict__ t, int n, uint64_t order, uint32_t rank,
+                              uint32_t count, int32_t dinit, OvlAcc& a)
+{
+    for (uint32_t c = 0; c < count; ++c, ++rank) {
+        ovl_take(a, (int32_t)plain_makespan(t, n, order, max(dinit, 0)), rank);
+        if (c + 1 < count) order = next_order(order, n);
+    }
+}
+
+// The same under the partial-overlap rule: each order resumes the event loop
+// from the snapshot at the first position where it differs from the one
+// before (the lexicographic successor changes the last ~e positions on
+// average), instead of simulating from time 0.
+template <typename W>
+__device__ void ovl_run(const int4* __restrict__ t, int n, uint64_t order, uint32_t rank,
+                        uint32_t count, const Div& slow, const Div& full, OvlAcc& a)
+{
+    OvlSnap<W> snap[TM_MAX_EXHAUSTIVE];
+    snap[0] = OvlSnap<W>{0, 0, 0, 0u};
+    int from = 0;
+    for (uint32_t c = 0; c < count; ++c, ++rank) {
+        ovl_take(a, (int32_t)overlap_makespan_from<W>(t, n, order, slow, full, snap, from), rank);
+        if (c + 1 < count) {
+            const uint64_t nx = next_order(order, n);
+            from = (__ffsll((long long)(order ^ nx)) - 1) >> 2;   // first position that changes
+            order = nx;
+        }
+    }
+}
+
 // Thread t walks global order indices [t R, (t + 1) R) (base[g] = first index
 // of group g, base[G] = total).
 __global__ void __launch_bounds__(kOvlBlock)
@@ -292,20 +380,14 @@ ovl_enum_kernel(const unsigned long long* __restrict__ base, int G,
         const OvlInfo oi = info[g];
         if (oi.status != 0) { x = gend; continue; }
         const int4* t = tbl + oi.off;
-        uint32_t rank = (uint32_t)(x - base[g]);
-        uint64_t order = unrank(rank, oi.n);
+        const uint32_t rank = (uint32_t)(x - base[g]);
+        const uint64_t order = unrank(rank, oi.n);
         OvlAcc a{INT32_MAX, -1, 0xFFFFFFFFu, 0xFFFFFFFFu, 0ull};
-        for (; x < gend; ++x, ++rank) {
-            const long long ms = (oi.dinit >= 0 || num == den)
-                                     ? plain_makespan(t, oi.n, order, max(oi.dinit, 0))
-                                 : oi.w32 ? (long long)overlap_makespan<int32_t>(t, oi.n, order, slow, full)
-                                          : overlap_makespan<long long>(t, oi.n, order, slow, full);
-            const int32_t m = (int32_t)ms;
-            a.sum += (unsigned long long)(uint32_t)m;
-            if (m < a.best) { a.best = m; a.best_rank = rank; }       // ranks rise: first kept
-            if (m > a.worst) { a.worst = m; a.worst_rank = rank; }
-            if (x + 1 < gend) order = next_order(order, oi.n);
-        }
+        const uint32_t count = (uint32_t)(gend - x);
+        if (oi.dinit >= 0 || num == den) ovl_run_plain(t, oi.n, order, rank, count, oi.dinit, a);
+        else if (oi.w32) ovl_run<int32_t>(t, oi.n, order, rank, count, slow, full, a);
+        else ovl_run<long long>(t, oi.n, order, rank, count, slow, full, a);
+        x = gend;
         ovl_flush(a, acc, g);
     }
 }
