@@ -768,44 +768,45 @@ def run_serve(args):
 # has at most 3n events.
 OVERLAP_OPS_PER_EVENT = 8 + 3 + 26 + 12 + 15
 OVERLAP_RUN = 64            # consecutive ranks per enumeration thread
+# One DtH of the closed-form tail: the kernels up to it (an add each, about
+# one per DtH), the max with the DtH engine and the add of its duration, and
+# the position bookkeeping (2).
+OVERLAP_OPS_PER_TAIL = 1 + 2 + 2
 
 
 def overlap_loop_events(t, order, num, den):
-    """Events of the partial-overlap loop for one order, and the event count
-    reached when the HtD queue turns to each position (the resume points of
-    the enumeration kernel).  Counting only: the makespans come from the
-    kernels, and their parity from the tests."""
+    """Events of the partial-overlap loop for one order until the last HtD
+    ends (after that the kernel finishes in closed form), the event count
+    reached when the HtD queue turns to each position (the enumeration
+    kernel's resume points), and the number of DtH left to the closed-form
+    tail.  Counting only: the makespans come from the kernels, and their
+    parity from the tests."""
     n = len(order)
     ih = ik = idd = 0
     hb = kb = db = False
     hl = kl = dl = 0
     T = 0
     events, at = 0, [0] * n
-    while True:
-        if not hb and ih < n:
+    while ih < n:
+        if not hb:
             at[ih] = events
             hb, hl = True, int(t[order[ih]][0]) * den
         if not kb and ik < ih:
             kb, kl = True, int(t[order[ik]][1])
         if not db and idd < ik:
             db, dl = True, int(t[order[idd]][2]) * den
-        if not (hb or kb or db):
-            return events, at
         events += 1
-        rate = num if (hb and db) else den
-        ends = []
-        if hb:
-            ends.append(T + -(-hl // rate))
+        rate = num if db else den
+        ends = [T + -(-hl // rate)]
         if kb:
             ends.append(T + kl)
         if db:
             ends.append(T + -(-dl // rate))
         nxt = min(ends)
         dt, T = nxt - T, nxt
-        if hb:
-            hl -= rate * dt
-            if hl <= 0:
-                hb, ih = False, ih + 1
+        hl -= rate * dt
+        if hl <= 0:
+            hb, ih = False, ih + 1
         if kb:
             kl -= dt
             if kl <= 0:
@@ -814,14 +815,17 @@ def overlap_loop_events(t, order, num, den):
             dl -= rate * dt
             if dl <= 0:
                 db, idd = False, idd + 1
+    return events, at, n - (idd + 1 if db else idd)
 
 
-def overlap_events_per_order(b, num, den, runs_per_group=16):
-    """Average events the enumeration kernel executes per order: each thread
-    simulates the first order of its run of OVERLAP_RUN ranks in full and
-    resumes every later one at the first position where it differs from the
-    one before.  Measured on runs spread over each group's rank space."""
-    total_events = total_orders = 0
+def overlap_ops_per_order(b, num, den, runs_per_group=16):
+    """Average integer operations the enumeration kernel executes per order:
+    each thread simulates the first order of its run of OVERLAP_RUN ranks in
+    full and resumes every later one at the first position where it differs
+    from the one before; events cost OVERLAP_OPS_PER_EVENT, each DtH of the
+    closed-form tail OVERLAP_OPS_PER_TAIL.  Measured on runs spread over each
+    group's rank space.  Returns (ops, events, tail steps) per order."""
+    ev_total = tail_total = orders = 0
     for g in range(b.G):
         t = b.group(g)
         n = t.shape[0]
@@ -835,13 +839,11 @@ def overlap_events_per_order(b, num, den, runs_per_group=16):
                 rank %= f
             prev = None
             for _ in range(OVERLAP_RUN):
-                ev, at = overlap_loop_events(t, order, num, den)
-                if prev is None:
-                    total_events += ev
-                else:
-                    q = next(i for i in range(n) if order[i] != prev[i])
-                    total_events += ev - at[q]
-                total_orders += 1
+                ev, at, tail = overlap_loop_events(t, order, num, den)
+                q = 0 if prev is None else next(i for i in range(n) if order[i] != prev[i])
+                ev_total += ev - at[q]
+                tail_total += tail
+                orders += 1
                 prev = list(order)
                 # lexicographic successor
                 i = n - 2
@@ -854,7 +856,8 @@ def overlap_events_per_order(b, num, den, runs_per_group=16):
                     j -= 1
                 order[i], order[j] = order[j], order[i]
                 order[i + 1:] = reversed(order[i + 1:])
-    return total_events / total_orders
+    ev, tail = ev_total / orders, tail_total / orders
+    return OVERLAP_OPS_PER_EVENT * ev + OVERLAP_OPS_PER_TAIL * tail, ev, tail
 
 
 def run_overlap(args):
@@ -906,8 +909,8 @@ def run_overlap(args):
     for g, o in picks:
         oracle.predict_overlap(b.group(g), o, 2, num, den)
     cpu_s = time.perf_counter() - t0
-    events = overlap_events_per_order(b, num, den)
-    achieved = OVERLAP_OPS_PER_EVENT * events * value / 1e12
+    ops_order, events, tail = overlap_ops_per_order(b, num, den)
+    achieved = ops_order * value / 1e12
     out = {
         "metric": "orderings evaluated/s (partial-overlap model, N=10, exhaustive)",
         "value": value, "unit": "orders/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
@@ -922,11 +925,13 @@ def run_overlap(args):
         "roofline": {"bound": "alu", "kernel": "ovl_enum_kernel (event loop per order)",
                      "achieved": achieved, "peak": INT32_PEAK_TOPS, "unit": "Tops/s (int32)",
                      "frac": achieved / INT32_PEAK_TOPS, "traffic": None,
-                     "ops_per_order": round(OVERLAP_OPS_PER_EVENT * events, 1),
+                     "ops_per_order": round(ops_order, 1),
                      "events_per_order": round(events, 2),
-                     "ops_basis": "events the kernel executes per order (runs of 64 ranks, each "
-                                  "order resumed at its first changed position; counted on 16 "
-                                  "runs per group) x ops per event of the loop body",
+                     "tail_steps_per_order": round(tail, 2),
+                     "ops_basis": "what the kernel executes per order (runs of 64 ranks, each "
+                                  "order resumed at its first changed position, closed-form tail "
+                                  "after the last HtD; counted on 16 runs per group): events x "
+                                  "ops per event of the loop body + tail DtH x ops per tail step",
                      "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)"},
         "cpu_baseline": {"value": sample / cpu_s, "unit": "orders/s", "cores": 1,
                          "kind": "oracle",

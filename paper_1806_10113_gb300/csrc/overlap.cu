@@ -114,7 +114,10 @@ struct OvlSnap {
 };
 
 // overlap_makespan resumed from snap[from] (snap[0] is the empty start);
-// on the way it stores the snapshots of positions from + 1 .. n - 1.
+// on the way it stores the snapshots of positions from + 1 .. n - 1.  Once
+// the last HtD has ended no two transfers overlap any more, so the rest is
+// the plain recurrence from the engines' state: kernels back to back, each
+// DtH at full speed after its kernel and the DtH before it.
 template <typename W>
 __device__ W overlap_makespan_from(const int4* __restrict__ tbl, int n, uint64_t order,
                                    const Div& slow, const Div& full, OvlSnap<W>* snap, int from)
@@ -125,7 +128,7 @@ __device__ W overlap_makespan_from(const int4* __restrict__ tbl, int n, uint64_t
     bool hb = false, kb = ((s0.q >> 16) & 1u) != 0u, db = ((s0.q >> 17) & 1u) != 0u;
     W hl = 0, kl = s0.kl, dl = s0.dl;
     W T = s0.T;
-    for (;;) {
+    while (ih < n) {
         if (!hb && ih < n) {
             if (ih > from)
                 snap[ih] = OvlSnap<W>{T, kl, dl, (uint32_t)ik | ((uint32_t)id << 8) |
@@ -135,21 +138,34 @@ __device__ W overlap_makespan_from(const int4* __restrict__ tbl, int n, uint64_t
         }
         if (!kb && ik < ih) { kb = true; kl = tbl[nib_get(order, ik)].y; }
         if (!db && id < ik) { db = true; dl = (W)tbl[nib_get(order, id)].z * rf; }
-        if (!hb && !kb && !db) break;
-        const bool both = hb && db;
+        const bool both = db;            // an HtD runs throughout this loop
         const Div& v = both ? slow : full;
         const W rate = both ? rs : rf;
-        W next = sizeof(W) == 4 ? (W)INT32_MAX : (W)LLONG_MAX;
-        if (hb) next = min(next, (W)(T + ceil_div(hl, v)));
+        W next = (W)(T + ceil_div(hl, v));
         if (kb) next = min(next, (W)(T + kl));
         if (db) next = min(next, (W)(T + ceil_div(dl, v)));
         const W dt = next - T;
         T = next;
-        if (hb) { hl -= rate * dt; if (hl <= 0) { hb = false; ++ih; } }
+        hl -= rate * dt;
+        if (hl <= 0) { hb = false; ++ih; }
         if (kb) { kl -= dt; if (kl <= 0) { kb = false; ++ik; } }
         if (db) { dl -= rate * dt; if (dl <= 0) { db = false; ++id; } }
     }
-    return T;
+    // the tail: every HtD has ended by T
+    W kfree = kb ? (W)(T + kl) : T;      // the kernel engine frees
+    int kp = kb ? ik + 1 : ik;           // next kernel to start
+    W dfree = db ? (W)(T + ceil_div(dl, full)) : T;
+    for (int p = db ? id + 1 : id; p < n; ++p) {
+        W ke = T;                        // kernels below ik ended by T
+        if (p == ik && kb) {
+            ke = kfree;
+        } else if (p >= ik) {
+            for (; kp <= p; ++kp) kfree += (W)tbl[nib_get(order, kp)].y;
+            ke = kfree;
+        }
+        dfree = max(dfree, ke) + (W)tbl[nib_get(order, p)].z;
+    }
+    return max(dfree, kfree);
 }
 
 // Whether the 32-bit loop is exact for a group: every transfer's work
