@@ -11,16 +11,20 @@
 //
 // The max-plus decomposition of the plain model does not hold here (a
 // transfer's speed depends on what the other engine does), so every order is
-// one event loop over the three engines: at each step the free engines take
+// an event loop over the three engines: at each step the free engines take
 // their queue's next command if its dependency has ended, the speeds follow
-// from which transfers run, and time jumps to the earliest end.
+// from which transfers run, and time jumps to the earliest end.  Once the
+// last HtD has ended nothing overlaps any more and the rest is the plain
+// recurrence.
 //
 //   overlap_predict_kernel   one given order per group (thread per group)
 //   ovl_prep_kernel          per group: input checks, padded task table,
 //                            reduction words
 //   ovl_enum_kernel          every order of every group: a thread walks a
 //                            run of consecutive ranks (lexicographic successor
-//                            after the first unranking) and reduces them
+//                            after the first unranking), resuming each order's
+//                            loop where it first differs from the previous
+//                            one, and reduces them
 //   ovl_finalize_kernel      reduction words -> tm_stats
 #include <algorithm>
 #include <climits>
