@@ -1,6 +1,6 @@
 // heuristic.cuh -- the Batch Reordering heuristic (Sec. 5.1, Algorithm 1),
-// one warp per task group, lane j holding task j.  Used by the heuristic
-// kernel and by the fused scheduling launch.
+// one warp (or half a warp) per task group, lane j holding task j.  Used by
+// the heuristic kernel and by the fused scheduling launches.
 //
 // The selection rules follow the paper's wording under these readings:
 //   select_first_task: largest K - HtD (short HtD, long K); ties -> longer
@@ -26,14 +26,32 @@ namespace heur {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ int64_t warp_min_i64(int64_t v)
+// A group runs on a segment of W lanes of one warp (W = 32: the whole warp;
+// W = 16: half a warp, two groups per warp; groups have at most 16 tasks):
+// `mask` holds the segment's lanes, lane numbers are within the segment.
+template <int W>
+__device__ __forceinline__ unsigned seg_mask()
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(kFull, (long long)v, o));
-    return v;
+    return W == 32 ? kFull : (0xFFFFu << (threadIdx.x & 16u));
+}
+
+template <int W>
+__device__ __forceinline__ unsigned seg_ballot(unsigned mask, bool pred)
+{
+    const unsigned b = __ballot_sync(mask, pred);
+    return W == 32 ? b : (b >> (threadIdx.x & 16u)) & 0xFFFFu;
 }
 
 __device__ __forceinline__ int lowest_lane(unsigned mask) { return __ffs(mask) - 1; }
+
+template <int W>
+__device__ __forceinline__ int64_t seg_min_i64(unsigned mask, int64_t v)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1)
+        v = min(v, (int64_t)__shfl_xor_sync(mask, (long long)v, o, W));
+    return v;
+}
 
 // With one DMA engine the DtH chain of OT starts when the last of OT's HtDs
 // ends; as a max-plus function of that start x it is max(x + sumD, C), where
@@ -82,15 +100,18 @@ __device__ __forceinline__ int32_t finish_two(const HeurState& st, int dma, int3
     return d;
 }
 
-// Algorithm 1 for group g (tasks[off .. off + n)), run by one full warp.
-__device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ tasks, int off, int n,
-                                                int dma, int g, int lane,
-                                                int32_t* __restrict__ orders_out,
-                                                int32_t* __restrict__ ms_out,
-                                                int32_t* __restrict__ status)
+// Algorithm 1 for group g (tasks[off .. off + n)), run by a segment of W
+// lanes (every lane of it; lane = the lane within the segment).
+template <int W>
+__device__ __forceinline__ void heuristic_group_seg(const tm_task* __restrict__ tasks, int off,
+                                                    int n, int dma, int g, int lane,
+                                                    int32_t* __restrict__ orders_out,
+                                                    int32_t* __restrict__ ms_out,
+                                                    int32_t* __restrict__ status)
 {
+    const unsigned mask = seg_mask<W>();
     // the input check of check_group, one task per lane
-    if (n < 1 || n > TM_MAX_TASKS || (dma != 1 && dma != 2)) {
+    if (n < 1 || n > TM_MAX_TASKS || n > W || (dma != 1 && dma != 2)) {
         if (lane == 0 && status) status[g] = TM_EINVAL;
         return;
     }
@@ -101,11 +122,11 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
     }
     long long tot = (long long)H + K + D, hsum = H;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        tot += __shfl_xor_sync(kFull, tot, o);
-        hsum += __shfl_xor_sync(kFull, hsum, o);
+    for (int o = W / 2; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(mask, tot, o, W);
+        hsum += __shfl_xor_sync(mask, hsum, o, W);
     }
-    const int err = __ballot_sync(kFull, H < 0 || K < 0 || D < 0) ? TM_ENEG
+    const int err = seg_ballot<W>(mask, H < 0 || K < 0 || D < 0) ? TM_ENEG
                     : tot > INT32_MAX                              ? TM_EOVERFLOW
                                                                    : 0;
     if (err != 0) {
@@ -116,8 +137,8 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
     unsigned rt = (n >= 32) ? kFull : ((1u << n) - 1u);   // remaining tasks
     HeurState st{0, 0, dinit, 0, kNegC, 0, -1};
     auto take = [&](int j) {
-        int32_t hj = __shfl_sync(kFull, H, j), kj = __shfl_sync(kFull, K, j),
-                dj = __shfl_sync(kFull, D, j);
+        int32_t hj = __shfl_sync(mask, H, j, W), kj = __shfl_sync(mask, K, j, W),
+                dj = __shfl_sync(mask, D, j, W);
         append(st, lane, dma, j, hj, kj, dj);
         rt &= ~(1u << j);
     };
@@ -129,10 +150,10 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
             // select_first_task
             bool in = (rt >> lane) & 1u;
             int32_t gain = in ? K - H : INT32_MIN;
-            int32_t best_gain = __reduce_max_sync(kFull, gain);
+            int32_t best_gain = __reduce_max_sync(mask, gain);
             bool c1 = in && gain == best_gain;
-            int32_t best_d = (int32_t)__reduce_max_sync(kFull, c1 ? (unsigned)D : 0u);
-            take(lowest_lane(__ballot_sync(kFull, c1 && D == best_d)));
+            int32_t best_d = (int32_t)__reduce_max_sync(mask, c1 ? (unsigned)D : 0u);
+            take(lowest_lane(seg_ballot<W>(mask, c1 && D == best_d)));
             // select_next_task while more than two tasks remain
             while (__popc(rt) > 2) {
                 bool inr = (rt >> lane) & 1u;
@@ -140,19 +161,19 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
                 int64_t a = ((int64_t)st.tK - st.tH) - H;
                 int64_t b = ((int64_t)st.tD - s) - K;
                 int64_t cost = inr ? (a < 0 ? -a : a) + (b < 0 ? -b : b) : INT64_MAX;
-                int64_t best_cost = warp_min_i64(cost);
+                int64_t best_cost = seg_min_i64<W>(mask, cost);
                 bool c = inr && cost == best_cost;
-                int32_t best_k = (int32_t)__reduce_max_sync(kFull, c ? (unsigned)K : 0u);
-                take(lowest_lane(__ballot_sync(kFull, c && K == best_k)));
+                int32_t best_k = (int32_t)__reduce_max_sync(mask, c ? (unsigned)K : 0u);
+                take(lowest_lane(seg_ballot<W>(mask, c && K == best_k)));
             }
         }
         // select_last_tasks on the two remaining tasks a < b
         int a = __ffs(rt) - 1;
         int b = 31 - __clz(rt);
-        int32_t ha = __shfl_sync(kFull, H, a), ka = __shfl_sync(kFull, K, a),
-                da = __shfl_sync(kFull, D, a);
-        int32_t hb = __shfl_sync(kFull, H, b), kb = __shfl_sync(kFull, K, b),
-                db = __shfl_sync(kFull, D, b);
+        int32_t ha = __shfl_sync(mask, H, a, W), ka = __shfl_sync(mask, K, a, W),
+                da = __shfl_sync(mask, D, a, W);
+        int32_t hb = __shfl_sync(mask, H, b, W), kb = __shfl_sync(mask, K, b, W),
+                db = __shfl_sync(mask, D, b, W);
         int32_t m_ab = finish_two(st, dma, hs, ha, ka, da, hb, kb, db);
         int32_t m_ba = finish_two(st, dma, hs, hb, kb, db, ha, ka, da);
         bool ba = (m_ab != m_ba) ? (m_ba < m_ab) : (da < db);
@@ -163,6 +184,16 @@ __device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ task
         if (ms_out) ms_out[g] = st.tD;
         if (status) status[g] = 0;
     }
+}
+
+// Algorithm 1 for group g by one full warp.
+__device__ __forceinline__ void heuristic_group(const tm_task* __restrict__ tasks, int off, int n,
+                                                int dma, int g, int lane,
+                                                int32_t* __restrict__ orders_out,
+                                                int32_t* __restrict__ ms_out,
+                                                int32_t* __restrict__ status)
+{
+    heuristic_group_seg<32>(tasks, off, n, dma, g, lane, orders_out, ms_out, status);
 }
 
 }  // namespace heur
