@@ -132,3 +132,28 @@ def test_64bit_work_path():
     for g in range(b.G):
         o = orders[b.offsets[g]:b.offsets[g + 1]]
         assert ms[g] == oracle.predict_overlap(b.group(g), o, int(b.dma[g]), 1000, 1024)
+
+
+@pytest.mark.parametrize("rate", [(2, 3), (5, 9)])
+def test_exhaustive_n9_every_order_against_predict(rate):
+    """Every one of the 9! orders of two 9-task groups: the exhaustive
+    search (each order resumed where it first differs from the one before,
+    the tail after the last HtD in closed form) against the predict kernel,
+    which simulates each order from time 0 and is itself checked against the
+    oracle above."""
+    num, den = rate
+    b = inputs.random_groups(47 + num, [9, 9], hi=3_000_000, dma=[2, 2])
+    got = tm.stats_to_dicts(tm.tm_exhaustive_overlap_batch(b.tasks, b.offsets, b.dma, num, den),
+                            b.sizes())
+    perms = np.array(list(itertools.permutations(range(9))), dtype=np.int32)   # lexicographic
+    P = perms.shape[0]
+    for g in range(b.G):
+        t = b.group(g)
+        tasks = np.tile(t, (P, 1)).astype(np.int32)
+        offsets = (np.arange(P + 1) * 9).astype(np.int32)
+        ms = tm.tm_predict_overlap_batch(tasks, offsets, perms.reshape(-1), np.full(P, 2, np.int32),
+                                         num, den).astype(np.int64)
+        assert got[g]["best"] == ms.min() and got[g]["worst"] == ms.max(), g
+        assert got[g]["sum"] == ms.sum(), g
+        assert got[g]["best_rank"] == int(np.argmax(ms == ms.min())), g
+        assert got[g]["worst_rank"] == int(np.argmax(ms == ms.max())), g
