@@ -778,9 +778,9 @@ def overlap_loop_events(t, order, num, den):
     """Events of the partial-overlap loop for one order until the last HtD
     ends (after that the kernel finishes in closed form), the event count
     reached when the HtD queue turns to each position (the enumeration
-    kernel's resume points), and the number of DtH left to the closed-form
-    tail.  Counting only: the makespans come from the kernels, and their
-    parity from the tests."""
+    kernel's resume points), the number of DtH left to the closed-form tail,
+    and the makespan the same steps give (two DMA engines).  For counting:
+    the bench's makespans come from the kernels."""
     n = len(order)
     ih = ik = idd = 0
     hb = kb = db = False
@@ -815,7 +815,23 @@ def overlap_loop_events(t, order, num, den):
             dl -= rate * dt
             if dl <= 0:
                 db, idd = False, idd + 1
-    return events, at, n - (idd + 1 if db else idd)
+    # the tail: every HtD has ended by T, nothing overlaps any more
+    kfree = T + kl if kb else T
+    kp = ik + 1 if kb else ik
+    dfree = T + -(-dl // den) if db else T
+    tail = 0
+    for p in range(idd + 1 if db else idd, n):
+        ke = T
+        if p == ik and kb:
+            ke = kfree
+        elif p >= ik:
+            while kp <= p:
+                kfree += int(t[order[kp]][1])
+                kp += 1
+            ke = kfree
+        dfree = max(dfree, ke) + int(t[order[p]][2])
+        tail += 1
+    return events, at, tail, max(dfree, kfree)
 
 
 def overlap_ops_per_order(b, num, den, runs_per_group=16):
@@ -839,7 +855,7 @@ def overlap_ops_per_order(b, num, den, runs_per_group=16):
                 rank %= f
             prev = None
             for _ in range(OVERLAP_RUN):
-                ev, at, tail = overlap_loop_events(t, order, num, den)
+                ev, at, tail, _ = overlap_loop_events(t, order, num, den)
                 q = 0 if prev is None else next(i for i in range(n) if order[i] != prev[i])
                 ev_total += ev - at[q]
                 tail_total += tail

@@ -120,3 +120,24 @@ def test_exhaustive_overlap_by_enumeration():
     assert got["best"] == min(ms) and got["worst"] == max(ms) and got["sum"] == sum(ms)
     assert got["best_rank"] == ms.index(min(ms)) and got["worst_rank"] == ms.index(max(ms))
     assert got["mean"] == sum(ms) / 120
+
+
+def test_closed_form_tail_matches_the_event_simulation():
+    """The enumeration kernel stops simulating events once the last HtD has
+    ended and finishes the order with the plain recurrence (kernels back to
+    back, each DtH at full speed after its kernel and the DtH before).  The
+    bench's counting model takes the same steps (bench.overlap_loop_events);
+    here its makespans must equal the oracle's event simulation."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rng = np.random.default_rng(12)
+    for trial in range(400):
+        n = int(rng.integers(1, 9))
+        hi = int(rng.choice([5, 40, 2_000_000]))
+        t = rng.integers(0, hi, size=(n, 3)).astype(np.int32)
+        num, den = [(1, 2), (2, 3), (3, 8), (5, 9), (1, 1), (7, 10)][trial % 6]
+        order = [int(x) for x in rng.permutation(n)]
+        _, _, _, ms = bench.overlap_loop_events(t, order, num, den)
+        assert ms == oracle.predict_overlap(t, order, 2, num, den), (t.tolist(), order, num, den)
