@@ -127,6 +127,9 @@ struct Context {
     tm_plan* plan = nullptr;
     std::vector<int32_t> plan_offsets;
     unsigned plan_epoch = 0;
+    // the mapped blocks the plan's captured graph reads and writes
+    const void* graph_in = nullptr;
+    const void* graph_out = nullptr;
     void release()
     {
         if (plan) tm_plan_destroy(plan);
@@ -528,6 +531,7 @@ int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const t
         if ((rc = tm_plan_create(offsets, G, &c->plan)) != TM_OK) return rc;
         c->plan_offsets = offs;
         c->plan_epoch = epoch;
+        c->graph_in = c->graph_out = nullptr;
     }
     const int T = offsets[G];
     cudaStream_t s = c->stream;
@@ -551,10 +555,19 @@ int exhaustive_host(const tm_task* tasks, const int32_t* offsets, int G, const t
     int32_t* d_status = reinterpret_cast<int32_t*>(dout + o_status);
     int32_t* d_ms = reinterpret_cast<int32_t*>(dout + o_ms);
     int32_t* d_orders = reinterpret_cast<int32_t*>(dout + o_orders);
-    if (orders_out)
-        rc = tm_schedule_batch_dev(c->plan, d_tasks, d_devs, d_stats, d_orders, d_ms, d_status, s);
-    else
+    if (orders_out) {
+        // the whole pass as one CUDA graph, captured once per plan and blocks
+        if (c->graph_in != din || c->graph_out != dout) {
+            if ((rc = tm_plan_capture(c->plan, d_tasks, d_devs, d_stats, d_orders, d_ms,
+                                      d_status)) != TM_OK)
+                return rc;
+            c->graph_in = din;
+            c->graph_out = dout;
+        }
+        rc = tm_plan_graph_launch(c->plan, s);
+    } else {
         rc = tm_exhaustive_batch_dev(c->plan, d_tasks, d_devs, d_stats, d_status, s);
+    }
     if (rc != TM_OK) return rc;
     TM_CUDA(cudaStreamSynchronize(s));
     const unsigned char* hout = static_cast<const unsigned char*>(c->pin_out.p);
