@@ -207,15 +207,20 @@ int tm_exhaustive_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
 
 /* The whole scheduling pass of the paper's method for every group of the
  * plan: the exhaustive search (d_stats) and the reordering heuristic
- * (d_orders_out in the task layout; d_makespans_out may be NULL), in two
- * kernel launches.  Same results as tm_exhaustive_batch_dev followed by
- * tm_heuristic_batch_dev.  d_status reports the per-group input checks. */
+ * (d_orders_out in the task layout; d_makespans_out may be NULL), in the
+ * plan's launches (tm_plan_launches: prep, enumeration, finalize; the
+ * heuristic's warps run beside the finalize warps).  Same results as
+ * tm_exhaustive_batch_dev followed by tm_heuristic_batch_dev.  d_status
+ * reports the per-group input checks. */
 int tm_schedule_batch_dev(const tm_plan* plan, const tm_task* d_tasks,
                           const tm_device* d_devs, tm_stats* d_stats,
                           int32_t* d_orders_out, int32_t* d_makespans_out,
                           int32_t* d_status /* may be NULL */, void* stream);
 
-/* Host-pointer form of tm_schedule_batch_dev (synchronous).  n <= 12. */
+/* Host-pointer form of tm_schedule_batch_dev (synchronous).  n <= 12.  The
+ * calling thread's plan for the last batch shape is kept, and its launches
+ * are captured once as a CUDA graph that later calls with the same shape
+ * replay; inputs and results pass through mapped page-locked memory. */
 int tm_schedule_batch(const tm_task* tasks, const int32_t* offsets, int G,
                       const tm_device* devs, tm_stats* stats,
                       int32_t* orders_out, int32_t* makespans_out /* may be NULL */);
