@@ -151,8 +151,6 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
     __shared__ unsigned long long buf[kMaxCand];
     __shared__ BeamState ns[64];
     const int cands = n - pos;
-    int nk = 32;
-    while (nk < B * R) nk <<= 1;    // keys sorted: a power of two >= B * R
     // log-sum-exp of each live beam's candidate logits: all of a beam's
     // logits are loaded at once (one memory latency, not one per
     // candidate), then reduced in candidate order
@@ -185,7 +183,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         for (int q = 0; q < 2; ++q) {
             const int i = 64 * w + 32 * q + lane;
             const int b = i / R, c = i - (i / R) * R;
-            if (i < nk && b < B && c < cands && cur[(size_t)g * B + b].alive) {
+            if (b < B && c < cands && cur[(size_t)g * B + b].alive) {
                 const float score = cur[(size_t)g * B + b].logp +
                                     (logits[((size_t)g * B + b) * R + c] - lse[b]);
                 key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
