@@ -34,11 +34,14 @@
  * Ties for best / worst go to the first order met, i.e. the lowest
  * lexicographic rank.  mean = (double)sum / (double)n!.
  *
- * Heuristic (Sec. 5.1, Algorithm 1).  PARITY UNPINNED beyond the readings
- * below: the paper describes the selection criteria in words only, so only
- * properties (a valid permutation, the exact optimum for n = 2, the first
- * task's criterion, the optimal order of the last two tasks, never better
- * than the exhaustive best) can pin it.
+ * Heuristic (Sec. 5.1, Algorithm 1).  The paper describes the selection
+ * criteria in words only and prints no chosen order, so the readings below
+ * are this oracle's; the code is pinned to them by runs of Algorithm 1
+ * derived by hand on groups of Table 2 tasks (every update, every candidate's
+ * cost, both completions of the last two tasks), and by properties (a valid
+ * permutation, the exact optimum for n = 2, never better than the exhaustive
+ * best).  Whether a reading is the authors' own is PARITY UNPINNED: nothing
+ * in the paper can decide it.
  *   H1  select_first_task: largest K - HtD; ties -> longer DtH; ties -> lower
  *       task index.
  *   H2  update(OT): simulate OT as if it were the whole group; t_HTD, t_K and

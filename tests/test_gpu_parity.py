@@ -214,6 +214,29 @@ def test_heuristic_worked_example(tm):
     assert tm.tm_heuristic(t3, 1) == ([0, 2, 1], 19_000_000)
 
 
+def test_heuristic_select_next_worked_by_hand(tm):
+    """The hand-derived Algorithm 1 runs (select_next_task twice, a cost tie
+    settled by K, an HtD ending after the kernel engine frees): the half-warp
+    heuristic kernel and the full-warp heuristic inside the scheduling pass
+    both give the stored orders."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "heuristic_select_next_T2tasks.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    groups = {r[1]: r[2].split(",") for r in rows if r[0] == "group"}
+    want = [(r[1], int(r[2]), [int(x) for x in r[3].split(",")], int(r[4]) * 1_000_000)
+            for r in rows if r[0] == "heuristic"]
+    assert len(want) == 6
+    for name, dma, order, ms in want:
+        assert tm.tm_heuristic(inputs.table2_tasks(groups[name]), dma) == (order, ms), (name, dma)
+    b = inputs.make_batch([inputs.table2_tasks(groups[name]) for name, _, _, _ in want],
+                          [dma for _, dma, _, _ in want])
+    orders, ms = tm.tm_heuristic_batch(b.tasks, b.offsets, b.dma)
+    _, orders2, ms2 = tm.tm_schedule_batch(b.tasks, b.offsets, b.dma)
+    exp_orders = np.concatenate([np.asarray(o, dtype=np.int32) for _, _, o, _ in want])
+    exp_ms = np.asarray([m for _, _, _, m in want])
+    assert (orders == exp_orders).all() and (ms == exp_ms).all()
+    assert (orders2 == exp_orders).all() and (ms2 == exp_ms).all()
+
+
 # ---- the whole scheduling pass ----------------------------------------------------
 
 def test_schedule_batch_matches_oracle_on_ragged_groups(tm):

@@ -2,8 +2,9 @@
 
 Each case plants one mistake in a temporary copy of the oracle source (a
 dropped dependency, a wrong queue layout, transposed stages, a wrong clock
-step, a wrong tie rule, a wrong divisor), builds it, and runs the pin suite
-against it in a child process.  The suite must fail for every mutant.
+step, a wrong tie rule, a wrong divisor, a misread term, sign, start time or
+tie rule in the heuristic's cost), builds it, and runs the pin suite against
+it in a child process.  The suite must fail for every mutant.
 """
 import os
 import subprocess
@@ -43,6 +44,23 @@ MUTANTS = {
     "first_task_min_gain": ("if (gj > gb ||", "if (gj < gb ||"),
     "last_two_not_compared": ("if (m_ab != m_ba) take_ba = m_ba < m_ab;",
                               "if (m_ab != m_ba) take_ba = false;"),
+    # select_next_task (H3): each term of the cost, its sign, the kernel start
+    # s_j and the tie rule
+    "h3_drops_kernel_fit": ("std::llabs((e.t_dth - s) - k);", "0 * std::llabs((e.t_dth - s) - k);"),
+    "h3_drops_htd_fit": ("int64_t cost = std::llabs((e.t_k - e.t_htd) - h) +",
+                         "int64_t cost = 0 * std::llabs((e.t_k - e.t_htd) - h) +"),
+    "h3_signed_cost": ("int64_t cost = std::llabs((e.t_k - e.t_htd) - h) +\n"
+                       "                       std::llabs((e.t_dth - s) - k);",
+                       "int64_t cost = ((e.t_k - e.t_htd) - h) +\n"
+                       "                       ((e.t_dth - s) - k);"),
+    "h3_kernel_starts_at_t_k": ("int64_t s = std::max(e.t_k, e.t_htd + h);",
+                                "int64_t s = e.t_k;"),
+    "h3_kernel_starts_after_htd": ("int64_t s = std::max(e.t_k, e.t_htd + h);",
+                                   "int64_t s = e.t_htd + h;"),
+    "h3_tie_prefers_shorter_k": ("(cost == best_cost && tasks[j].k > tasks[best].k)",
+                                 "(cost == best_cost && tasks[j].k < tasks[best].k)"),
+    "h3_tie_lower_index": ("(cost == best_cost && tasks[j].k > tasks[best].k)",
+                           "(cost == best_cost && false)"),
 }
 
 

@@ -345,3 +345,68 @@ def test_prefix_samples_partition_the_exhaustive_search():
             worst = min(parts, key=lambda p: (-p["worst"], p["worst_rank"]))
             assert (best["best"], best["best_rank"]) == (full["best"], full["best_rank"])
             assert (worst["worst"], worst["worst_rank"]) == (full["worst"], full["worst_rank"])
+
+
+# ---- heuristic: select_next_task worked by hand (H1-H4) -----------------------
+
+def read_select_next_golden():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "heuristic_select_next_T2tasks.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    groups = {r[1]: r[2].split(",") for r in rows if r[0] == "group"}
+    return groups, [r for r in rows if r[0] != "group"]
+
+
+def _ints(field):
+    return [int(x) for x in field.split(",")]
+
+
+def test_heuristic_select_next_worked_by_hand():
+    """Algorithm 1 on three groups of Table 2 tasks, every step derived by hand
+    (first task, each update() and each candidate's start and cost, both
+    completions of the last two, the chosen order).  Groups A and B make
+    select_next_task run twice, with a cost tie that the K rule settles and a
+    candidate whose HtD ends after the kernel engine frees, so each plausible
+    misreading of the cost or the tie rule changes the chosen order."""
+    groups, rows = read_select_next_golden()
+    unit = 1_000_000
+    seen = set()
+    for row in rows:
+        kind, name, dma = row[0], row[1], int(row[2])
+        ms_tasks = inputs.table2_tasks(groups[name], 1)
+        ns_tasks = inputs.table2_tasks(groups[name], unit)
+        seen.add((kind, name, dma))
+        if kind == "first":
+            order, _ = oracle.heuristic(ns_tasks, dma)
+            assert order[0] == int(row[3])
+        elif kind == "update":
+            ot = _ints(row[3])
+            sub = ns_tasks[ot]
+            total, tl = oracle.predict(sub, list(range(len(ot))), dma, timeline=True)
+            want = [int(x) for x in row[4:7]]
+            # ends of the last HtD, K and DtH of OT simulated as the whole group
+            assert [int(tl[-1, 0, 1]), int(tl[-1, 1, 1]), int(tl[-1, 2, 1])] == \
+                [w * unit for w in want], (name, dma, ot)
+            assert total == want[2] * unit
+            assert stepped_total_time(ms_tasks[ot], list(range(len(ot))), dma) == want[2]
+        elif kind == "complete":
+            order = _ints(row[3])
+            assert oracle.predict(ns_tasks, order, dma) == int(row[4]) * unit
+            assert stepped_total_time(ms_tasks, order, dma) == int(row[4])
+        elif kind == "heuristic":
+            order, ms = oracle.heuristic(ns_tasks, dma)
+            assert order == _ints(row[3]) and ms == int(row[4]) * unit, (name, dma, order)
+            # the scale of the time unit changes nothing
+            assert oracle.heuristic(ms_tasks, dma) == (_ints(row[3]), int(row[4]))
+    # the stored candidate rows agree with the stored choices: at every step the
+    # chosen task is the listed candidate of smallest cost, ties to larger K
+    chosen = {(r[1], int(r[2])): _ints(r[3]) for r in rows if r[0] == "heuristic"}
+    steps = {}
+    for r in rows:
+        if r[0] == "cand":
+            steps.setdefault((r[1], int(r[2]), r[3]), []).append((int(r[4]), int(r[6])))
+    for (name, dma, ot), cands in steps.items():
+        k = {j: int(inputs.TABLE2_MS[groups[name][j]][1]) for j, _ in cands}
+        pick = min(cands, key=lambda c: (c[1], -k[c[0]], c[0]))[0]
+        prefix = _ints(ot)
+        assert chosen[(name, dma)][:len(prefix) + 1] == prefix + [pick], (name, dma, ot)
+    assert {(n, d) for _, n, d in seen} == {(n, d) for n in groups for d in (1, 2)}
