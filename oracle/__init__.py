@@ -83,10 +83,19 @@ def _load():
                                             P(ctypes.c_int64), P(ctypes.c_int64)]
         lib.orc_exhaustive_overlap.argtypes = [P(OrcTask), ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int32, ctypes.c_int32, P(OrcStats)]
+        lib.orc_predict_chain.argtypes = [P(OrcTask), ctypes.c_int, ctypes.c_int,
+                                          P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int64),
+                                          P(ctypes.c_int64)]
+        lib.orc_exhaustive_chain.argtypes = [P(OrcTask), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             P(OrcStats)]
+        lib.orc_exhaustive_chain_batch.argtypes = [P(OrcTask), P(ctypes.c_int32),
+                                                   P(ctypes.c_int32), ctypes.c_int,
+                                                   P(ctypes.c_int32), ctypes.c_int, P(OrcStats)]
         lib.orc_hardware_threads.argtypes = []
         for f in ("orc_predict", "orc_exhaustive", "orc_exhaustive_batch", "orc_heuristic",
                   "orc_heuristic_batch", "orc_hardware_threads", "orc_exhaustive_prefixes",
-                  "orc_predict_overlap", "orc_exhaustive_overlap"):
+                  "orc_predict_overlap", "orc_exhaustive_overlap", "orc_predict_chain",
+                  "orc_exhaustive_chain", "orc_exhaustive_chain_batch"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -238,3 +247,55 @@ def heuristic_batch(tasks, offsets, dma_engines, nthreads: int = 0):
                                      _ptr(orders, ctypes.c_int32), _ptr(ms, ctypes.c_int64))
     _check(rc, "heuristic_batch")
     return orders[: t.shape[0]], ms[:G]
+
+
+# ---- chained tasks ---------------------------------------------------------------
+
+def predict_chain(tasks, workers: int, order, dma_engines: int, timeline: bool = False):
+    """Total time of one order of a chained group (Sec. 6.1 experiment setup):
+    tasks[r * workers + w] is worker w's task of round r; `order` lists the
+    task indices round by round.  With ``timeline=True`` also returns the
+    (n, 3, 2) {start, end} array of every position's HtD, K and DtH."""
+    t = _tasks(tasks)
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    n = t.shape[0]
+    if int(workers) < 1 or n % int(workers):
+        raise ValueError("predict_chain: the task count must be a multiple of workers")
+    rounds = n // int(workers)
+    ms = ctypes.c_int64(0)
+    tl = np.zeros(6 * max(n, 1), dtype=np.int64)
+    rc = _load().orc_predict_chain(_ptr(t, OrcTask), int(workers), rounds,
+                                   _ptr(o, ctypes.c_int32), int(dma_engines), ctypes.byref(ms),
+                                   _ptr(tl, ctypes.c_int64))
+    _check(rc, "predict_chain")
+    if timeline:
+        return int(ms.value), tl[:6 * n].reshape(n, 3, 2)
+    return int(ms.value)
+
+
+def exhaustive_chain(tasks, workers: int, dma_engines: int) -> dict:
+    """All (workers!)^rounds orders of one chained group."""
+    t = _tasks(tasks)
+    n = t.shape[0]
+    if int(workers) < 1 or n % int(workers):
+        raise ValueError("exhaustive_chain: the task count must be a multiple of workers")
+    out = OrcStats()
+    rc = _load().orc_exhaustive_chain(_ptr(t, OrcTask), int(workers), n // int(workers),
+                                      int(dma_engines), ctypes.byref(out))
+    _check(rc, "exhaustive_chain")
+    return _stats_dict(out, n)
+
+
+def exhaustive_chain_batch(tasks, offsets, workers, dma_engines, nthreads: int = 0) -> list:
+    """exhaustive_chain of every group of a ragged batch (workers[g] per group)."""
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(workers, dtype=np.int32), (G,)))
+    dma = np.ascontiguousarray(np.broadcast_to(np.asarray(dma_engines, dtype=np.int32), (G,)))
+    out = (OrcStats * max(G, 1))()
+    rc = _load().orc_exhaustive_chain_batch(_ptr(t, OrcTask), _ptr(off, ctypes.c_int32),
+                                            _ptr(w, ctypes.c_int32), G, _ptr(dma, ctypes.c_int32),
+                                            int(nthreads), out)
+    _check(rc, "exhaustive_chain_batch")
+    return [_stats_dict(out[g], int(off[g + 1] - off[g])) for g in range(G)]

@@ -248,6 +248,109 @@ int64_t simulate_overlap(const orc_task* tasks, int n, const int32_t* order, int
     return T_sim;
 }
 
+/* Chained tasks (Sec. 6.1, experiment setup): `workers` workers each submit
+ * a chain of `rounds` dependent tasks; a worker's next task is released only
+ * once its previous task has completely finished.  The paper enumerates
+ * (T!)^N orders for T workers and chains of N tasks, i.e. the group runs as
+ * N rounds in sequence, round r holding the r-th task of every worker in
+ * some order.  Task index r * workers + w is worker w's task of round r; an
+ * order `seq` lists the n = workers * rounds task indices, round 0's block
+ * first.  The queues are those of simulate(), filled in sequence order, with
+ * one extra dependency: the HtD of worker w's round-r task (r >= 1) starts
+ * only after the DtH of its round-(r - 1) task has ended.  With one DMA
+ * engine each round is submitted as a group of its own: the transfer FIFO
+ * holds round 0's HtDs, then round 0's DtHs, then round 1's HtDs, and so on
+ * (one FIFO holding every HtD before any DtH could never drain under the
+ * chain dependency).  Returns the total time, or -1 if the queues cannot
+ * drain (a self-check). */
+int64_t simulate_chain(const orc_task* tasks, int workers, int rounds, const int32_t* seq,
+                       int dma_engines, int64_t* timeline)
+{
+    const int n = workers * rounds;
+    std::vector<int> pos_of(n, 0);
+    for (int p = 0; p < n; ++p) pos_of[seq[p]] = p;
+    std::vector<Fifo> fifo(dma_engines == 2 ? 3 : 2);
+    if (dma_engines == 2) {
+        for (int p = 0; p < n; ++p) {
+            const orc_task& t = tasks[seq[p]];
+            fifo[0].items.push_back({p, HTD, stage(t, HTD)});
+            fifo[1].items.push_back({p, KER, stage(t, KER)});
+            fifo[2].items.push_back({p, DTH, stage(t, DTH)});
+        }
+    } else {
+        for (int r = 0; r < rounds; ++r) {
+            for (int i = 0; i < workers; ++i) {
+                const int p = r * workers + i;
+                fifo[0].items.push_back({p, HTD, stage(tasks[seq[p]], HTD)});
+            }
+            for (int i = 0; i < workers; ++i) {
+                const int p = r * workers + i;
+                fifo[0].items.push_back({p, DTH, stage(tasks[seq[p]], DTH)});
+            }
+        }
+        for (int p = 0; p < n; ++p) fifo[1].items.push_back({p, KER, stage(tasks[seq[p]], KER)});
+    }
+    std::vector<char> done(3 * n, 0);
+    std::vector<int64_t> t_start(3 * n, 0), t_end(3 * n, 0);
+    int64_t T_sim = 0;
+    for (;;) {
+        for (Fifo& f : fifo) {
+            if (f.busy || f.empty()) continue;
+            const Cmd& c = f.front();
+            bool ready;
+            if (c.type == HTD) {
+                /* the previous task of the same worker must have finished */
+                const int t = seq[c.pos];
+                ready = t < workers || done[3 * pos_of[t - workers] + DTH];
+            } else {
+                ready = done[3 * c.pos + (c.type - 1)];
+            }
+            if (!ready) continue;
+            f.busy = true;
+            f.end = T_sim + c.dur;
+            t_start[3 * c.pos + c.type] = T_sim;
+        }
+        bool any = false;
+        int64_t next = INT64_MAX;
+        for (const Fifo& f : fifo)
+            if (f.busy) { any = true; next = std::min(next, f.end); }
+        if (!any) break;
+        T_sim = next;
+        for (Fifo& f : fifo) {
+            if (!f.busy || f.end != T_sim) continue;
+            const Cmd& c = f.front();
+            done[3 * c.pos + c.type] = 1;
+            t_end[3 * c.pos + c.type] = T_sim;
+            f.head++;
+            f.busy = false;
+        }
+    }
+    for (const Fifo& f : fifo)
+        if (!f.empty()) return -1;
+    if (timeline) {
+        for (int i = 0; i < n; ++i)
+            for (int ty = 0; ty < 3; ++ty) {
+                timeline[6 * i + 2 * ty + 0] = t_start[3 * i + ty];
+                timeline[6 * i + 2 * ty + 1] = t_end[3 * i + ty];
+            }
+    }
+    return T_sim;
+}
+
+/* Chained orders are enumerated like a counter whose digits are the rounds'
+ * permutations, round 0 most significant: the next order advances the last
+ * round to its next permutation, and a round that wraps around to its first
+ * permutation carries into the round before it.  Each round's block holds
+ * fixed task indices, so this is the lexicographic order of the sequences.
+ * Returns false after the last order (the sequence is then the first one). */
+bool next_chain_order(std::vector<int32_t>& seq, int workers, int rounds, int first_round)
+{
+    for (int r = rounds - 1; r >= first_round; --r)
+        if (std::next_permutation(seq.begin() + r * workers, seq.begin() + (r + 1) * workers))
+            return true;
+    return false;
+}
+
 uint64_t factorial(int n)
 {
     uint64_t f = 1;
@@ -655,6 +758,117 @@ int orc_exhaustive_overlap(const orc_task* tasks, int n, int dma_engines, int32_
         out->worst_order[i] = i < n ? worst_order[i] : -1;
     }
     return 0;
+}
+
+static bool valid_chain_seq(const int32_t* seq, int workers, int rounds)
+{
+    const int n = workers * rounds;
+    std::vector<char> seen(n, 0);
+    for (int p = 0; p < n; ++p) {
+        const int t = seq[p];
+        if (t < 0 || t >= n || seen[t] || t / workers != p / workers) return false;
+        seen[t] = 1;
+    }
+    return true;
+}
+
+static bool valid_chain_shape(int workers, int rounds)
+{
+    return workers >= 1 && workers <= 8 && rounds >= 1 && workers * rounds <= 16;
+}
+
+int orc_predict_chain(const orc_task* tasks, int workers, int rounds, const int32_t* seq,
+                      int dma_engines, int64_t* makespan, int64_t* timeline)
+{
+    if (!tasks || !seq || !makespan || !valid_chain_shape(workers, rounds)) return -1;
+    if (dma_engines != 1 && dma_engines != 2) return -1;
+    if (!valid_tasks(tasks, workers * rounds) || !valid_chain_seq(seq, workers, rounds))
+        return -1;
+    const int64_t ms = simulate_chain(tasks, workers, rounds, seq, dma_engines, timeline);
+    if (ms < 0) return -1;
+    *makespan = ms;
+    return 0;
+}
+
+int orc_exhaustive_chain_batch(const orc_task* tasks, const int32_t* offsets,
+                               const int32_t* workers, int G, const int32_t* dma_engines,
+                               int nthreads, orc_stats* out)
+{
+    if (!tasks || !offsets || !workers || !dma_engines || !out || G < 0) return -1;
+    for (int g = 0; g < G; ++g) {
+        const int n = offsets[g + 1] - offsets[g], w = workers[g];
+        if (w < 1 || n % w != 0 || !valid_chain_shape(w, n / w)) return -1;
+        if (dma_engines[g] != 1 && dma_engines[g] != 2) return -1;
+        if (!valid_tasks(tasks + offsets[g], n)) return -1;
+    }
+    /* One work item per (group, permutation of the first round); item q of a
+     * group covers ranks [q * (T!)^(N-1), (q + 1) * (T!)^(N-1)). */
+    std::vector<int> item_group, item_q;
+    for (int g = 0; g < G; ++g)
+        for (uint64_t q = 0; q < factorial(workers[g]); ++q) {
+            item_group.push_back(g);
+            item_q.push_back((int)q);
+        }
+    std::vector<Partial> parts(item_group.size());
+    parallel_for((int)parts.size(), nthreads, [&](int i) {
+        const int g = item_group[i], T = workers[g];
+        const int n = offsets[g + 1] - offsets[g], R = n / T;
+        const orc_task* t = tasks + offsets[g];
+        std::vector<int32_t> seq(n);
+        std::iota(seq.begin(), seq.end(), 0);
+        /* round 0's permutation of lexicographic rank q: its digits in the
+         * factorial number system pick, position by position, among the
+         * task indices not yet used */
+        std::vector<int32_t> rest(seq.begin(), seq.begin() + T);
+        uint64_t q = (uint64_t)item_q[i];
+        for (int j = 0; j < T; ++j) {
+            const uint64_t f = factorial(T - 1 - j);
+            seq[j] = rest[q / f];
+            rest.erase(rest.begin() + (long)(q / f));
+            q %= f;
+        }
+        uint64_t per_first = 1;
+        for (int r = 1; r < R; ++r) per_first *= factorial(T);
+        uint64_t rank = (uint64_t)item_q[i] * per_first;
+        Partial& pr = parts[i];
+        do {
+            const int64_t ms = simulate_chain(t, T, R, seq.data(), dma_engines[g], nullptr);
+            pr.sum += ms;
+            if (ms < pr.best) { pr.best = ms; pr.best_rank = rank; pr.best_order = seq; }
+            if (ms > pr.worst) { pr.worst = ms; pr.worst_rank = rank; pr.worst_order = seq; }
+            ++rank;
+        } while (next_chain_order(seq, T, R, 1));
+    });
+    size_t i = 0;
+    for (int g = 0; g < G; ++g) {
+        const int T = workers[g], n = offsets[g + 1] - offsets[g], R = n / T;
+        Partial acc;
+        for (uint64_t q = 0; q < factorial(T); ++q, ++i) {
+            const Partial& p = parts[i];
+            acc.sum += p.sum;
+            if (p.best < acc.best) {
+                acc.best = p.best; acc.best_rank = p.best_rank; acc.best_order = p.best_order;
+            }
+            if (p.worst > acc.worst) {
+                acc.worst = p.worst; acc.worst_rank = p.worst_rank;
+                acc.worst_order = p.worst_order;
+            }
+        }
+        fill_stats(acc, n, out + g);
+        uint64_t count = 1;
+        for (int r = 0; r < R; ++r) count *= factorial(T);
+        out[g].mean = (double)acc.sum / (double)count;
+    }
+    return 0;
+}
+
+int orc_exhaustive_chain(const orc_task* tasks, int workers, int rounds, int dma_engines,
+                         orc_stats* out)
+{
+    if (!valid_chain_shape(workers, rounds)) return -1;
+    const int32_t offsets[2] = {0, workers * rounds};
+    const int32_t w = workers, d = dma_engines;
+    return orc_exhaustive_chain_batch(tasks, offsets, &w, 1, &d, 0, out);
 }
 
 int orc_hardware_threads(void) { return resolve_threads(0); }

@@ -78,7 +78,6 @@ int orc_heuristic_batch(const orc_task* tasks, const int32_t* offsets, int G,
                         const int32_t* dma_engines, int nthreads,
                         int32_t* orders_out, int64_t* makespans_out);
 
-/* Number of hardware threads the batch calls use when nthreads <= 0. */
 /* The partial-overlap variant of the model (Sec. 4.2.1; no formula in the
  * paper, so PARITY UNPINNED beyond the properties its tests check): an HtD
  * and a DtH transfer running together each progress at rate_num / rate_den
@@ -92,6 +91,28 @@ int orc_predict_overlap(const orc_task* tasks, int n, const int32_t* order,
 int orc_exhaustive_overlap(const orc_task* tasks, int n, int dma_engines,
                            int32_t rate_num, int32_t rate_den, orc_stats* out);
 
+/* Chained tasks (Sec. 6.1, experiment setup): T = `workers` workers each
+ * submit a chain of N = `rounds` dependent tasks, run as N rounds in
+ * sequence (round r: the r-th task of every worker, in some order), so a
+ * group has (T!)^N orders.  tasks[r * T + w] is worker w's task of round r;
+ * seq lists the n = T * N task indices in run order, round 0's block first
+ * (each block a permutation of its round's indices).  The HtD of a worker's
+ * round-r task waits for the end of the DtH of its round-(r - 1) task.  One
+ * DMA engine: the transfer FIFO holds each round's HtDs then its DtHs, round
+ * after round.  1 <= T <= 8, T * N <= 16.  The exhaustive search enumerates
+ * the (T!)^N orders lexicographically (the rounds as the digits of a
+ * counter, round 0 most significant); ties go to the lowest rank;
+ * mean = (double)sum / (double)(T!)^N; best_order / worst_order hold the
+ * sequence.  Returns 0, or -1 on bad arguments. */
+int orc_predict_chain(const orc_task* tasks, int workers, int rounds, const int32_t* seq,
+                      int dma_engines, int64_t* makespan, int64_t* timeline);
+int orc_exhaustive_chain(const orc_task* tasks, int workers, int rounds, int dma_engines,
+                         orc_stats* out);
+int orc_exhaustive_chain_batch(const orc_task* tasks, const int32_t* offsets,
+                               const int32_t* workers, int G, const int32_t* dma_engines,
+                               int nthreads, orc_stats* out);
+
+/* Number of hardware threads the batch calls use when nthreads <= 0. */
 int orc_hardware_threads(void);
 
 #ifdef __cplusplus

@@ -14,14 +14,32 @@ import itertools
 HTD, KER, DTH = 0, 1, 2
 
 
-def stepped_total_time(tasks, order, dma_engines):
+def stepped_total_time(tasks, order, dma_engines, workers=None):
+    """Total time of `order` (positions -> task indices).  With `workers` set,
+    the group is chained (the paper's experiment setup, Sec. 6.1): task index
+    r * workers + w is worker w's round-r task, the order runs round by
+    round, and a worker's round-r HtD waits until its round-(r - 1) DtH has
+    finished; with one DMA engine each round's HtDs and then its DtHs take
+    their turn in the single transfer queue."""
     n = len(order)
+    chain = workers is not None
+    rounds = n // workers if chain else 1
+    blk = workers if chain else n
     if dma_engines == 2:
         queues = [[(i, HTD) for i in range(n)], [(i, KER) for i in range(n)],
                   [(i, DTH) for i in range(n)]]
     else:
-        queues = [[(i, HTD) for i in range(n)] + [(i, DTH) for i in range(n)],
+        queues = [sum(([(i, HTD) for i in range(r * blk, (r + 1) * blk)] +
+                       [(i, DTH) for i in range(r * blk, (r + 1) * blk)]
+                       for r in range(rounds)), []),
                   [(i, KER) for i in range(n)]]
+    pos_of = {int(t): i for i, t in enumerate(order)}
+
+    def released(i):
+        """A chained task's HtD waits for the previous task of its worker."""
+        t = int(order[i])
+        return not chain or t < workers or (pos_of[t - workers], DTH) in finished
+
     finished = set()
     running = [None] * len(queues)
     t = 0
@@ -33,7 +51,7 @@ def stepped_total_time(tasks, order, dma_engines):
             for qi, q in enumerate(queues):
                 if running[qi] is None and q:
                     i, s = q[0]
-                    if s == HTD or (i, s - 1) in finished:
+                    if (s == HTD and released(i)) or (s != HTD and (i, s - 1) in finished):
                         q.pop(0)
                         d = int(tasks[order[i]][s])
                         if d == 0:
@@ -59,3 +77,11 @@ def stepped_total_time(tasks, order, dma_engines):
 def all_orders(n):
     """All orders in lexicographic order (index == lexicographic rank)."""
     return list(itertools.permutations(range(n)))
+
+
+def all_chain_orders(workers, rounds):
+    """Every chained order, in lexicographic order: the rounds' permutations
+    as the digits of a counter, round 0 most significant."""
+    per_round = [[tuple(r * workers + w for w in p) for p in itertools.permutations(range(workers))]
+                 for r in range(rounds)]
+    return [sum(combo, ()) for combo in itertools.product(*per_round)]

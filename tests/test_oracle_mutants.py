@@ -3,8 +3,9 @@
 Each case plants one mistake in a temporary copy of the oracle source (a
 dropped dependency, a wrong queue layout, transposed stages, a wrong clock
 step, a wrong tie rule, a wrong divisor, a misread term, sign, start time or
-tie rule in the heuristic's cost), builds it, and runs the pin suite against
-it in a child process.  The suite must fail for every mutant.
+tie rule in the heuristic's cost, a wrong link between chained tasks), builds
+it, and runs the pin suites against it in a child process.  They must fail
+for every mutant.
 """
 import os
 import subprocess
@@ -61,7 +62,19 @@ MUTANTS = {
                                  "(cost == best_cost && tasks[j].k < tasks[best].k)"),
     "h3_tie_lower_index": ("(cost == best_cost && tasks[j].k > tasks[best].k)",
                            "(cost == best_cost && false)"),
+    # chained tasks: the link between a worker's tasks, the rank order, the mean
+    "chain_link_dropped": ("ready = t < workers || done[3 * pos_of[t - workers] + DTH];",
+                           "ready = true;"),
+    "chain_link_waits_for_kernel": ("ready = t < workers || done[3 * pos_of[t - workers] + DTH];",
+                                    "ready = t < workers || done[3 * pos_of[t - workers] + KER];"),
+    "chain_link_by_position": ("ready = t < workers || done[3 * pos_of[t - workers] + DTH];",
+                               "ready = t < workers || done[3 * (c.pos - workers) + DTH];"),
+    "chain_last_round_most_significant": ("for (int r = rounds - 1; r >= first_round; --r)",
+                                          "for (int r = first_round; r < rounds; ++r)"),
+    "chain_mean_over_n_factorial": ("out[g].mean = (double)acc.sum / (double)count;",
+                                    "(void)count;"),
 }
+PIN_FILES = ("test_oracle_pins.py", "test_chain_oracle.py")
 
 
 @pytest.mark.slow
@@ -81,6 +94,6 @@ def test_pins_catch_mutant(name, tmp_path):
                     str(mut)], check=True)
     env = dict(os.environ, TM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        *[os.path.join(ROOT, "tests", f) for f in PIN_FILES]],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
