@@ -272,8 +272,14 @@ int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
  *     TM_ECAPACITY (e.g. 64 groups of 8 tasks, or 9 groups of 12 fit);
  *     n <= 12 per group, else TM_ETOOBIG.
  *   It calls no cudaMalloc, cudaFree or other allocating routine.  The first
- *     call on a device (with that device current) looks up the array's
- *     device address once; make it before starting any stream capture.
+ *     call on a device (with that device current) does a one-time set-up:
+ *     it looks up the array's device address and loads every kernel the
+ *     call can launch.  Under lazy module loading (the CUDA default) that
+ *     loading is what places the array in device memory, so make the first
+ *     call before your own allocator reserves the device's memory (or set
+ *     CUDA_MODULE_LOADING=EAGER), and before starting any stream capture.
+ *     After the device's context changes (cudaDeviceReset) the next call
+ *     repeats the set-up, under the same rules.
  *   Every call uses the same array, which keeps the previous call's
  *     contents; each call resets what must start from a known value.  Calls
  *     whose work can overlap on the GPU race on the array: serialise them.

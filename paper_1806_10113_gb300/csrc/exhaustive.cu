@@ -939,6 +939,20 @@ void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
     p.launches = exhaustive_launch_count(p);
 }
 
+cudaError_t exhaustive_preload()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, prep_kernel)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, finalize_kernel)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<3, false>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<3, true>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<4, false>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<4, true>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<5, false>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, enum_kernel<5, true>);
+}
+
 int exhaustive_launch_count(const Plan& p)
 {
     if (p.G == 0) return 0;

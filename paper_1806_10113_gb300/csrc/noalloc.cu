@@ -16,15 +16,25 @@
 //
 // Host code must not use the array's symbol as an address: on the host it
 // names a stand-in object, not device memory.  The first call on each
-// device, with that device current, asks the runtime for the array's device
-// address (cudaGetSymbolAddress) and caches it; make that first call before
-// starting any stream capture.
+// device, with that device current, does the set-up: it asks the runtime
+// for the array's device address (cudaGetSymbolAddress) and loads every
+// kernel the call can launch.  Under lazy module loading (the CUDA default)
+// a module -- this file's, with the 1 MiB array, and the search's -- is only
+// loaded, and its device memory only taken, when first used; doing it all
+// in the set-up means no later call loads anything.  So make the first call
+// before the caller's own allocator reserves the device's memory (or run
+// with CUDA_MODULE_LOADING=EAGER, which loads every module at start-up), and
+// before starting any stream capture.  The set-up is redone if the device's
+// context changes (after cudaDeviceReset, for example); the same rules then
+// apply to the first call after it.
 //
 // All calls share the one array, and it keeps whatever the previous call
 // left there; each call re-initialises the parts that must start from a
 // known value (offsets, work list, reduction words) on its stream before
 // the search.  Two calls whose work overlaps on the GPU race on the array:
 // serialise them (one stream, or events).
+#include <cuda.h>
+
 #include <mutex>
 
 #include "tm_internal.h"
@@ -53,18 +63,51 @@ __global__ void noalloc_init_kernel(InitArgs a, GroupPlan* gp, unsigned long lon
 }
 
 std::mutex g_mu;
-void* g_addr[64] = {};  // device address of g_scratch, per device ordinal
 
+// The context current on the calling thread, from the driver's
+// cuCtxGetCurrent (found through the runtime, so the library does not link
+// the driver library); nullptr if the driver does not offer it.
+CUcontext current_context()
+{
+    using CtxGetCurrent = CUresult (*)(CUcontext*);
+    static const CtxGetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return static_cast<CtxGetCurrent>(nullptr);
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    CUcontext ctx = nullptr;
+    if (fn && fn(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    return ctx;
+}
+
+struct DeviceSetup {
+    CUcontext ctx = nullptr;   // the context the set-up ran in
+    void* addr = nullptr;      // device address of g_scratch in that context
+};
+DeviceSetup g_setup[64];       // per device ordinal
+
+// Device address of g_scratch on `device` (current).  The first call, and
+// the first after the device's context changed, also loads this file's
+// kernel and the search's kernels.
 int scratch_address(int device, unsigned char** out)
 {
     if (device < 0 || device >= 64) return TM_EINVAL;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[device]) {
+    DeviceSetup& su = g_setup[device];
+    if (!su.addr || su.ctx != current_context()) {
         void* p = nullptr;
+        cudaFuncAttributes fa;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return TM_ECUDA;
-        g_addr[device] = p;
+        if (cudaFuncGetAttributes(&fa, noalloc_init_kernel) != cudaSuccess) return TM_ECUDA;
+        if (exhaustive_preload() != cudaSuccess) return TM_ECUDA;
+        su.addr = p;
+        su.ctx = current_context();   // read after the runtime has made its context current
     }
-    *out = static_cast<unsigned char*>(g_addr[device]);
+    *out = static_cast<unsigned char*>(su.addr);
     return TM_OK;
 }
 

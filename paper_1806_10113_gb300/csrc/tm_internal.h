@@ -281,6 +281,11 @@ int exhaustive_launch_count(const Plan& plan);
 // Sets plan.threads and plan.leaves_per_thread for the given device;
 // blocks_per_sm 0 = occupancy limit.
 void exhaustive_partition(Plan& plan, int device, int blocks_per_sm = 0);
+// Loads every kernel launch_exhaustive can launch (prep, each enumeration
+// variant, finalize) on the current device, so that no later launch has to
+// load code (under lazy module loading the first launch of a kernel loads
+// its module, which allocates device memory).
+cudaError_t exhaustive_preload();
 
 cudaError_t launch_predict(const tm_task* d_tasks, const int32_t* d_offsets,
                            int G, const int32_t* d_orders,

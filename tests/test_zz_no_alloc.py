@@ -12,7 +12,9 @@ batches, and compares each result with the plan-based entry point
 tm_exhaustive_batch_dev.  Everything compared is an integer, or a double
 computed by the same expression, so the comparison is exact (the tolerance
 of the other parity tests).  The second call also checks that state left in
-the shared array by the first call does not leak into its result.
+the shared array by the first call does not leak into its result.  Another
+test checks that, once the device is set up, calls leave the device's free
+memory unchanged.
 
 This file is collected last on purpose, and passes both alone in a fresh
 process and after the rest of the suite.
@@ -62,6 +64,28 @@ def test_no_alloc_matches_plan_entry_point_on_two_calls(tm):
         assert got.tobytes() == ref.tobytes()
         st = got.view(tm.STATS_DTYPE)
         assert (st["best"] <= st["worst"]).all()
+
+
+def test_no_alloc_call_takes_no_device_memory(tm):
+    """What the entry point is for: once a device is set up, a call leaves the
+    device's free memory exactly as it was (a cudaMalloc anywhere on its path,
+    even of a few bytes, takes at least one allocation page)."""
+    torch = pytest.importorskip("torch")
+    b = inputs.random_groups(202, [8, 6, 9, 4, 7, 5], hi=2_000_000)
+    dev = torch.device("cuda")
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(b.G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    d_status = torch.zeros(b.G, dtype=torch.int32, device=dev)
+    tm.tm_exhaustive_batch_noalloc(d_tasks, b.offsets, d_dma, d_stats, d_status)   # set-up
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        tm.tm_exhaustive_batch_noalloc(d_tasks, b.offsets, d_dma, d_stats, d_status)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert (d_status.cpu().numpy() == 0).all()
 
 
 def test_no_alloc_rejects_batches_beyond_its_capacity(tm):
