@@ -2,11 +2,13 @@
 
 Makespans, sums, best / worst values and ranks are integers and must match
 exactly; the mean is the same IEEE expression on both sides and must match
-bit for bit.  At full workload sizes (64 groups of 10 tasks, 12-task groups)
-the oracle cannot enumerate every order in seconds, so those tests check
-every reported order with the oracle, sample ranks, and run the full oracle
-on a few groups.
+bit for bit.  The benchmark's workloads are checked in full where the oracle
+finishes in seconds on the host cores: every order of the 64 groups of 10
+tasks under both models, of all 8192 ragged groups, and of two complete
+12-task groups; the remaining 12-task groups have every reported order and a
+sample of ranks checked.
 """
+import itertools
 import math
 import os
 import random
@@ -150,21 +152,86 @@ def check_reported_orders(tm, b, stats, samples=64, seed=0):
             assert ms != s["worst"] or r >= s["worst_rank"]
 
 
+def scheduled_as_benched(tm, b):
+    """The whole scheduling pass (exhaustive search + heuristic) the way the
+    benchmark runs it: tuning picked by the autotuner on this batch, one
+    tm_schedule_batch_dev call on device buffers."""
+    import torch
+    from paper_1806_10113_gb300 import autotune
+    dev = torch.device("cuda")
+    tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
+    plan = tm.Plan(b.offsets, **tuning)
+    d_tasks = torch.from_numpy(b.tasks).to(dev)
+    d_dma = torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(b.G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    d_orders = torch.full((b.tasks.shape[0],), -1, dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(b.G, dtype=torch.int32, device=dev)
+    d_status = torch.full((b.G,), 99, dtype=torch.int32, device=dev)
+    tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status)
+    torch.cuda.synchronize()
+    plan.close()
+    assert (d_status.cpu().numpy() == 0).all()
+    stats = tm.stats_to_dicts(d_stats.cpu().numpy().view(tm.STATS_DTYPE), b.sizes())
+    return stats, d_orders.cpu().numpy(), d_ms.cpu().numpy().astype(np.int64), tuning
+
+
 def test_exhaustive_full_size_sixty_four_groups(tm):
-    """64 groups of 10 tasks (half DK, half DT) under both models, the bench
-    workload, with the bench's launch path (tm_exhaustive_batch)."""
+    """The benchmark's workload and launch: 64 groups of 10 tasks (half DK,
+    half DT) under both models, autotuned, one scheduling pass.  All 128 x
+    10! orders are enumerated by the oracle too, and every statistic and
+    every heuristic order must match."""
     b = inputs.dk_dt_groups(groups=64, n=10, seed=1)
-    stats = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), b.sizes())
-    check_reported_orders(tm, b, stats, samples=32)
+    stats, orders, hms, tuning = scheduled_as_benched(tm, b)
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(stats[g], ref[g], (g, tuning))
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert (orders == ref_orders).all() and (hms == ref_ms).all()
     # the paper's heuristic can never beat the exhaustive best
-    _, hms = tm.tm_heuristic_batch(b.tasks, b.offsets, b.dma)
     assert all(hms[g] >= stats[g]["best"] for g in range(b.G))
 
 
-def test_exhaustive_twelve_tasks_sampled(tm):
-    b = inputs.half_dk_half_dt(groups=2, n=12, seed=3, models=(2, 1))
-    stats = tm.stats_to_dicts(tm.tm_exhaustive_batch(b.tasks, b.offsets, b.dma), b.sizes())
-    check_reported_orders(tm, b, stats, samples=256)
+def oracle_full_by_prefixes(b, g):
+    """Oracle statistics of group g from its two-task-prefix subtrees (all n!
+    orders, spread evenly over the host cores)."""
+    n = int(b.sizes()[g])
+    prefixes = [p for p in itertools.permutations(range(n), 2)]
+    parts = oracle.exhaustive_prefixes(b.tasks, b.offsets, b.dma, [g] * len(prefixes), prefixes)
+    best = min(parts, key=lambda p: (p["best"], p["best_rank"]))
+    worst = min(parts, key=lambda p: (-p["worst"], p["worst_rank"]))
+    total = sum(p["sum"] for p in parts)
+    return {"best": best["best"], "best_rank": best["best_rank"], "best_order": best["best_order"],
+            "worst": worst["worst"], "worst_rank": worst["worst_rank"],
+            "worst_order": worst["worst_order"], "sum": total,
+            "mean": float(total) / float(math.factorial(n))}
+
+
+def test_exhaustive_twelve_tasks_full_oracle(tm):
+    """The 12-task workload (32 groups, half DK / half DT tasks, under 2 and 1
+    DMA engines), autotuned and run as benched.  Two groups, one per device
+    model, are enumerated completely by the oracle (2 x 479,001,600 orders);
+    every other group's reported orders and a sample of ranks are checked."""
+    b = inputs.half_dk_half_dt(groups=32, n=12, seed=3, models=(2, 1))
+    stats, orders, hms, tuning = scheduled_as_benched(tm, b)
+    for g in (0, 32 + 5):
+        assert int(b.dma[g]) == (2 if g < 32 else 1)
+        assert_stats_equal(stats[g], oracle_full_by_prefixes(b, g), (g, tuning))
+    check_reported_orders(tm, b, stats, samples=16)
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert (orders == ref_orders).all() and (hms == ref_ms).all()
+
+
+def test_ragged_8192_groups_full_oracle(tm):
+    """The batched workload: 8192 ragged groups of 4..9 tasks, mixed profiles,
+    engines alternating, autotuned and run as benched; every group's
+    statistics and heuristic order against the oracle's full enumeration."""
+    b = inputs.ragged_mixed(groups=8192, seed=2)
+    stats, orders, hms, tuning = scheduled_as_benched(tm, b)
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(stats[g], ref[g], (g, tuning))
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert (orders == ref_orders).all() and (hms == ref_ms).all()
 
 
 def test_exhaustive_duration_sum_at_int32_limit(tm):
