@@ -292,6 +292,51 @@ int tm_exhaustive_batch_noalloc(const tm_task* d_tasks, const int32_t* h_offsets
                                 int G, const tm_device* d_devs, tm_stats* d_stats,
                                 int32_t* d_status /* may be NULL */, void* stream);
 
+/* ---- chained tasks ------------------------------------------------------------ */
+
+/* The paper's experiment setup (Sec. 6.1): T workers each submit a chain of
+ * N dependent tasks, a worker's next task released only when its previous
+ * task has completely finished; the paper counts (T!)^N orders, i.e. the
+ * group runs as N rounds in sequence, round r holding the r-th task of every
+ * worker in some order.
+ *   Layout: a chained group of n = T * N tasks (1 <= T <=
+ *     TM_CHAIN_MAX_WORKERS, n <= TM_MAX_TASKS); tasks[r * T + w] is worker
+ *     w's round-r task.  An order lists the n task indices round by round:
+ *     positions r T .. r T + T - 1 hold a permutation of round r's indices.
+ *   Model: the queues of Sec. 4.1 filled in that order, plus one dependency:
+ *     the HtD of worker w's round-r task starts after the DtH of its
+ *     round-(r - 1) task has ended.  With one DMA engine each round is
+ *     submitted as a group of its own (its HtDs, then its DtHs, in the one
+ *     transfer queue, round after round).
+ *   Search: all (T!)^N orders, ranked lexicographically (the rounds as the
+ *     digits of a counter, round 0 most significant), reduced as
+ *     tm_exhaustive does (first best / worst rank, exact sum, mean = sum /
+ *     (T!)^N); best_order / worst_order hold task indices (0xFF past n).
+ *   Errors: TM_EINVAL for a bad shape (T, n % T, n) or an order that breaks
+ *     the round layout; the input errors of tm_predict otherwise.  Host
+ *     calls are synchronous and leave outputs untouched on error; _dev calls
+ *     are stream-ordered and report per group in d_status (may be NULL),
+ *     with h_offsets / h_workers the HOST copies of the device arrays. */
+#define TM_CHAIN_MAX_WORKERS 8
+
+int tm_predict_chain(const tm_task* tasks, int workers, int rounds, const int32_t* order,
+                     const tm_device* dev, int32_t* makespan);
+int tm_exhaustive_chain(const tm_task* tasks, int workers, int rounds, const tm_device* dev,
+                        tm_stats* out);
+/* Ragged batch: group g owns tasks[offsets[g] .. offsets[g + 1]) and has
+ * workers[g] workers. */
+int tm_exhaustive_chain_batch(const tm_task* tasks, const int32_t* offsets,
+                              const int32_t* workers, int G, const tm_device* devs,
+                              tm_stats* out);
+int tm_exhaustive_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                                  const int32_t* h_offsets, const int32_t* d_workers,
+                                  const int32_t* h_workers, int G, const tm_device* d_devs,
+                                  tm_stats* d_stats, int32_t* d_status, void* stream);
+int tm_predict_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                               const int32_t* d_workers, int G, const int32_t* d_orders,
+                               const tm_device* d_devs, int32_t* d_makespans, int32_t* d_status,
+                               void* stream);
+
 /* ---- partial-overlap variant of the model --------------------------------- */
 
 /* The paper's simulator also slows down an HtD and a DtH transfer that run
@@ -362,6 +407,7 @@ int tm_exhaustive_overlap_batch_dev(const tm_task* d_tasks, const int32_t* d_off
 #define TM_RANKER_FEATURES 32
 #define TM_RANKER_PARAMS 37377
 #define TM_BEAM_MAX_WIDTH 64
+#define TM_BEAM_MAX_REFINE_STARTS 8
 
 typedef struct tm_ranker tm_ranker;
 
@@ -420,6 +466,15 @@ int tm_ranker_grad_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
                        const int32_t* d_state_off, const int32_t* d_target,
                        int32_t states, float* d_grad, float* d_loss, void* stream);
 
+/* The forward pass with its hidden layers kept, for tests and inspection:
+ * the logits of `rows` feature rows as tm_ranker_forward_dev, and the
+ * bfloat16 activations a1, a2, a3 (bit patterns) in d_acts [3 x rows x 128],
+ * layer-major, row-major within a layer.  path 0: the tensor-core scoring
+ * kernel of tm_ranker_forward_dev; path 1: the forward kernel of training
+ * (tm_ranker_grad_dev).  d_X and d_acts 16-byte aligned.  Stream-ordered. */
+int tm_ranker_forward_keep_dev(tm_ranker* ranker, const uint16_t* d_X, int64_t rows,
+                               float* d_logits, uint16_t* d_acts, int path, void* stream);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr
  * on the gradient of the last tm_ranker_grad_dev.  Stream-ordered. */
 int tm_ranker_adam_dev(tm_ranker* ranker, float lr, void* stream);
@@ -429,17 +484,42 @@ int tm_ranker_adam_dev(tm_ranker* ranker, float lr, void* stream);
  * each unplaced task, the ranker scores the proposals, and the beam_width
  * (1 .. TM_BEAM_MAX_WIDTH) best by summed log-softmax score survive (ties:
  * lower beam, then lower task index); each beam carries the exact int32
- * engine times of its prefix.  The result is the finished beam with the
- * smallest makespan if it beats the heuristic's order (tm_heuristic_batch_dev,
- * run first), else the heuristic's order: never worse than the heuristic.
- * Writes d_orders_out (task layout), d_makespans_out [G] (may be NULL),
- * d_status [G] (may be NULL) and d_beam_won [G] (may be NULL; 1 where the
- * beam's order was kept).  Stream-ordered. */
+ * engine times of its prefix.
+ * refine_starts = 0: the result is the finished beam with the smallest
+ * makespan if it beats the heuristic's order (tm_heuristic_batch_dev, run
+ * first), else the heuristic's order.
+ * refine_starts = K in 1 .. TM_BEAM_MAX_REFINE_STARTS: the K finished beams
+ * of smallest makespan (ties: lower beam) and the heuristic's order each
+ * start the exact-model descent of tm_refine_batch_dev, and the smallest
+ * result wins (ties: the better-ranked start, the heuristic's last).
+ * Either way the result is never worse than the heuristic and its makespan
+ * is the model's exact value.  Writes d_orders_out (task layout),
+ * d_makespans_out [G] (may be NULL), d_status [G] (may be NULL) and
+ * d_beam_won [G] (may be NULL; 1 where the result came from a beam).
+ * Stream-ordered. */
 int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
                       const int32_t* d_offsets, const int32_t* h_offsets, int G,
-                      const tm_device* d_devs, int beam_width,
+                      const tm_device* d_devs, int beam_width, int refine_starts,
                       int32_t* d_orders_out, int32_t* d_makespans_out,
                       int32_t* d_status, int32_t* d_beam_won, void* stream);
+
+/* Exact-model descent from the caller's orders (no counterpart in the paper;
+ * it polishes the orders of the heuristic, Sec. 5.1, or of the beam
+ * search).  For every group (1 <= n <= TM_MAX_TASKS) it repeatedly applies
+ * the single move that lowers the makespan of the model (Sec. 4.1) the most
+ * -- a swap of two positions, or one task moved to another position at
+ * least two away -- until no move lowers it, or after 64 moves.  Ties go to
+ * the first move in this order: swaps (i, j), i < j, by j then i; then
+ * moves of the task at i to position j, by max(i, j), then i, then j.
+ * d_orders (task layout, a permutation of 0 .. n - 1 per group) is read and
+ * overwritten with the result; d_makespans [G] (may be NULL) receives its
+ * makespan; d_status [G] (may be NULL) receives 0 or the group's error
+ * (TM_EINVAL for an order that is not a permutation, and the input errors
+ * of tm_predict; the group's order is then left as it was).
+ * Stream-ordered. */
+int tm_refine_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets, int G,
+                        const tm_device* d_devs, int32_t* d_orders,
+                        int32_t* d_makespans, int32_t* d_status, void* stream);
 
 /* ---- serving ---------------------------------------------------------------- */
 
@@ -450,7 +530,7 @@ int tm_beam_batch_dev(tm_ranker* ranker, const tm_task* d_tasks,
  * and runs it on that lane's CUDA stream.  Exact lanes give groups of
  * n <= exact_max_n the exhaustive optimum (first best order, as
  * tm_exhaustive_batch_dev); search lanes give larger groups the beam search
- * with `ranker` (tm_beam_batch_dev) if beam_width > 0, else the heuristic
+ * with `ranker` (tm_beam_batch_dev, with refine_starts) if beam_width > 0, else the heuristic
  * (tm_heuristic_batch_dev).  The two kinds run side by side, so a small
  * group never waits behind a long search.  A group's result does not depend
  * on the other groups of its batch.
@@ -474,6 +554,7 @@ typedef struct tm_server_config {
     int32_t exact_max_n;    /* 0..12: groups up to this size are solved exactly */
     int32_t beam_width;     /* 0..64; 0: heuristic for the larger groups */
     tm_tuning tuning;       /* exhaustive-search knobs (fuse_finalize must not be 1) */
+    int32_t refine_starts;  /* 0..TM_BEAM_MAX_REFINE_STARTS: as tm_beam_batch_dev */
 } tm_server_config;
 
 #define TM_METHOD_EXHAUSTIVE 0

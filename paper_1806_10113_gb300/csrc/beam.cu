@@ -20,6 +20,7 @@
 
 #include "rank_features.cuh"
 #include "ranker.h"
+#include "refine.cuh"
 #include "tm_device.cuh"
 
 namespace tmgpu {
@@ -38,6 +39,7 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 constexpr int kMaxCand = 64 * 16;   // beam width <= 64, tasks <= 16
+constexpr int kMaxRefineStarts = TM_BEAM_MAX_REFINE_STARTS;
 
 __device__ __forceinline__ int slot_task(uint32_t used, int n, int slot)
 {
@@ -306,6 +308,87 @@ __global__ void beam_finish_kernel(const int32_t* __restrict__ offsets,
     if (beam_won) beam_won[g] = use_beam ? 1 : 0;
 }
 
+// The finish with the exact-model descent of refine.cuh: one block per group,
+// warp w < K starts from the finished beam of rank w (smallest makespan
+// first, ties to the lower beam), warp K from the heuristic's order (already
+// in `orders`); each warp descends, and the smallest result wins (ties: the
+// lower warp).  beam_won[g] = 1 where the winner started from a beam.
+__global__ void __launch_bounds__(32 * (kMaxRefineStarts + 1))
+beam_refine_kernel(const tm_task* __restrict__ tasks, const int32_t* __restrict__ offsets,
+                   const tm_device* __restrict__ devs, const int32_t* __restrict__ status,
+                   const BeamState* __restrict__ st, int B, int K,
+                   const int32_t* __restrict__ heur_ms, int32_t* __restrict__ orders,
+                   int32_t* __restrict__ ms, int32_t* __restrict__ beam_won)
+{
+    __shared__ int4 s_rows[16];
+    __shared__ int4 s_pre[kMaxRefineStarts + 1][17];
+    __shared__ unsigned long long s_key[64];
+    __shared__ unsigned long long s_res[kMaxRefineStarts + 1];
+    __shared__ unsigned long long s_ord[kMaxRefineStarts + 1];
+    const int g = blockIdx.x;
+    if (status[g] != 0) return;   // the whole block
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    const int dma = devs[g].dma_engines;
+    if (threadIdx.x < n) {
+        const tm_task t = tasks[off + threadIdx.x];
+        s_rows[threadIdx.x] = make_int4(t.htd, t.k, t.dth, 0);
+    }
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const BeamState x = st[(size_t)g * B + b];
+        s_key[b] = ((unsigned long long)(x.alive ? (uint32_t)x.d : 0xFFFFFFFFu) << 32) | (uint32_t)b;
+    }
+    __syncthreads();
+    int32_t hs = 0;
+    for (int p = 0; p < n; ++p) hs += s_rows[p].x;
+    const int32_t dinit = dma == 1 ? hs : 0;
+    uint64_t o = 0;
+    int32_t cur = INT32_MAX;
+    bool have = false;
+    if (w < K) {
+        // the beam whose key has rank w among the B keys
+        for (int b = lane; b < B; b += 32) {
+            const unsigned long long kb = s_key[b];
+            int rank = 0;
+            for (int c = 0; c < B; ++c) rank += s_key[c] < kb;
+            if (rank == w && (kb >> 32) != 0xFFFFFFFFull) {
+                have = true;
+                cur = (int32_t)(kb >> 32);
+                o = st[(size_t)g * B + b].order;
+            }
+        }
+        const unsigned who = __ballot_sync(0xFFFFFFFFu, have);
+        if (who) {
+            const int src = __ffs(who) - 1;
+            o = __shfl_sync(0xFFFFFFFFu, o, src);
+            cur = __shfl_sync(0xFFFFFFFFu, cur, src);
+            have = true;
+        }
+    } else {
+        const int e = lane < n ? orders[off + lane] : 0;
+        for (int p = 0; p < n; ++p)
+            o |= (uint64_t)(__shfl_sync(0xFFFFFFFFu, e, p) & 0xF) << (4 * p);
+        cur = heur_ms[g];
+        have = true;
+    }
+    if (have) refine::descend(&o, &cur, n, dinit, s_rows, s_pre[w], lane);
+    if (lane == 0) {
+        s_res[w] = have ? (((unsigned long long)(uint32_t)cur << 32) | (uint32_t)w) : ~0ull;
+        s_ord[w] = o;
+    }
+    __syncthreads();
+    if (w != 0) return;
+    unsigned long long best = ~0ull;
+    for (int v = 0; v <= K; ++v) best = min(best, s_res[v]);
+    const int win = (int)(best & 0xFFFFFFFFull);
+    const uint64_t bo = s_ord[win];
+    if (lane < n) orders[off + lane] = (int32_t)((bo >> (4 * lane)) & 0xF);
+    if (lane == 0) {
+        if (ms) ms[g] = (int32_t)(best >> 32);
+        if (beam_won) beam_won[g] = win < K ? 1 : 0;
+    }
+}
+
 // ---- training rows ----------------------------------------------------------
 
 // Exclusive prefix sums over groups of the training rows (n (n + 1) / 2 - 1
@@ -498,6 +581,17 @@ cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const voi
     beam_finish_kernel<<<(G + 127) / 128, 128, 0, s>>>(offsets, status,
                                                        static_cast<const BeamState*>(st), G, B,
                                                        heur_ms, orders, ms, beam_won);
+    return cudaGetLastError();
+}
+
+cudaError_t beam_refine(const tm_task* tasks, const int32_t* offsets, const tm_device* devs,
+                        const int32_t* status, const void* st, int G, int B, int K,
+                        const int32_t* heur_ms, int32_t* orders, int32_t* ms, int32_t* beam_won,
+                        cudaStream_t s)
+{
+    beam_refine_kernel<<<G, 32 * (K + 1), 0, s>>>(tasks, offsets, devs, status,
+                                                  static_cast<const BeamState*>(st), B, K, heur_ms,
+                                                  orders, ms, beam_won);
     return cudaGetLastError();
 }
 

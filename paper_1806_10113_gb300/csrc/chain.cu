@@ -1,0 +1,742 @@
+// chain.cu -- chained tasks (Sec. 6.1, experiment setup): T workers each
+// submit a chain of N dependent tasks, and a worker's next task is released
+// only when its previous one has completely finished.  The paper counts
+// (T!)^N orders: the group runs as N rounds in sequence, round r holding the
+// r-th task of every worker in some order.  Task index r * T + w is worker
+// w's round-r task; an order lists the n = T * N task indices round by round.
+//
+// Model.  The FIFO queues of the plain model (tm_device.cuh), filled in
+// order, with one more dependency: the HtD of worker w's round-r task starts
+// only after the DtH of its round-(r - 1) task, whose end c_w is known when
+// round r starts.  Appending worker w's task of the current round:
+//     h' = max(h, c_w) + htd      k' = max(k, h') + k      d' = max(d, k') + dth
+// With one DMA engine each round is submitted as a group of its own (its
+// HtDs, then its DtHs, in the one transfer queue), so when round r starts
+// the transfer engine is free at d, every c_w <= d, and the round's first
+// DtH cannot start before its last HtD:  h = d,  d = d + (sum of the round's
+// HtDs).  All values stay below the group's duration sum, checked to fit in
+// int32.
+//
+// Enumeration.  Orders are ranked lexicographically, i.e. as a counter whose
+// digits are the rounds' permutations (round 0 most significant).  The last
+// m = min(T, 4) positions (the tail, all in the last round) vary fastest, so
+// a BLOCK of m! consecutive ranks shares the first n - m positions.  A
+// thread takes a contiguous range of blocks: it unranks the first one,
+// evaluates the tail's m! orders straight-line (depth-first, the engine
+// state of each tail prefix shared), advances the counter to the next block
+// (a nibble-packed next-permutation of the last round's head, carrying into
+// earlier rounds) and recomputes the engine states from the first changed
+// position only, from per-position snapshots.  Per-thread best / worst with
+// the first rank and the exact sum go to per-group 64-bit key atomics.
+//
+//   chain_prep_kernel      per group: checks, reduction words
+//   chain_enum_kernel      every order of every group
+//   chain_finalize_kernel  reduction words -> tm_stats (orders unranked)
+//   chain_predict_kernel   one given order per group
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "tm_device.cuh"
+
+namespace tmgpu {
+namespace {
+
+constexpr int kChainBlock = 128;
+constexpr int kChainMaxWorkers = 8;
+
+struct ChainInfo {
+    int32_t off;      // first task
+    int32_t T;        // workers
+    int32_t R;        // rounds
+    int32_t dma;      // 1 or 2
+    int32_t status;   // 0 or a tm_status code
+    int32_t pad[3];
+};
+
+__host__ __device__ inline int chain_tail(int T) { return T < 4 ? T : 4; }
+
+// (T!)^R orders, or 0 for a shape outside 1 <= T <= 8, T * R <= 16.
+__host__ __device__ inline uint64_t chain_orders(int T, int R)
+{
+    if (T < 1 || T > kChainMaxWorkers || R < 1 || T * R > TM_MAX_TASKS) return 0;
+    uint64_t c = 1;
+    for (int r = 0; r < R; ++r) c *= factorial_u64(T);
+    return c;
+}
+
+// Per-group checks (shape, durations, device model); 0 or a tm_status code.
+__device__ int check_chain(const tm_task* tasks, int n, int T, int dma)
+{
+    if (T < 1 || T > kChainMaxWorkers || n < 1 || n > TM_MAX_TASKS || n % T != 0)
+        return TM_EINVAL;
+    int32_t hs = 0, dinit = 0;
+    return check_group(tasks, n, dma, TM_MAX_TASKS, &hs, &dinit);
+}
+
+__device__ __forceinline__ Eng step_c(Eng s, int32_t c, int4 t)
+{
+    Eng r;
+    r.h = max(s.h, c) + t.x;
+    r.k = max(s.k, r.h) + t.y;
+    r.d = max(s.d, r.k) + t.z;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t nib32(uint32_t w, int i) { return (w >> (4 * i)) & 0xFu; }
+
+// Lexicographic next permutation of the T nibbles of w.  Returns the index
+// of the first changed nibble, or -1 when w was the last permutation (it is
+// then reset to the first, ascending).
+__device__ int next_perm_nib(uint32_t& w, int T)
+{
+    int i = T - 2;
+    while (i >= 0 && nib32(w, i) >= nib32(w, i + 1)) --i;
+    if (i < 0) {
+        uint32_t a = 0;
+        for (int e = 0; e < T; ++e) a |= (uint32_t)e << (4 * e);
+        w = a;
+        return -1;
+    }
+    int j = T - 1;
+    while (nib32(w, j) <= nib32(w, i)) --j;
+    const uint32_t x = (nib32(w, i) ^ nib32(w, j));
+    w ^= (x << (4 * i)) | (x << (4 * j));
+    for (int a = i + 1, b = T - 1; a < b; ++a, --b) {   // reverse i + 1 .. T - 1
+        const uint32_t y = nib32(w, a) ^ nib32(w, b);
+        w ^= (y << (4 * a)) | (y << (4 * b));
+    }
+    return i;
+}
+
+// Permutation of T workers with lexicographic rank q (q < T!), as nibbles.
+__device__ uint32_t unrank_round(uint32_t q, int T)
+{
+    uint64_t list = nib_identity(T);
+    uint32_t w = 0;
+    for (int i = 0; i < T; ++i) {
+        const int k = T - 1 - i;
+        const uint32_t c = min(div_fact(q, k), (uint32_t)k);
+        q -= c * (uint32_t)factorial_u64(k);
+        w |= (uint32_t)nib_get(list, (int)c) << (4 * i);
+        list = nib_remove(list, (int)c);
+    }
+    return w;
+}
+
+__device__ __forceinline__ uint32_t inverse_nib(uint32_t w, int T)
+{
+    uint32_t inv = 0;
+    for (int i = 0; i < T; ++i) inv |= (uint32_t)i << (4 * nib32(w, i));
+    return inv;
+}
+
+__global__ void chain_prep_kernel(const tm_task* __restrict__ tasks,
+                                  const int32_t* __restrict__ offsets,
+                                  const int32_t* __restrict__ workers, int G,
+                                  const tm_device* __restrict__ devs, ChainInfo* __restrict__ info,
+                                  unsigned long long* __restrict__ acc, int32_t* __restrict__ status)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int off = offsets[g], n = offsets[g + 1] - off, T = workers[g];
+    const int dma = devs[g].dma_engines;
+    const int rc = check_chain(tasks + off, n, T, dma);
+    ChainInfo ci;
+    ci.off = off;
+    ci.T = T;
+    ci.R = rc == 0 ? n / T : 0;
+    ci.dma = dma;
+    ci.status = rc;
+    ci.pad[0] = ci.pad[1] = ci.pad[2] = 0;
+    info[g] = ci;
+    acc[4 * (size_t)g + 0] = ~0ull;
+    acc[4 * (size_t)g + 1] = 0ull;
+    acc[4 * (size_t)g + 2] = 0ull;
+    if (status && rc != 0) status[g] = rc;
+}
+
+// One thread's view of one group: the current order (worker of every
+// position, nibbles), the engine state after every position, the inverse of
+// every round, and the last round's task rows with their release times c_w.
+struct ChainWalk {
+    int T, R, n, m, dma, off;
+    uint64_t seq;            // worker at position p in bits 4p .. 4p + 3
+    int32_t sh[TM_MAX_TASKS], sk[TM_MAX_TASKS], sd[TM_MAX_TASKS];
+    uint32_t inv[TM_MAX_TASKS];
+};
+
+// Sum of the HtDs of round r.
+__device__ __forceinline__ int32_t round_htd(const tm_task* __restrict__ tasks, int off, int T,
+                                             int r)
+{
+    int32_t s = 0;
+    for (int w = 0; w < T; ++w) s += tasks[off + r * T + w].htd;
+    return s;
+}
+
+// Recomputes the states from position p0 up to the start of the tail
+// (n - m), entering rounds on the way; when it enters the last round it
+// refills the last round's rows (with c_w) in `last`.  Returns the state at
+// the start of the tail.
+__device__ Eng chain_resume(ChainWalk& cw, int p0, const tm_task* __restrict__ tasks,
+                            int4* __restrict__ last)
+{
+    const int T = cw.T, head_end = cw.n - cw.m, last_start = (cw.R - 1) * T;
+    Eng s = p0 == 0 ? Eng{0, 0, 0} : Eng{cw.sh[p0 - 1], cw.sk[p0 - 1], cw.sd[p0 - 1]};
+    // the round that starts at position p (p == r T) is entered before p
+    auto enter = [&](int r) {
+        if (cw.dma == 1) {
+            s.h = s.d;
+            s.d += round_htd(tasks, cw.off, T, r);
+        }
+        if (r == cw.R - 1) {
+            for (int w = 0; w < T; ++w) {
+                const tm_task t = tasks[cw.off + r * T + w];
+                const int32_t c = r == 0 ? 0 : cw.sd[(r - 1) * T + min((int)nib32(cw.inv[r - 1], w), T - 1)];
+                last[w * kChainBlock] = make_int4(t.htd, t.k, t.dth, c);
+            }
+        }
+    };
+    for (int p = p0; p < head_end; ++p) {
+        const int r = p / T, i = p - r * T;
+        if (i == 0) enter(r);
+        const int w = (int)((cw.seq >> (4 * p)) & 0xF);
+        int4 row;
+        if (r == cw.R - 1) {
+            row = last[w * kChainBlock];
+        } else {
+            const tm_task t = tasks[cw.off + r * T + w];
+            const int32_t c = r == 0 ? 0 : cw.sd[(r - 1) * T + min((int)nib32(cw.inv[r - 1], w), T - 1)];
+            row = make_int4(t.htd, t.k, t.dth, c);
+        }
+        s = step_c(s, row.w, row);
+        cw.sh[p] = s.h;
+        cw.sk[p] = s.k;
+        cw.sd[p] = s.d;
+        if (i == T - 1)
+            cw.inv[r] = inverse_nib((uint32_t)(cw.seq >> (4 * r * T)) & (T >= 8 ? 0xFFFFFFFFu : ((1u << (4 * T)) - 1u)), T);
+    }
+    if (head_end == last_start && p0 <= head_end) enter(cw.R - 1);   // no head in the last round
+    return s;
+}
+
+// Per-thread reduction of one group.
+struct ChainAcc {
+    int32_t best, worst;
+    uint32_t brank, wrank;
+    unsigned long long sum;
+};
+
+__device__ __forceinline__ void take_pair(ChainAcc& a, int32_t m0, int32_t m1, uint32_t rank)
+{
+    const int32_t mn = min(m0, m1), mx = max(m0, m1);
+    if (mn < a.best) { a.best = mn; a.brank = rank + (m0 != mn); }
+    if (mx > a.worst) { a.worst = mx; a.wrank = rank + (m0 != mx); }
+    a.sum += (unsigned long long)((uint32_t)m0 + (uint32_t)m1);
+}
+
+__device__ __forceinline__ void take_one(ChainAcc& a, int32_t m0, uint32_t rank)
+{
+    if (m0 < a.best) { a.best = m0; a.brank = rank; }
+    if (m0 > a.worst) { a.worst = m0; a.wrank = rank; }
+    a.sum += (unsigned long long)(uint32_t)m0;
+}
+
+// The two orders of the last two workers u < v from state s.
+__device__ __forceinline__ void tail2(Eng s, const int4* __restrict__ last, int u, int v,
+                                      ChainAcc& a, uint32_t rank)
+{
+    const int4 ru = last[u * kChainBlock], rv = last[v * kChainBlock];
+    const int32_t m_uv = step_c(step_c(s, ru.w, ru), rv.w, rv).d;
+    const int32_t m_vu = step_c(step_c(s, rv.w, rv), ru.w, ru).d;
+    take_pair(a, m_uv, m_vu, rank);
+}
+
+// The 6 orders of workers a < b < c (lexicographic: abc acb bac bca cab cba).
+__device__ __forceinline__ void tail3(Eng s, const int4* __restrict__ last, int x0, int x1,
+                                      int x2, ChainAcc& a, uint32_t rank)
+{
+    const int4 r0 = last[x0 * kChainBlock], r1 = last[x1 * kChainBlock],
+               r2 = last[x2 * kChainBlock];
+    tail2(step_c(s, r0.w, r0), last, x1, x2, a, rank);
+    tail2(step_c(s, r1.w, r1), last, x0, x2, a, rank + 2);
+    tail2(step_c(s, r2.w, r2), last, x0, x1, a, rank + 4);
+}
+
+__device__ __forceinline__ void tail4(Eng s, const int4* __restrict__ last, int x0, int x1,
+                                      int x2, int x3, ChainAcc& a, uint32_t rank)
+{
+    const int4 r0 = last[x0 * kChainBlock], r1 = last[x1 * kChainBlock],
+               r2 = last[x2 * kChainBlock], r3 = last[x3 * kChainBlock];
+    tail3(step_c(s, r0.w, r0), last, x1, x2, x3, a, rank);
+    tail3(step_c(s, r1.w, r1), last, x0, x2, x3, a, rank + 6);
+    tail3(step_c(s, r2.w, r2), last, x0, x1, x3, a, rank + 12);
+    tail3(step_c(s, r3.w, r3), last, x0, x1, x2, a, rank + 18);
+}
+
+__device__ void flush(ChainAcc& a, unsigned long long* __restrict__ acc, int g)
+{
+    if (a.best == INT32_MAX) return;
+    atomicMin(&acc[4 * (size_t)g + 0],
+              ((unsigned long long)(uint32_t)a.best << 32) | a.brank);
+    atomicMax(&acc[4 * (size_t)g + 1],
+              ((unsigned long long)(uint32_t)a.worst << 32) | (0xFFFFFFFFu - a.wrank));
+    atomicAdd(&acc[4 * (size_t)g + 2], a.sum);
+    a = ChainAcc{INT32_MAX, -1, 0u, 0u, 0ull};
+}
+
+__global__ void __launch_bounds__(kChainBlock)
+chain_enum_kernel(const unsigned long long* __restrict__ block_base, int G,
+                  const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
+                  unsigned long long* __restrict__ acc, unsigned long long per_thread)
+{
+    __shared__ int4 s_last[kChainMaxWorkers * kChainBlock];
+    int4* last = s_last + threadIdx.x;
+    const unsigned long long total = block_base[G];
+    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long b = t * per_thread;
+    const unsigned long long b_end = min(total, b + per_thread);
+    if (b >= b_end) return;
+    int g = 0;
+    {   // the last group whose first block is <= b
+        int lo = 0, hi = G;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (block_base[mid] <= b) lo = mid; else hi = mid;
+        }
+        g = lo;
+    }
+    ChainWalk cw;
+    ChainAcc a{INT32_MAX, -1, 0u, 0u, 0ull};
+    while (b < b_end) {
+        while (b >= block_base[g + 1]) ++g;   // groups without orders have no blocks
+        const ChainInfo ci = info[g];
+        if (ci.status != 0) {                 // rejected by the prep kernel
+            b = min(b_end, (unsigned long long)block_base[g + 1]);
+            continue;
+        }
+        cw.T = ci.T;
+        cw.R = ci.R;
+        cw.n = ci.T * ci.R;
+        cw.m = chain_tail(ci.T);
+        cw.dma = ci.dma;
+        cw.off = ci.off;
+        const int T = cw.T, m = cw.m;
+        // unrank the group's block b - base: rank (b - base) m!, round by round
+        const uint32_t F = (uint32_t)factorial_u64(T);
+        const uint32_t mf = (uint32_t)factorial_u64(m);
+        uint32_t rank = (uint32_t)(b - block_base[g]) * mf;
+        {
+            uint32_t q = rank;
+            cw.seq = 0;
+            for (int r = cw.R - 1; r >= 0; --r) {
+                const uint32_t digit = q % F;
+                q /= F;
+                cw.seq |= (uint64_t)unrank_round(digit, T) << (4 * r * T);
+            }
+        }
+        const unsigned long long g_end = min(b_end, (unsigned long long)block_base[g + 1]);
+        Eng s = chain_resume(cw, 0, tasks, last);
+        const int head_end = cw.n - m, last_start = (cw.R - 1) * T;
+        for (;;) {
+            // the tail: the last round's workers not in its head, ascending
+            uint32_t freew = (1u << T) - 1u;
+            for (int p = last_start; p < head_end; ++p) freew &= ~(1u << ((cw.seq >> (4 * p)) & 0xF));
+            const int x0 = __ffs(freew) - 1;
+            freew &= freew - 1;
+            if (m == 4) {
+                const int x1 = __ffs(freew) - 1; freew &= freew - 1;
+                const int x2 = __ffs(freew) - 1; freew &= freew - 1;
+                const int x3 = __ffs(freew) - 1;
+                tail4(s, last, x0, x1, x2, x3, a, rank);
+            } else if (m == 3) {
+                const int x1 = __ffs(freew) - 1; freew &= freew - 1;
+                const int x2 = __ffs(freew) - 1;
+                tail3(s, last, x0, x1, x2, a, rank);
+            } else if (m == 2) {
+                tail2(s, last, x0, __ffs(freew) - 1, a, rank);
+            } else {
+                const int4 r0 = last[x0 * kChainBlock];
+                take_one(a, step_c(s, r0.w, r0).d, rank);
+            }
+            rank += mf;
+            if (++b >= g_end) break;
+            // next block: the last round's head advances (its tail taken as
+            // descending, i.e. exhausted); a round that wraps carries into
+            // the round before it
+            int p0 = -1;
+            for (int r = cw.R - 1; r >= 0 && p0 < 0; --r) {
+                uint32_t w = (uint32_t)(cw.seq >> (4 * r * T)) &
+                             (T >= 8 ? 0xFFFFFFFFu : ((1u << (4 * T)) - 1u));
+                if (r == cw.R - 1) {
+                    // tail descending: reverse its ascending nibbles
+                    for (int x = T - m, y = T - 1; x < y; ++x, --y) {
+                        const uint32_t z = nib32(w, x) ^ nib32(w, y);
+                        w ^= (z << (4 * x)) | (z << (4 * y));
+                    }
+                }
+                const int i = next_perm_nib(w, T);
+                const uint64_t maskr = (T >= 8 ? 0xFFFFFFFFull : ((1ull << (4 * T)) - 1ull)) << (4 * r * T);
+                cw.seq = (cw.seq & ~maskr) | ((uint64_t)w << (4 * r * T));
+                if (i >= 0) p0 = r * T + i;
+            }
+            s = chain_resume(cw, p0, tasks, last);
+        }
+        flush(a, acc, g);
+    }
+}
+
+// Order of rank `rank` of a chained group as task indices, and its makespan.
+__device__ int32_t chain_order_of_rank(const tm_task* __restrict__ tasks, const ChainInfo& ci,
+                                       uint32_t rank, uint8_t* order_out)
+{
+    const int T = ci.T, R = ci.R;
+    const uint32_t F = (uint32_t)factorial_u64(T);
+    uint32_t rw[TM_MAX_TASKS];
+    for (int r = R - 1; r >= 0; --r) {
+        rw[r] = unrank_round(rank % F, T);
+        rank /= F;
+    }
+    Eng s{0, 0, 0};
+    int32_t dend[TM_MAX_TASKS];
+    for (int r = 0; r < R; ++r) {
+        if (ci.dma == 1) {
+            s.h = s.d;
+            s.d += round_htd(tasks, ci.off, T, r);
+        }
+        const uint32_t prev_inv = r ? inverse_nib(rw[r - 1], T) : 0u;
+        for (int i = 0; i < T; ++i) {
+            const int w = (int)nib32(rw[r], i);
+            const tm_task t = tasks[ci.off + r * T + w];
+            const int32_t c = r ? dend[(r - 1) * T + (int)nib32(prev_inv, w)] : 0;
+            s = step_c(s, c, make_int4(t.htd, t.k, t.dth, 0));
+            dend[r * T + i] = s.d;
+            if (order_out) order_out[r * T + i] = (uint8_t)(r * T + w);
+        }
+    }
+    return s.d;
+}
+
+__global__ void chain_finalize_kernel(const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
+                                      int G, const unsigned long long* __restrict__ acc,
+                                      tm_stats* __restrict__ stats, int32_t* __restrict__ status)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const ChainInfo ci = info[g];
+    if (ci.status != 0) return;
+    const unsigned long long kmin = acc[4 * (size_t)g], kmax = acc[4 * (size_t)g + 1];
+    tm_stats st;
+    st.best = (int32_t)(kmin >> 32);
+    st.worst = (int32_t)(kmax >> 32);
+    st.sum = (int64_t)acc[4 * (size_t)g + 2];
+    st.mean = (double)st.sum / (double)chain_orders(ci.T, ci.R);
+    st.best_rank = (uint32_t)kmin;
+    st.worst_rank = 0xFFFFFFFFu - (uint32_t)kmax;
+    for (int i = 0; i < 16; ++i) st.best_order[i] = st.worst_order[i] = 0xFF;
+    const int32_t b = chain_order_of_rank(tasks, ci, (uint32_t)st.best_rank, st.best_order);
+    const int32_t w = chain_order_of_rank(tasks, ci, (uint32_t)st.worst_rank, st.worst_order);
+    stats[g] = st;
+    // the unranked orders must reproduce the reduced values
+    if (status) status[g] = (b == st.best && w == st.worst) ? 0 : TM_ECUDA;
+}
+
+__global__ void chain_predict_kernel(const tm_task* __restrict__ tasks,
+                                     const int32_t* __restrict__ offsets,
+                                     const int32_t* __restrict__ workers, int G,
+                                     const int32_t* __restrict__ orders,
+                                     const tm_device* __restrict__ devs,
+                                     int32_t* __restrict__ makespans, int32_t* __restrict__ status)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int off = offsets[g], n = offsets[g + 1] - off, T = workers[g];
+    const int dma = devs[g].dma_engines;
+    int rc = check_chain(tasks + off, n, T, dma);
+    // each round's block must be a permutation of that round's task indices
+    uint32_t seen = 0;
+    for (int p = 0; rc == 0 && p < n; ++p) {
+        const int e = orders[off + p];
+        if (e < 0 || e >= n || e / T != p / T || ((seen >> e) & 1u)) rc = TM_EINVAL;
+        else seen |= 1u << e;
+    }
+    if (rc != 0) {
+        if (status) status[g] = rc;
+        return;
+    }
+    const int R = n / T;
+    Eng s{0, 0, 0};
+    int32_t dend[TM_MAX_TASKS];
+    int pos_prev[kChainMaxWorkers];
+    int pos_cur[kChainMaxWorkers];
+    for (int r = 0; r < R; ++r) {
+        if (dma == 1) {
+            s.h = s.d;
+            s.d += round_htd(tasks, off, T, r);
+        }
+        for (int i = 0; i < T; ++i) {
+            const int e = orders[off + r * T + i], w = e - r * T;
+            const tm_task t = tasks[off + e];
+            const int32_t c = r ? dend[(r - 1) * T + pos_prev[w]] : 0;
+            s = step_c(s, c, make_int4(t.htd, t.k, t.dth, 0));
+            dend[r * T + i] = s.d;
+            pos_cur[w] = i;
+        }
+        for (int w = 0; w < T; ++w) pos_prev[w] = pos_cur[w];
+    }
+    makespans[g] = s.d;
+    if (status) status[g] = 0;
+}
+
+struct ChainScratch {
+    void* p = nullptr;
+    size_t cap = 0;
+    int device = -1;
+    std::vector<unsigned long long> h_base;
+};
+thread_local ChainScratch t_chain;
+
+}  // namespace
+
+int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int32_t* h_offsets,
+                     const int32_t* d_workers, const int32_t* h_workers, int G,
+                     const tm_device* d_devs, tm_stats* d_stats, int32_t* d_status,
+                     cudaStream_t s)
+{
+    if (G == 0) return TM_OK;
+    ChainScratch& sc = t_chain;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_base = al((size_t)(G + 1) * 8), b_info = al((size_t)G * sizeof(ChainInfo)),
+                 b_acc = al((size_t)G * 32);
+    const size_t need = b_base + b_info + b_acc;
+    if (sc.device != dev || sc.cap < need) {
+        if (sc.p && sc.device == dev) {
+            cudaDeviceSynchronize();   // earlier calls may still use it
+            cudaFree(sc.p);
+        }
+        sc.p = nullptr;
+        sc.cap = 0;
+        if (cudaMalloc(&sc.p, need) != cudaSuccess) { sc.p = nullptr; return TM_ENOMEM; }
+        sc.cap = need;
+        sc.device = dev;
+    }
+    unsigned char* p = static_cast<unsigned char*>(sc.p);
+    unsigned long long* d_base = reinterpret_cast<unsigned long long*>(p);
+    ChainInfo* d_info = reinterpret_cast<ChainInfo*>(p + b_base);
+    unsigned long long* d_acc = reinterpret_cast<unsigned long long*>(p + b_base + b_info);
+    // blocks of m! orders per group (0 for a shape the prep kernel rejects)
+    sc.h_base.assign((size_t)G + 1, 0ull);
+    for (int g = 0; g < G; ++g) {
+        const int n = h_offsets[g + 1] - h_offsets[g], T = h_workers[g];
+        const uint64_t orders = (T >= 1 && n % T == 0) ? chain_orders(T, n / T) : 0;
+        sc.h_base[g + 1] = sc.h_base[g] + (orders ? orders / factorial_u64(chain_tail(T)) : 0);
+    }
+    if (cudaMemcpyAsync(d_base, sc.h_base.data(), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return TM_ECUDA;
+    chain_prep_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_tasks, d_offsets, d_workers, G, d_devs,
+                                                     d_info, d_acc, d_status);
+    const unsigned long long total = sc.h_base[G];
+    if (total > 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_enum_kernel, kChainBlock,
+                                                          0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const unsigned long long resident = (unsigned long long)std::max(sms, 1) * per_sm * kChainBlock;
+        const unsigned long long threads = std::min(total, resident);
+        const unsigned long long per_thread = (total + threads - 1) / threads;
+        const unsigned long long used = (total + per_thread - 1) / per_thread;
+        chain_enum_kernel<<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
+            d_base, G, d_info, d_tasks, d_acc, per_thread);
+    }
+    chain_finalize_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_info, d_tasks, G, d_acc, d_stats,
+                                                         d_status);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+cudaError_t launch_chain_predict(const tm_task* d_tasks, const int32_t* d_offsets,
+                                 const int32_t* d_workers, int G, const int32_t* d_orders,
+                                 const tm_device* d_devs, int32_t* d_makespans, int32_t* d_status,
+                                 cudaStream_t s)
+{
+    if (G == 0) return cudaSuccess;
+    chain_predict_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_tasks, d_offsets, d_workers, G,
+                                                        d_orders, d_devs, d_makespans, d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace tmgpu
+
+// ---- C ABI -------------------------------------------------------------------
+
+namespace {
+
+using namespace tmgpu;
+
+// Host-side checks of one chained group; TM_OK or the error code.
+int check_chain_host(const tm_task* tasks, int n, int T, int dma)
+{
+    if (!tasks || T < 1 || T > kChainMaxWorkers || n < 1 || n > TM_MAX_TASKS || n % T != 0)
+        return TM_EINVAL;
+    if (dma != 1 && dma != 2) return TM_EINVAL;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (tasks[i].htd < 0 || tasks[i].k < 0 || tasks[i].dth < 0) return TM_ENEG;
+        total += (int64_t)tasks[i].htd + tasks[i].k + tasks[i].dth;
+    }
+    return total > INT32_MAX ? TM_EOVERFLOW : TM_OK;
+}
+
+// Device copies of a host batch for the host-pointer calls (grown, never
+// shrunk; one per host thread).
+struct ChainStage {
+    void* p = nullptr;
+    size_t cap = 0;
+    int device = -1;
+    bool ensure(size_t need, int dev)
+    {
+        if (p && cap >= need && device == dev) return true;
+        if (p && device == dev) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc(&p, need) != cudaSuccess) { p = nullptr; return false; }
+        cap = need;
+        device = dev;
+        return true;
+    }
+};
+thread_local ChainStage t_stage;
+
+}  // namespace
+
+extern "C" {
+
+int tm_exhaustive_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                                  const int32_t* h_offsets, const int32_t* d_workers,
+                                  const int32_t* h_workers, int G, const tm_device* d_devs,
+                                  tm_stats* d_stats, int32_t* d_status, void* stream)
+{
+    if (G < 0) return TM_EINVAL;
+    if (G == 0) return TM_OK;
+    if (!d_tasks || !d_offsets || !h_offsets || !d_workers || !h_workers || !d_devs || !d_stats)
+        return TM_EINVAL;
+    if (h_offsets[0] != 0) return TM_EINVAL;
+    for (int g = 0; g < G; ++g)
+        if (h_offsets[g + 1] < h_offsets[g]) return TM_EINVAL;
+    return chain_exhaustive(d_tasks, d_offsets, h_offsets, d_workers, h_workers, G, d_devs,
+                            d_stats, d_status, static_cast<cudaStream_t>(stream));
+}
+
+int tm_predict_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
+                               const int32_t* d_workers, int G, const int32_t* d_orders,
+                               const tm_device* d_devs, int32_t* d_makespans, int32_t* d_status,
+                               void* stream)
+{
+    if (G < 0) return TM_EINVAL;
+    if (G == 0) return TM_OK;
+    if (!d_tasks || !d_offsets || !d_workers || !d_orders || !d_devs || !d_makespans)
+        return TM_EINVAL;
+    return launch_chain_predict(d_tasks, d_offsets, d_workers, G, d_orders, d_devs, d_makespans,
+                                d_status, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? TM_OK
+               : TM_ECUDA;
+}
+
+int tm_exhaustive_chain_batch(const tm_task* tasks, const int32_t* offsets,
+                              const int32_t* workers, int G, const tm_device* devs,
+                              tm_stats* out)
+{
+    if (G < 0 || !offsets || !workers || !devs || (G > 0 && (!tasks || !out))) return TM_EINVAL;
+    if (G == 0) return TM_OK;
+    if (offsets[0] != 0) return TM_EINVAL;
+    for (int g = 0; g < G; ++g) {
+        if (offsets[g + 1] < offsets[g]) return TM_EINVAL;
+        const int rc = check_chain_host(tasks + offsets[g], offsets[g + 1] - offsets[g],
+                                        workers[g], devs[g].dma_engines);
+        if (rc != TM_OK) return rc;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+    const int T = offsets[G];
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_t = al((size_t)T * sizeof(tm_task)), b_o = al((size_t)(G + 1) * 4),
+                 b_w = al((size_t)G * 4), b_d = al((size_t)G * sizeof(tm_device)),
+                 b_s = al((size_t)G * sizeof(tm_stats)), b_st = al((size_t)G * 4);
+    if (!t_stage.ensure(b_t + b_o + b_w + b_d + b_s + b_st, dev)) return TM_ENOMEM;
+    unsigned char* p = static_cast<unsigned char*>(t_stage.p);
+    tm_task* d_tasks = reinterpret_cast<tm_task*>(p);
+    int32_t* d_off = reinterpret_cast<int32_t*>(p + b_t);
+    int32_t* d_w = reinterpret_cast<int32_t*>(p + b_t + b_o);
+    tm_device* d_dv = reinterpret_cast<tm_device*>(p + b_t + b_o + b_w);
+    tm_stats* d_st = reinterpret_cast<tm_stats*>(p + b_t + b_o + b_w + b_d);
+    int32_t* d_status = reinterpret_cast<int32_t*>(p + b_t + b_o + b_w + b_d + b_s);
+    if (cudaMemcpy(d_tasks, tasks, (size_t)T * sizeof(tm_task), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_off, offsets, (size_t)(G + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_w, workers, (size_t)G * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_dv, devs, (size_t)G * sizeof(tm_device), cudaMemcpyHostToDevice) != cudaSuccess)
+        return TM_ECUDA;
+    int rc = chain_exhaustive(d_tasks, d_off, offsets, d_w, workers, G, d_dv, d_st, d_status, 0);
+    if (rc != TM_OK) return rc;
+    std::vector<int32_t> status((size_t)G);
+    if (cudaMemcpy(status.data(), d_status, (size_t)G * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TM_ECUDA;
+    for (int g = 0; g < G; ++g)
+        if (status[g] != 0) return status[g];
+    return cudaMemcpy(out, d_st, (size_t)G * sizeof(tm_stats), cudaMemcpyDeviceToHost) == cudaSuccess
+               ? TM_OK
+               : TM_ECUDA;
+}
+
+int tm_exhaustive_chain(const tm_task* tasks, int workers, int rounds, const tm_device* dev,
+                        tm_stats* out)
+{
+    if (!tasks || !dev || !out || workers < 1 || rounds < 1 || workers * rounds > TM_MAX_TASKS)
+        return TM_EINVAL;
+    const int32_t offsets[2] = {0, workers * rounds};
+    return tm_exhaustive_chain_batch(tasks, offsets, &workers, 1, dev, out);
+}
+
+int tm_predict_chain(const tm_task* tasks, int workers, int rounds, const int32_t* order,
+                     const tm_device* dev, int32_t* makespan)
+{
+    if (!tasks || !order || !dev || !makespan || workers < 1 || rounds < 1 ||
+        workers * rounds > TM_MAX_TASKS)
+        return TM_EINVAL;
+    const int n = workers * rounds;
+    int rc = check_chain_host(tasks, n, workers, dev->dma_engines);
+    if (rc != TM_OK) return rc;
+    uint32_t seen = 0;
+    for (int p = 0; p < n; ++p) {
+        const int e = order[p];
+        if (e < 0 || e >= n || e / workers != p / workers || ((seen >> e) & 1u)) return TM_EINVAL;
+        seen |= 1u << e;
+    }
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return TM_ECUDA;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_t = al((size_t)n * sizeof(tm_task));
+    if (!t_stage.ensure(b_t + 5 * 256, d)) return TM_ENOMEM;
+    unsigned char* p = static_cast<unsigned char*>(t_stage.p);
+    tm_task* d_tasks = reinterpret_cast<tm_task*>(p);
+    int32_t* d_off = reinterpret_cast<int32_t*>(p + b_t);
+    int32_t* d_w = reinterpret_cast<int32_t*>(p + b_t + 256);
+    int32_t* d_ord = reinterpret_cast<int32_t*>(p + b_t + 512);
+    tm_device* d_dv = reinterpret_cast<tm_device*>(p + b_t + 768);
+    int32_t* d_ms = reinterpret_cast<int32_t*>(p + b_t + 1024);
+    const int32_t off[2] = {0, n};
+    if (cudaMemcpy(d_tasks, tasks, (size_t)n * sizeof(tm_task), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_off, off, 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_w, &workers, 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_ord, order, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_dv, dev, sizeof(tm_device), cudaMemcpyHostToDevice) != cudaSuccess)
+        return TM_ECUDA;
+    if (launch_chain_predict(d_tasks, d_off, d_w, 1, d_ord, d_dv, d_ms, nullptr, 0) != cudaSuccess)
+        return TM_ECUDA;
+    return cudaMemcpy(makespan, d_ms, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+}  // extern "C"

@@ -23,6 +23,10 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
 cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const void* st, int G,
                         int B, const int32_t* heur_ms, int32_t* orders, int32_t* ms,
                         int32_t* beam_won, cudaStream_t s);
+cudaError_t beam_refine(const tm_task* tasks, const int32_t* offsets, const tm_device* devs,
+                        const int32_t* status, const void* st, int G, int B, int K,
+                        const int32_t* heur_ms, int32_t* orders, int32_t* ms, int32_t* beam_won,
+                        cudaStream_t s);
 cudaError_t rank_rows(const tm_task* tasks, const int32_t* offsets, int G, const tm_device* devs,
                       const int32_t* orders, const tm_stats* stats, int64_t* row_base,
                       int32_t* state_base, int64_t M, int S, bf16_raw* X, int32_t* state_off,
@@ -72,7 +76,7 @@ bool BeamScratch::reserve(int G, int nmax, int B)
 
 int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
                const int32_t* d_offsets, const int32_t* h_offsets, int G, const tm_device* d_devs,
-               int B, int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
+               int B, int K, int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
                int32_t* d_beam_won, cudaStream_t s)
 {
     if (G == 0) return TM_OK;
@@ -112,9 +116,13 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
                                 cur, nxt, gc, B, R, pos, fused ? sc.bx.as<bf16_raw>() : nullptr, s);
             std::swap(cur, nxt);
         }
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && K == 0)
             e = beam_finish(off, status + g0, cur, gc, B, hms + g0, d_orders_out,
                             d_makespans_out ? d_makespans_out + g0 : nullptr,
+                            d_beam_won ? d_beam_won + g0 : nullptr, s);
+        else if (e == cudaSuccess)
+            e = beam_refine(d_tasks, off, d_devs + g0, status + g0, cur, gc, B, std::min(K, B),
+                            hms + g0, d_orders_out, d_makespans_out ? d_makespans_out + g0 : nullptr,
                             d_beam_won ? d_beam_won + g0 : nullptr, s);
     }
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
@@ -256,6 +264,25 @@ int tm_ranker_forward_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows, float
     return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
+int tm_ranker_forward_keep_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows, float* d_logits,
+                               uint16_t* d_acts, int path, void* stream)
+{
+    if (!r || rows < 0 || (rows > 0 && (!d_X || !d_logits || !d_acts))) return TM_EINVAL;
+    if (path != 0 && path != 1) return TM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_X) % 16 || reinterpret_cast<uintptr_t>(d_acts) % 16)
+        return TM_EINVAL;
+    if (rows > INT32_MAX - 16) return TM_EINVAL;
+    if (int rc = on_device(r)) return rc;
+    if (rows == 0) return TM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    tmgpu::bf16_raw* keep = reinterpret_cast<tmgpu::bf16_raw*>(d_acts);
+    cudaError_t e = path == 0
+        ? tmgpu::ranker_forward_tc(d_X, rows, r->Wimg, d_logits, r->d_err, forward_blocks(r, rows),
+                                   s, keep)
+        : tmgpu::ranker_forward(d_X, rows, r->Wb, r->P, d_logits, keep, rows, 2 * r->sms, s);
+    return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
 int tm_ranker_grad_dev(tm_ranker* r, const uint16_t* d_X, int64_t rows,
                        const int32_t* d_state_off, const int32_t* d_target, int32_t states,
                        float* d_grad, float* d_loss, void* stream)
@@ -302,10 +329,11 @@ int tm_ranker_adam_dev(tm_ranker* r, float lr, void* stream)
 
 int tm_beam_batch_dev(tm_ranker* r, const tm_task* d_tasks, const int32_t* d_offsets,
                       const int32_t* h_offsets, int G, const tm_device* d_devs, int beam_width,
-                      int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
-                      int32_t* d_beam_won, void* stream)
+                      int refine_starts, int32_t* d_orders_out, int32_t* d_makespans_out,
+                      int32_t* d_status, int32_t* d_beam_won, void* stream)
 {
     if (!r || G < 0 || beam_width < 1 || beam_width > TM_BEAM_MAX_WIDTH) return TM_EINVAL;
+    if (refine_starts < 0 || refine_starts > TM_BEAM_MAX_REFINE_STARTS) return TM_EINVAL;
     if (G == 0) return TM_OK;
     if (!d_tasks || !d_offsets || !h_offsets || !d_devs || !d_orders_out) return TM_EINVAL;
     if (h_offsets[0] != 0) return TM_EINVAL;
@@ -315,7 +343,7 @@ int tm_beam_batch_dev(tm_ranker* r, const tm_task* d_tasks, const int32_t* d_off
     }
     if (int rc = on_device(r)) return rc;
     return tmgpu::beam_batch(r, r->beam, d_tasks, d_offsets, h_offsets, G, d_devs, beam_width,
-                             d_orders_out, d_makespans_out, d_status, d_beam_won,
+                             refine_starts, d_orders_out, d_makespans_out, d_status, d_beam_won,
                              (cudaStream_t)stream);
 }
 

@@ -51,11 +51,11 @@ constexpr int64_t kBeamFusedRows = int64_t(1) << 19;
 
 // Beam search of G groups (see tm_beam_batch_dev).  d_offsets / h_offsets
 // hold G + 1 task offsets (h_offsets need not start at 0; only differences
-// are used on the host).  Group sizes must be 1..16 and B 1..64 (checked by
-// the callers).  Uses `sc` (grown if needed) and reads the ranker's weights.
+// are used on the host).  Group sizes must be 1..16, B 1..64 and K (refine
+// starts) 0..8 (checked by the callers).  Uses `sc` (grown if needed) and reads the ranker's weights.
 int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
                const int32_t* d_offsets, const int32_t* h_offsets, int G, const tm_device* d_devs,
-               int B, int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
+               int B, int K, int32_t* d_orders_out, int32_t* d_makespans_out, int32_t* d_status,
                int32_t* d_beam_won, cudaStream_t s);
 
 }  // namespace tmgpu

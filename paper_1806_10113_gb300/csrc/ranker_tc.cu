@@ -230,9 +230,12 @@ __global__ void image_kernel(const float* __restrict__ P, const bf16* __restrict
     if (i < 4) reinterpret_cast<float*>(img + kImgB4)[i] = i == 0 ? P[kOffB4] : 0.0f;
 }
 
+// KEEP: also store the three hidden layers' bfloat16 activations, row-major,
+// layer l of row r at keep[(l * M + r) * 128] (for tests and inspection).
+template <bool KEEP>
 __global__ void __launch_bounds__(kThreads, 1)
 forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __restrict__ img,
-                  float* __restrict__ logits, int* __restrict__ err)
+                  float* __restrict__ logits, int* __restrict__ err, bf16* __restrict__ keep)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -339,6 +342,14 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                         *reinterpret_cast<uint4*>(act_p + core_off(row, 32 * c + 8 * q, kH)) =
                             make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
                                        packed[4 * q + 3]);
+                    if (KEEP && r0 + row < M) {
+                        uint4* dst = reinterpret_cast<uint4*>(
+                            keep + ((size_t)layer * M + r0 + row) * kH + 32 * c);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1],
+                                                packed[4 * q + 2], packed[4 * q + 3]);
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -348,7 +359,10 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                         for (int e = 0; e < 4; ++e) {
                             const int j = 4 * q + e;
                             const float h = fmaxf(__uint_as_float(r[j]) + bv[j], 0.0f);
-                            logit += __bfloat162float(__float2bfloat16_rn(h)) * wv[e];
+                            const bf16 hb = __float2bfloat16_rn(h);
+                            logit += __bfloat162float(hb) * wv[e];
+                            if (KEEP && r0 + row < M)
+                                keep[((size_t)2 * M + r0 + row) * kH + 32 * c + j] = hb;
                         }
                     }
                 }
@@ -388,18 +402,25 @@ cudaError_t ranker_image(const float* P, const bf16_raw* Wb, unsigned char* img,
 
 cudaError_t ranker_tc_configure()
 {
-    return cudaFuncSetAttribute(forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(forward_tc_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(forward_tc_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 cudaError_t ranker_forward_tc(const bf16_raw* X, int64_t M, const unsigned char* img,
-                              float* logits, int* err, int blocks, cudaStream_t s)
+                              float* logits, int* err, int blocks, cudaStream_t s, bf16_raw* keep)
 {
     if (M <= 0) return cudaSuccess;
     const int64_t groups = (M + (int64_t)kTile * kGroups - 1) / ((int64_t)kTile * kGroups);
     const int grid = (int)(groups < blocks ? groups : blocks);
-    forward_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(reinterpret_cast<const bf16*>(X), M, img,
-                                                          logits, err);
+    if (keep)
+        forward_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(
+            reinterpret_cast<const bf16*>(X), M, img, logits, err, reinterpret_cast<bf16*>(keep));
+    else
+        forward_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(
+            reinterpret_cast<const bf16*>(X), M, img, logits, err, nullptr);
     return cudaGetLastError();
 }
 

@@ -190,8 +190,8 @@ bool tm_server::try_launch(Lane& L)
         int32_t* d_orders = reinterpret_cast<int32_t*>(L.d_out + out.orders);
         if (cfg.beam_width > 0 && ranker) {
             const int brc = tmgpu::beam_batch(ranker, L.beam, d_tasks, d_off, h_off, G, d_dev,
-                                              cfg.beam_width, d_orders, d_ms, d_status, d_won,
-                                              L.stream);
+                                              cfg.beam_width, cfg.refine_starts, d_orders, d_ms,
+                                              d_status, d_won, L.stream);
             if (brc != TM_OK) rc = brc;
         } else {
             ok(tmgpu::launch_heuristic(d_tasks, d_off, G, d_dev, d_orders, d_ms, d_status,
@@ -314,7 +314,8 @@ int tm_server_create(const tm_server_config* config, const tm_ranker* ranker,
     if (c.lanes < 1 || c.lanes > 8 || c.lane_groups < 1 || c.lane_groups > (1 << 16) ||
         c.lane_tasks < TM_MAX_TASKS || c.lane_tasks > (1 << 22) || c.lane_subsets < 495 ||
         c.lane_subsets > (1 << 26) || c.exact_max_n < 0 || c.exact_max_n > TM_MAX_EXHAUSTIVE ||
-        c.beam_width < 0 || c.beam_width > TM_BEAM_MAX_WIDTH)
+        c.beam_width < 0 || c.beam_width > TM_BEAM_MAX_WIDTH || c.refine_starts < 0 ||
+        c.refine_starts > TM_BEAM_MAX_REFINE_STARTS)
         return TM_EINVAL;
     if (c.beam_width > 0 && !ranker) return TM_EINVAL;
     const tm_tuning& t = c.tuning;

@@ -175,6 +175,22 @@ def half_dk_half_dt(groups=32, n=12, seed=3, models=(2,)) -> Batch:
     return duplicate_for_models(b, models) if len(models) > 1 else b
 
 
+def chained_groups(groups=4096, workers=4, rounds=4, seed=7) -> Batch:
+    """Chained groups (the experiment setup of Sec. 6.1): `workers` workers
+    each with a chain of `rounds` tasks, task r * workers + w being worker
+    w's round-r task; each task DK or DT with p = 1/2, log-uniform durations
+    as in `ragged_mixed`; even groups two DMA engines, odd groups one.  The
+    batch's meta holds the workers per group."""
+    out, dma = [], []
+    for g in range(groups):
+        rng = group_stream(seed, g)
+        out.append([log_uniform_task(rng, rng.uniform_int(0, 1) == 1)
+                    for _ in range(workers * rounds)])
+        dma.append(2 if g % 2 == 0 else 1)
+    return make_batch(out, dma, f"chain_g{groups}_t{workers}_r{rounds}_seed{seed}",
+                      {"workers": np.full(groups, workers, dtype=np.int32)})
+
+
 def random_small(seed: int, n: int, lo: int = 0, hi: int = 9, dma: int = 2) -> Batch:
     """A tiny group with small integer durations, for brute-force checks."""
     rng = group_stream(seed, n)

@@ -29,6 +29,8 @@ TM_NOALLOC_MAX_SUBSETS = 4800
 TM_RANKER_FEATURES = 32
 TM_RANKER_PARAMS = 37377
 TM_BEAM_MAX_WIDTH = 64
+TM_BEAM_MAX_REFINE_STARTS = 8
+TM_CHAIN_MAX_WORKERS = 8
 
 STATS_DTYPE = np.dtype([
     ("best", "<i4"), ("worst", "<i4"), ("sum", "<i8"), ("mean", "<f8"),
@@ -89,10 +91,17 @@ _SIGS = {
     "tm_ranker_rows_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64,
                            ctypes.c_int32, _vp, _vp, _vp, _vp, _vp],
     "tm_ranker_forward_dev": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "tm_ranker_forward_keep_dev": [_vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_int, _vp],
     "tm_ranker_grad_dev": [_vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp],
     "tm_ranker_adam_dev": [_vp, ctypes.c_float, _vp],
-    "tm_beam_batch_dev": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
-                          _vp, _vp],
+    "tm_beam_batch_dev": [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                          _vp, _vp, _vp, _vp],
+    "tm_refine_batch_dev": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "tm_predict_chain": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int32)],
+    "tm_exhaustive_chain": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp],
+    "tm_exhaustive_chain_batch": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp],
+    "tm_exhaustive_chain_batch_dev": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tm_predict_chain_batch_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "tm_server_create": [_vp, _vp, ctypes.POINTER(_vp)],
     "tm_server_submit": [_vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_uint64)],
     "tm_server_poll": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
@@ -465,6 +474,13 @@ class Ranker:
         _check(lib().tm_ranker_forward_dev(self._h, _dptr(d_X), int(rows), _dptr(d_logits),
                                            _stream(stream)), "tm_ranker_forward_dev")
 
+    def forward_keep_dev(self, d_X, rows: int, d_logits, d_acts, path: int = 0, stream=None):
+        """Logits and the hidden layers' bfloat16 activations [3 x rows x 128];
+        path 0 the tensor-core scoring kernel, 1 the training forward."""
+        _check(lib().tm_ranker_forward_keep_dev(self.handle, _dptr(d_X), int(rows),
+                                                _dptr(d_logits), _dptr(d_acts), int(path),
+                                                _stream(stream)), "tm_ranker_forward_keep_dev")
+
     def grad_dev(self, d_X, rows: int, d_state_off, d_target, states: int, d_grad=None,
                  d_loss=None, stream=None):
         _check(lib().tm_ranker_grad_dev(self._h, _dptr(d_X), int(rows), _dptr(d_state_off),
@@ -489,14 +505,26 @@ class Ranker:
 
 def tm_beam_batch_dev(ranker: Ranker, d_tasks, d_offsets, offsets, d_devs, beam_width: int,
                       d_orders_out, d_makespans_out=None, d_status=None, d_beam_won=None,
-                      stream=None):
+                      stream=None, refine_starts: int = 0):
     """Beam search of every group with the ranker's proposals; never worse than
-    the heuristic.  ``offsets`` is the HOST copy of d_offsets."""
+    the heuristic.  ``offsets`` is the HOST copy of d_offsets.  With
+    refine_starts = K > 0 the K best finished beams and the heuristic's order
+    each start the exact-model descent (tm_refine_batch_dev)."""
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
     _check(lib().tm_beam_batch_dev(ranker.handle, _dptr(d_tasks), _dptr(d_offsets), _p(off),
                                    off.shape[0] - 1, _dptr(d_devs), int(beam_width),
-                                   _dptr(d_orders_out), _dptr(d_makespans_out), _dptr(d_status),
-                                   _dptr(d_beam_won), _stream(stream)), "tm_beam_batch_dev")
+                                   int(refine_starts), _dptr(d_orders_out),
+                                   _dptr(d_makespans_out), _dptr(d_status), _dptr(d_beam_won),
+                                   _stream(stream)), "tm_beam_batch_dev")
+
+
+def tm_refine_batch_dev(d_tasks, d_offsets, G: int, d_devs, d_orders, d_makespans=None,
+                        d_status=None, stream=None):
+    """Exact-model descent (swaps and moves of one task) from the orders in
+    d_orders, which receive the results."""
+    _check(lib().tm_refine_batch_dev(_dptr(d_tasks), _dptr(d_offsets), int(G), _dptr(d_devs),
+                                     _dptr(d_orders), _dptr(d_makespans), _dptr(d_status),
+                                     _stream(stream)), "tm_refine_batch_dev")
 
 
 # ---- serving -------------------------------------------------------------------
@@ -515,7 +543,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("lane_groups", ctypes.c_int32),
                 ("lane_tasks", ctypes.c_int32), ("lane_subsets", ctypes.c_int32),
                 ("exact_max_n", ctypes.c_int32), ("beam_width", ctypes.c_int32),
-                ("tuning", Tuning)]
+                ("tuning", Tuning), ("refine_starts", ctypes.c_int32)]
 
 
 class Server:
@@ -525,9 +553,10 @@ class Server:
 
     def __init__(self, exact_max_n: int = 12, beam_width: int = 0, ranker: Ranker = None,
                  lanes: int = 0, lane_groups: int = 0, lane_tasks: int = 0,
-                 lane_subsets: int = 0, tuning: Tuning = None):
+                 lane_subsets: int = 0, tuning: Tuning = None, refine_starts: int = 0):
         self.config = ServerConfig(lanes, lane_groups, lane_tasks, lane_subsets, exact_max_n,
-                                   beam_width, tuning if tuning is not None else Tuning())
+                                   beam_width, tuning if tuning is not None else Tuning(),
+                                   refine_starts)
         self._ranker = ranker          # keeps the ranker alive while the server runs
         h = ctypes.c_void_p()
         _check(lib().tm_server_create(ctypes.byref(self.config),
@@ -634,3 +663,68 @@ def tm_exhaustive_overlap_batch_dev(d_tasks, d_offsets, offsets, d_devs, rate_nu
                                                  int(rate_den), _dptr(d_stats), _dptr(d_status),
                                                  _stream(stream)),
            "tm_exhaustive_overlap_batch_dev")
+
+
+# ---- chained tasks ---------------------------------------------------------------
+
+def _workers(workers, G: int) -> np.ndarray:
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(workers, dtype=np.int32), (G,)))
+
+
+def tm_predict_chain(tasks, workers: int, order, dma_engines: int) -> int:
+    """Makespan of one order of a chained group: tasks[r * workers + w] is
+    worker w's round-r task; `order` lists task indices round by round."""
+    t = _tasks(tasks)
+    n = t.shape[0]
+    if workers < 1 or n % workers:
+        raise TMError(-1, "tm_predict_chain")
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    ms = ctypes.c_int32(0)
+    _check(lib().tm_predict_chain(_p(t), int(workers), n // int(workers), _p(o), _p(dev),
+                                  ctypes.byref(ms)), "tm_predict_chain")
+    return int(ms.value)
+
+
+def tm_exhaustive_chain(tasks, workers: int, dma_engines: int) -> dict:
+    """All (workers!)^rounds orders of one chained group."""
+    t = _tasks(tasks)
+    n = t.shape[0]
+    if workers < 1 or n % workers:
+        raise TMError(-1, "tm_exhaustive_chain")
+    dev = np.asarray([dma_engines], dtype=np.int32)
+    st = np.zeros(1, dtype=STATS_DTYPE)
+    _check(lib().tm_exhaustive_chain(_p(t), int(workers), n // int(workers), _p(dev), _p(st)),
+           "tm_exhaustive_chain")
+    return stats_to_dicts(st, [n])[0]
+
+
+def tm_exhaustive_chain_batch(tasks, offsets, workers, dma) -> np.ndarray:
+    """tm_stats of every chained group of a ragged batch (workers[g] each)."""
+    t = _tasks(tasks)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    st = np.zeros(max(G, 1), dtype=STATS_DTYPE)
+    _check(lib().tm_exhaustive_chain_batch(_p(t), _p(off), _p(_workers(workers, G)), G,
+                                           _p(_devs(dma, G)), _p(st)), "tm_exhaustive_chain_batch")
+    return st[:G]
+
+
+def tm_exhaustive_chain_batch_dev(d_tasks, d_offsets, offsets, d_workers, workers, d_devs,
+                                  d_stats, d_status=None, stream=None):
+    """Device-pointer form; ``offsets`` and ``workers`` are the HOST copies."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    G = off.shape[0] - 1
+    w = _workers(workers, G)
+    _check(lib().tm_exhaustive_chain_batch_dev(_dptr(d_tasks), _dptr(d_offsets), _p(off),
+                                               _dptr(d_workers), _p(w), G, _dptr(d_devs),
+                                               _dptr(d_stats), _dptr(d_status), _stream(stream)),
+           "tm_exhaustive_chain_batch_dev")
+
+
+def tm_predict_chain_batch_dev(d_tasks, d_offsets, d_workers, G: int, d_orders, d_devs,
+                               d_makespans, d_status=None, stream=None):
+    _check(lib().tm_predict_chain_batch_dev(_dptr(d_tasks), _dptr(d_offsets), _dptr(d_workers),
+                                            int(G), _dptr(d_orders), _dptr(d_devs),
+                                            _dptr(d_makespans), _dptr(d_status), _stream(stream)),
+           "tm_predict_chain_batch_dev")
