@@ -178,7 +178,10 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  left runs as straight-line code, and the orders' sum
  *                  shares the FMA pipe (faster on batches of one group
  *                  size); 2: as a loop (less code: faster on batches that
- *                  mix group sizes); 0: default 2 */
+ *                  mix group sizes); 3: as 1, with each order's addition
+ *                  on the FMA pipe too; 4: as 3, compiled for four
+ *                  resident blocks per SM (at most 128 registers);
+ *                  0: default 2 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;

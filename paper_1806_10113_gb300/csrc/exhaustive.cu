@@ -550,13 +550,29 @@ __device__ __forceinline__ int first_completion(int32_t k, int32_t d, int32_t v,
 // stay on the ALU pipe.  That balance pays where the walk's straight-line
 // level keeps the ALU pipe busy (5% on uniform batches) and costs 2% in the
 // looped walk, so the two go together.
-template <bool SUM32, bool FMA_SUM>
+// Walk modes (tm_tuning.unroll): 1 the straight-line level with the
+// FMA-pipe sum; 2 every level as a loop (ALU sum); 3 as 1, and each order's
+// addition k + beta as a multiply-add by S.one, so that it too issues on the
+// FMA pipe beside the ALU pipe's maxima and minima; 4 as 3, compiled for four
+// resident blocks per SM (at most 128 registers) instead of three.
+__host__ __device__ constexpr bool mode_straight(int mode) { return mode != 2; }
+__host__ __device__ constexpr bool mode_fma_add(int mode) { return mode >= 3; }
+__host__ __device__ constexpr int mode_min_blocks(int mode) { return mode == 4 ? 4 : TM_ENUM_MIN_BLOCKS; }
+
+template <bool SUM32, int MODE>
 __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& a)
 {
+    constexpr bool FMA_SUM = mode_straight(MODE);
     const int32_t c0 = d + S.alpha;
     int32_t m[24];
+    if constexpr (mode_fma_add(MODE)) {
 #pragma unroll
-    for (int j = 0; j < 24; ++j) m[j] = max3i(c0, S.c[j], k + S.b[j]);
+        for (int j = 0; j < 24; ++j)
+            m[j] = max3i(c0, S.c[j], (int32_t)((uint32_t)k * S.one + (uint32_t)S.b[j]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 24; ++j) m[j] = max3i(c0, S.c[j], k + S.b[j]);
+    }
     int32_t t8[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) t8[i] = min3i(m[3 * i], m[3 * i + 1], m[3 * i + 2]);
@@ -587,61 +603,61 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
 }
 
 // The last two prefix positions, holding tasks x < y: orders (x, y), (y, x).
-template <bool SUM32, bool FMA_SUM>
+template <bool SUM32, int MODE>
 __device__ __forceinline__ void last_two(Eng st, int4 x, int4 y, const Sfx& S, Acc& a)
 {
     const Eng sxy = step(step(st, x.x, x.y, x.z), y.x, y.y, y.z);
     const Eng syx = step(step(st, y.x, y.y, y.z), x.x, x.y, x.z);
-    leaves<SUM32, FMA_SUM>(sxy.k, sxy.d, S, a);
-    leaves<SUM32, FMA_SUM>(syx.k, syx.d, S, a);
+    leaves<SUM32, MODE>(sxy.k, sxy.d, S, a);
+    leaves<SUM32, MODE>(syx.k, syx.d, S, a);
 }
 
 // Depth-first walk over the D remaining prefix tasks (ascending in `rem`):
 // their orders in lexicographic order, so `walked` counts prefixes in rank
-// order.  UNROLL: the level with three tasks left runs as straight-line code
+// order.  Straight-line modes: the level with three tasks left runs as straight-line code
 // (its six prefixes in one block, which the compiler can interleave); else
 // as a loop (less code: better when a batch mixes group sizes and so runs
 // many walk depths and both sum widths at once).
-template <int D, bool SUM32, bool UNROLL>
+template <int D, bool SUM32, int MODE>
 __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict__ tbl,
                                     const Sfx& S, Acc& a)
 {
     if constexpr (D == 0) {
-        leaves<SUM32, UNROLL>(st.k, st.d, S, a);
+        leaves<SUM32, MODE>(st.k, st.d, S, a);
     } else if constexpr (D == 1) {
         int4 t = tbl[nib_get(rem, 0)];
         Eng s1 = step(st, t.x, t.y, t.z);
-        leaves<SUM32, UNROLL>(s1.k, s1.d, S, a);
+        leaves<SUM32, MODE>(s1.k, s1.d, S, a);
     } else if constexpr (D == 2) {
-        last_two<SUM32, UNROLL>(st, tbl[nib_get(rem, 0)], tbl[nib_get(rem, 1)], S, a);
-    } else if constexpr (D == 3 && UNROLL) {
+        last_two<SUM32, MODE>(st, tbl[nib_get(rem, 0)], tbl[nib_get(rem, 1)], S, a);
+    } else if constexpr (D == 3 && mode_straight(MODE)) {
         // the three tasks' rows loaded once; their six orders in
         // lexicographic order (the list is ascending)
         const int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)], t2 = tbl[nib_get(rem, 2)];
-        last_two<SUM32, UNROLL>(step(st, t0.x, t0.y, t0.z), t1, t2, S, a);
-        last_two<SUM32, UNROLL>(step(st, t1.x, t1.y, t1.z), t0, t2, S, a);
-        last_two<SUM32, UNROLL>(step(st, t2.x, t2.y, t2.z), t0, t1, S, a);
+        last_two<SUM32, MODE>(step(st, t0.x, t0.y, t0.z), t1, t2, S, a);
+        last_two<SUM32, MODE>(step(st, t1.x, t1.y, t1.z), t0, t2, S, a);
+        last_two<SUM32, MODE>(step(st, t2.x, t2.y, t2.z), t0, t1, S, a);
     } else {
 #pragma unroll 1
         for (int c = 0; c < D; ++c) {
             int4 t = tbl[nib_get(rem, c)];
-            dfs<D - 1, SUM32, UNROLL>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
+            dfs<D - 1, SUM32, MODE>(step(st, t.x, t.y, t.z), nib_remove(rem, c), tbl, S, a);
         }
     }
 }
 
-template <int PDMAX, bool SUM32, bool UNROLL>
+template <int PDMAX, bool SUM32, int MODE>
 __device__ __forceinline__ void walk_prefixes(int pd, Eng st, uint64_t rem,
                                               const int4* __restrict__ tbl, const Sfx& S, Acc& a)
 {
     switch (pd) {
-    case 0: dfs<0, SUM32, UNROLL>(st, rem, tbl, S, a); break;
-    case 1: dfs<1, SUM32, UNROLL>(st, rem, tbl, S, a); break;
-    case 2: dfs<2, SUM32, UNROLL>(st, rem, tbl, S, a); break;
+    case 0: dfs<0, SUM32, MODE>(st, rem, tbl, S, a); break;
+    case 1: dfs<1, SUM32, MODE>(st, rem, tbl, S, a); break;
+    case 2: dfs<2, SUM32, MODE>(st, rem, tbl, S, a); break;
     default:
-        if constexpr (PDMAX >= 3) { if (pd == 3) dfs<3, SUM32, UNROLL>(st, rem, tbl, S, a); }
-        if constexpr (PDMAX >= 4) { if (pd == 4) dfs<4, SUM32, UNROLL>(st, rem, tbl, S, a); }
-        if constexpr (PDMAX >= 5) { if (pd == 5) dfs<5, SUM32, UNROLL>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 3) { if (pd == 3) dfs<3, SUM32, MODE>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 4) { if (pd == 4) dfs<4, SUM32, MODE>(st, rem, tbl, S, a); }
+        if constexpr (PDMAX >= 5) { if (pd == 5) dfs<5, SUM32, MODE>(st, rem, tbl, S, a); }
         break;
     }
 }
@@ -721,7 +737,7 @@ __device__ __noinline__ uint32_t item_rank(uint32_t at, int32_t v, uint32_t hd, 
 // The items whose first cost unit lies in [x0, x1), in order: walk them,
 // settle each against the thread's running best / worst, and report to the
 // group accumulators when the group changes and at the end.
-template <int PDMAX, bool UNROLL>
+template <int PDMAX, int MODE>
 __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
                                            const GroupInfo* __restrict__ info,
                                            const int4* __restrict__ tbl,
@@ -800,8 +816,8 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
         uint32_t placed;
         Eng st = run_head(hd, f, P, gi.dinit, rem, placed, gt);
         a.start_item();
-        if (gi.sum32) walk_prefixes<PDMAX, true, UNROLL>(pd, st, rem, gt, S, a);
-        else walk_prefixes<PDMAX, false, UNROLL>(pd, st, rem, gt, S, a);
+        if (gi.sum32) walk_prefixes<PDMAX, true, MODE>(pd, st, rem, gt, S, a);
+        else walk_prefixes<PDMAX, false, MODE>(pd, st, rem, gt, S, a);
         // Settle the item against the running best / worst: every lane of a
         // warp gets here together, so this rank work does not diverge.  A
         // tie can only lower the rank if the item's first order ranks below
@@ -821,8 +837,8 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
     flush_final(a, sink, g);
 }
 
-template <int PDMAX, bool UNROLL>
-__global__ void __launch_bounds__(kEnumBlock, TM_ENUM_MIN_BLOCKS)
+template <int PDMAX, int MODE>
+__global__ void __launch_bounds__(kEnumBlock, mode_min_blocks(MODE))
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
             uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks,
@@ -832,7 +848,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
         const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         uint64_t x0, x1;
         static_range(t, per_thread, split_c, split_warps, split_hi, split_klo, &x0, &x1);
-        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, x0, x1, item_cost, sink);
+        enum_range<PDMAX, MODE>(gp, info, tbl, sub, G, x0, x1, item_cost, sink);
         return;
     }
     // dynamic: each warp takes 32 consecutive chunks at a time, one per lane
@@ -843,7 +859,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
         c0 = __shfl_sync(kFull, c0, 0);
         if (c0 >= nchunks) break;
         const uint64_t c = (uint64_t)c0 + lane;
-        enum_range<PDMAX, UNROLL>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
+        enum_range<PDMAX, MODE>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
                           sink);
         __syncwarp();
     }
@@ -870,34 +886,69 @@ __global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc
     if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, a.tbl, acc, a.stats, a.status);
 }
 
-template <int PDMAX, bool UNROLL>
+template <int PDMAX, int MODE>
 cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
 {
     uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
     const bool dyn = p.chunks_per_thread > 1;
-    enum_kernel<PDMAX, UNROLL><<<blocks, kEnumBlock, 0, stream>>>(
+    enum_kernel<PDMAX, MODE><<<blocks, kEnumBlock, 0, stream>>>(
         p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
         sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u, dyn ? 0ull : p.split_c,
         p.split_warps, p.split_hi, p.split_klo);
     return cudaGetLastError();
 }
 
-template <int PDMAX, bool UNROLL>
+template <int PDMAX, int MODE>
 cudaError_t enum_occupancy(int* per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, enum_kernel<PDMAX, UNROLL>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, enum_kernel<PDMAX, MODE>,
                                                          kEnumBlock, 0);
 }
 
-int resident_threads(int pdmax, bool unroll, int device, int blocks_per_sm)
+template <int PDMAX>
+cudaError_t enum_occupancy_mode(int mode, int* per_sm)
+{
+    switch (mode) {
+    case 1: return enum_occupancy<PDMAX, 1>(per_sm);
+    case 2: return enum_occupancy<PDMAX, 2>(per_sm);
+    case 3: return enum_occupancy<PDMAX, 3>(per_sm);
+    case 4: return enum_occupancy<PDMAX, 4>(per_sm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PDMAX>
+cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, cudaStream_t stream)
+{
+    switch (p.unroll) {
+    case 1: return launch_enum<PDMAX, 1>(p, sink, stream);
+    case 2: return launch_enum<PDMAX, 2>(p, sink, stream);
+    case 3: return launch_enum<PDMAX, 3>(p, sink, stream);
+    case 4: return launch_enum<PDMAX, 4>(p, sink, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PDMAX>
+cudaError_t preload_modes()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 1>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 2>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 3>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 4>);
+}
+
+int resident_threads(int pdmax, int mode, int device, int blocks_per_sm)
 {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaErrorInvalidValue;
     switch (pdmax) {
-    case 3: e = unroll ? enum_occupancy<3, true>(&per_sm) : enum_occupancy<3, false>(&per_sm); break;
-    case 4: e = unroll ? enum_occupancy<4, true>(&per_sm) : enum_occupancy<4, false>(&per_sm); break;
-    case 5: e = unroll ? enum_occupancy<5, true>(&per_sm) : enum_occupancy<5, false>(&per_sm); break;
+    case 3: e = enum_occupancy_mode<3>(mode, &per_sm); break;
+    case 4: e = enum_occupancy_mode<4>(mode, &per_sm); break;
+    case 5: e = enum_occupancy_mode<5>(mode, &per_sm); break;
     default: break;
     }
     if (e != cudaSuccess || sms <= 0 || per_sm <= 0) return 152 * 512;
@@ -909,7 +960,7 @@ int resident_threads(int pdmax, bool unroll, int device, int blocks_per_sm)
 
 void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
 {
-    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, p.unroll == 1, device, blocks_per_sm),
+    uint64_t threads = std::min<uint64_t>((uint64_t)resident_threads(p.pdmax, p.unroll, device, blocks_per_sm),
                                           std::max<uint64_t>(p.total_items, 1));
     p.leaves_per_thread = std::max<uint64_t>(1, (p.total_leaves + threads - 1) / threads);
     p.threads = (uint32_t)((p.total_leaves + p.leaves_per_thread - 1) / p.leaves_per_thread);
@@ -945,12 +996,9 @@ cudaError_t exhaustive_preload()
     cudaError_t e;
     if ((e = cudaFuncGetAttributes(&fa, prep_kernel)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, finalize_kernel)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<3, false>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<3, true>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<4, false>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<4, true>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<5, false>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, enum_kernel<5, true>);
+    if ((e = preload_modes<3>()) != cudaSuccess) return e;
+    if ((e = preload_modes<4>()) != cudaSuccess) return e;
+    return preload_modes<5>();
 }
 
 int exhaustive_launch_count(const Plan& p)
@@ -1000,11 +1048,10 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
         if (p.ev_before &&
             (e = cudaEventRecordWithFlags(p.ev_before, stream, rec_flags)) != cudaSuccess)
             return e;
-        const bool unroll = p.unroll == 1;
         switch (p.pdmax) {
-        case 3: e = unroll ? launch_enum<3, true>(p, sink, stream) : launch_enum<3, false>(p, sink, stream); break;
-        case 4: e = unroll ? launch_enum<4, true>(p, sink, stream) : launch_enum<4, false>(p, sink, stream); break;
-        case 5: e = unroll ? launch_enum<5, true>(p, sink, stream) : launch_enum<5, false>(p, sink, stream); break;
+        case 3: e = launch_enum_mode<3>(p, sink, stream); break;
+        case 4: e = launch_enum_mode<4>(p, sink, stream); break;
+        case 5: e = launch_enum_mode<5>(p, sink, stream); break;
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;

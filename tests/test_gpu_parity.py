@@ -393,7 +393,11 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
                                     dict(chunks_per_thread=2, item_cost=1, blocks_per_sm=1),
                                     dict(unroll=1), dict(pdmax=3, unroll=1),
                                     dict(pdmax=5, unroll=1, chunks_per_thread=3),
-                                    dict(pdmax=4, unroll=2, item_cost=1)])
+                                    dict(pdmax=4, unroll=2, item_cost=1),
+                                    dict(pdmax=5, unroll=3), dict(pdmax=3, unroll=3,
+                                                                   chunks_per_thread=6),
+                                    dict(pdmax=5, unroll=4), dict(pdmax=3, unroll=4),
+                                    dict(pdmax=4, unroll=4, chunks_per_thread=3)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
