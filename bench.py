@@ -14,6 +14,13 @@ Prints one JSON line (rank 0).  `value` is device-timed with inputs resident
 in HBM; `e2e` goes through the host-pointer C ABI with host<->device copies
 inside the timed region.  `--impl reference` times the CPU oracle on the
 host cores on a bounded sample of the same workload.
+
+At one GPU the default run also measures, each with its own clocks, the
+metric's other clauses and the chained-task search as extra keys: `n12`
+(orders/s of the 12-task exhaustive search), `learned` (task groups
+scheduled/s by the learned path on 12-task groups, with the gap to the
+exhaustive optimum timed in the same run, the ranker trained in the run) and
+`chain` (orders/s of the search over chained tasks).
 """
 from __future__ import annotations
 
@@ -54,12 +61,15 @@ WORKLOADS = {
                    "2/1: exhaustive n! orders + heuristic per group"),
     "beam12": ("2048 groups x 12 tasks (6 dominant-kernel + 6 dominant-transfer, log-uniform "
                "[1e4,1e7] ns, seed 3), each under 2 and 1 DMA engines: learned beam search "
-               "(width 64; ranker trained on 2M exhaustively labelled groups, n~U{6..10}) "
+               "(width 16; ranker trained on 2M exhaustively labelled groups, n~U{6..10}) "
                "vs the exhaustive optimum"),
     "overlap10": ("16 groups x 10 tasks (8 dominant-kernel: K~U[1M,5M] ns, HtD/DtH~U[50k,500k]; "
                   "8 dominant-transfer: reverse), seed 1, two DMA engines whose concurrent "
                   "transfers each run at 2/3 speed (partial-overlap model): exhaustive 10! orders "
                   "per group, every order simulated"),
+    "chain4x4": ("4096 chained groups: 4 workers x 4 dependent tasks (Sec. 6.1 experiment setup), "
+                 "each task dominant-kernel or dominant-transfer (p=1/2), log-uniform [1e4,1e7] ns, "
+                 "seed 7, DMA engines alternating 2/1: exhaustive (4!)^4 = 331,776 orders per group"),
     "heuristic1m": ("1,048,576 ragged groups, n~U{4..16}, each task dominant-kernel or dominant-"
                     "transfer (p=1/2), log-uniform [1e4,1e7] ns, seed 6, DMA engines alternating: "
                     "the reordering heuristic (Algorithm 1) for every group"),
@@ -350,6 +360,23 @@ def _reference_arm(name: str, cores: int):
                   "unit": "groups/s", "higher_is_better": True, "dtype": "int64",
                   "each_step": f"{per} consecutive groups, oracle heuristic on {cores} threads"}
         return fields, step
+    if name == "chain4x4":
+        b = inputs.chained_groups(4096, 4, 4, seed=7)
+        w = b.meta["workers"]
+        per = 4
+
+        def step(k):
+            g0 = (k * per) % (b.G - per)
+            off = b.offsets[g0:g0 + per + 1]
+            t0 = time.perf_counter()
+            oracle.exhaustive_chain_batch(b.tasks[off[0]:off[-1]], off - off[0], w[g0:g0 + per],
+                                          b.dma[g0:g0 + per])
+            return per * math.factorial(4) ** 4, time.perf_counter() - t0
+        fields = {"metric": "orderings evaluated/s (exact model, chained tasks)", "unit": UNIT,
+                  "higher_is_better": True, "dtype": "int64",
+                  "each_step": f"every order of {per} consecutive groups, oracle on {cores} "
+                               "host threads"}
+        return fields, step
     if name == "single6":
         b = inputs.single_group_uniform(n=6, seed=0)
 
@@ -404,6 +431,226 @@ def run_reference(args):
 
 
 # ---- the CUDA path ----------------------------------------------------------------
+
+# ---- the metric's other clauses, measured in the default run ----------------------
+
+BEAM_WIDTH = 16           # learned beam width on the 12-task groups
+REFINE_STARTS = 4         # beams (plus the heuristic's order) that start the exact descent
+CHAIN_WORKERS, CHAIN_ROUNDS, CHAIN_GROUPS = 4, 4, 4096
+
+
+def timed_steps(step, K: int, flush=None):
+    """Device time (ms) of each of K steps on the current stream, with the
+    clocks sampled during them; `flush` (if given) runs before each step,
+    outside the events."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    sampler = ClockSampler(bus_id_of(torch.cuda.current_device()))
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    for k in range(K):
+        if flush is not None:
+            flush()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return [a.elapsed_time(c) for a, c in ev], clocks
+
+
+def n12_leg(args, log) -> dict:
+    """Orders/s of the 12-task exhaustive search (N = 12 half of the metric):
+    32 groups x 12 tasks under both device models, autotuned, one
+    tm_schedule_batch_dev pass per step (search + heuristic), L2 flushed."""
+    import torch
+    from paper_1806_10113_gb300 import autotune, tm
+    dev = torch.device("cuda")
+    b = workload(0, "dkdt32x12")
+    G, T = b.G, int(b.tasks.shape[0])
+    n_orders = orders_per_step(b)
+    tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=5)
+    plan = tm.Plan(b.offsets, **tuning)
+    d_tasks, d_dma = torch.from_numpy(b.tasks).to(dev), torch.from_numpy(b.dma).to(dev)
+    d_stats = torch.zeros(G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    d_status = torch.zeros(G, dtype=torch.int32, device=dev)
+    d_orders = torch.zeros(T, dtype=torch.int32, device=dev)
+    d_ms = torch.zeros(G, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    step = lambda: tm.tm_schedule_batch_dev(plan, d_tasks, d_dma, d_stats, d_orders, d_ms, d_status)
+    for _ in range(args.warmup):
+        step()
+    K = 20
+    ek = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for a, c in ek:          # torch creates an event on its first record
+        a.record()
+        c.record()
+    it = iter(ek)
+
+    def timed():
+        a, c = next(it)
+        plan.set_timing(a, c)
+        step()
+
+    ms, clocks = timed_steps(timed, K, flush=flush.zero_)
+    plan.set_timing(None, None)
+    torch.cuda.synchronize()
+    if (d_status.cpu().numpy() != 0).any():
+        raise RuntimeError("12-task workload: device status errors")
+    plan.close()
+    step_s = statistics.mean(ms) / 1000.0
+    enum_s = statistics.mean(a.elapsed_time(c) for a, c in ek) / 1000.0
+    ops = ops_per_order(b)
+    achieved = ops * n_orders / enum_s / 1e12
+    log(f"n12: {n_orders / step_s:.3e} orders/s")
+    return {"workload": WORKLOADS["dkdt32x12"], "value": n_orders / step_s, "unit": UNIT,
+            "ms_per_step": 1000 * step_s, "steps": K, "orders_per_step": n_orders,
+            "groups_per_s": G / step_s, "tuning": tuning,
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": INT32_PEAK_TOPS,
+                         "unit": "Tops/s (int32)", "frac": achieved / INT32_PEAK_TOPS,
+                         "kernel": "enum_kernel (exhaustive enumeration)",
+                         "kernel_ms": 1000 * enum_s, "ops_per_order": round(ops, 3),
+                         "traffic": None},
+            "clocks": clocks}
+
+
+def learned_leg(args, log) -> dict:
+    """Task groups scheduled/s at <= 1% gap (the metric's second clause): the
+    ranker is trained in this run (2M exhaustively labelled groups of 6..10
+    tasks, 3 epochs, all on the GPU), then the learned path -- beam search
+    with the ranker's proposals, the exact model judging, the heuristic's
+    order as a start, the exact-model descent from the best beams and the
+    heuristic -- schedules 2048 twelve-task groups under both device models,
+    against the exhaustive optimum of the same groups timed in the same run."""
+    import torch
+    from paper_1806_10113_gb300 import learn, tm
+    ranker, train_info = trained_ranker(args, log)
+    test = inputs.half_dk_half_dt(2048, 12, seed=3, models=(2, 1))
+    G, T = test.G, int(test.tasks.shape[0])
+    d_tasks, d_offsets, d_devs = learn.to_device(test)
+    # the exhaustive optimum of every test group, timed (the plain GPU search)
+    d_stats = torch.zeros(G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    warm = tm.Plan(test.offsets[:9])
+    tm.tm_exhaustive_batch_dev(warm, d_tasks, d_devs, d_stats)
+    plan = tm.Plan(test.offsets, pdmax=5)
+    ex_ms, _ = timed_steps(lambda: tm.tm_exhaustive_batch_dev(plan, d_tasks, d_devs, d_stats), 2)
+    best = learn.stats_host(d_stats, G)["best"].astype(np.int64)
+    plan.close()
+    warm.close()
+    ex_s = min(ex_ms) / 1000.0
+    d_orders = torch.zeros(T, dtype=torch.int32, device="cuda")
+    d_ms = torch.zeros(G, dtype=torch.int32, device="cuda")
+    d_won = torch.zeros(G, dtype=torch.int32, device="cuda")
+    step = lambda: tm.tm_beam_batch_dev(ranker, d_tasks, d_offsets, test.offsets, d_devs,
+                                        BEAM_WIDTH, d_orders, d_ms, d_beam_won=d_won,
+                                        refine_starts=REFINE_STARTS)
+    for _ in range(args.warmup):
+        step()
+    ms, clocks = timed_steps(step, 20)
+    step_s = statistics.mean(ms) / 1000.0
+    got = d_ms.cpu().numpy().astype(np.int64)
+    gap = (got - best) / best
+    # the same search without the descent, for the ablation
+    tm.tm_beam_batch_dev(ranker, d_tasks, d_offsets, test.offsets, d_devs, BEAM_WIDTH, d_orders,
+                         d_ms)
+    gap0 = (d_ms.cpu().numpy().astype(np.int64) - best) / best
+    _, hms = tm.tm_heuristic_batch(test.tasks, test.offsets, test.dma)
+    gaph = (hms.astype(np.int64) - best) / best
+    within = float((gap <= 0.01).mean())
+    log(f"learned: {G / step_s:.3e} groups/s, within 1% {within:.4f}")
+    return {"workload": WORKLOADS["beam12"] + f"; exact-model descent from the best "
+                        f"{REFINE_STARTS} beams and the heuristic's order",
+            "metric": "task groups scheduled/s at <=1% gap", "value": G / step_s,
+            "unit": "groups/s", "ms_per_step": 1000 * step_s, "steps": 20,
+            "groups_within_1pct_per_s": within * G / step_s,
+            "within_1pct": within, "optimal": float((gap == 0).mean()),
+            "gap_mean": float(gap.mean()), "gap_p99": float(np.quantile(gap, 0.99)),
+            "gap_max": float(gap.max()), "beam_won": float(d_won.float().mean()),
+            "exhaustive_groups_per_s": G / ex_s,
+            "speedup_vs_exhaustive": ex_s / step_s,
+            "ablation": {"beam_only_within_1pct": float((gap0 <= 0.01).mean()),
+                         "beam_only_gap_mean": float(gap0.mean()),
+                         "heuristic_within_1pct": float((gaph <= 0.01).mean()),
+                         "heuristic_gap_mean": float(gaph.mean())},
+            "l2": "inputs < L2; no flush (ranker weights stay resident by design)",
+            "clocks": clocks, "train": train_info}
+
+
+def chain_ops_per_order(T: int) -> float:
+    """Integer operations per order of the chained search's tail, the part
+    every order needs: the last m = min(T, 4) positions walked depth-first
+    (64 / 15 / 4 / 1 steps for m! = 24 / 6 / 2 / 1 orders, 6 operations per
+    step: three maxima, three additions) and the reduction (7 operations
+    per pair of orders: min, max, 32-bit add, 64-bit add, two compares; 4
+    for a single order).  The head positions recomputed between blocks are
+    not counted."""
+    m = min(T, 4)
+    steps = {4: 64, 3: 15, 2: 4, 1: 1}[m]
+    red = {4: 12 * 7, 3: 3 * 7, 2: 7, 1: 4}[m]
+    return (6 * steps + red) / math.factorial(m)
+
+
+def chain_leg(args, log, groups: int = CHAIN_GROUPS, steps: int = 20) -> dict:
+    """Orders/s of the chained-task search (Sec. 6.1 experiment setup):
+    4096 groups of 4 workers x 4 dependent tasks, (4!)^4 = 331,776 orders
+    each, one tm_exhaustive_chain_batch_dev call per step, L2 flushed."""
+    import torch
+    from paper_1806_10113_gb300 import tm
+    dev = torch.device("cuda")
+    b = inputs.chained_groups(groups, CHAIN_WORKERS, CHAIN_ROUNDS, seed=7)
+    w = b.meta["workers"]
+    G = b.G
+    n_orders = G * math.factorial(CHAIN_WORKERS) ** CHAIN_ROUNDS
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_tasks, d_off, d_w, d_dma = d(b.tasks), d(b.offsets), d(w), d(b.dma)
+    d_stats = torch.zeros(G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    d_status = torch.zeros(G, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    step = lambda: tm.tm_exhaustive_chain_batch_dev(d_tasks, d_off, b.offsets, d_w, w, d_dma,
+                                                    d_stats, d_status)
+    for _ in range(args.warmup):
+        step()
+    ms, clocks = timed_steps(step, steps, flush=flush.zero_)
+    torch.cuda.synchronize()
+    if (d_status.cpu().numpy() != 0).any():
+        raise RuntimeError("chained workload: device status errors")
+    step_s = statistics.mean(ms) / 1000.0
+    ops = chain_ops_per_order(CHAIN_WORKERS)
+    achieved = ops * n_orders / step_s / 1e12
+    log(f"chain: {n_orders / step_s:.3e} orders/s")
+    return {"workload": (f"{G} chained groups: {CHAIN_WORKERS} workers x {CHAIN_ROUNDS} dependent "
+                         f"tasks, each DK or DT (p=1/2), log-uniform [1e4,1e7] ns, seed 7, DMA "
+                         f"engines alternating 2/1: exhaustive (T!)^N orders per group"),
+            "value": n_orders / step_s, "unit": UNIT, "ms_per_step": 1000 * step_s, "steps": steps,
+            "orders_per_step": n_orders,
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": INT32_PEAK_TOPS,
+                         "unit": "Tops/s (int32)", "frac": achieved / INT32_PEAK_TOPS,
+                         "kernel": "chain prep + enumeration + finalize (whole call)",
+                         "ops_per_order": round(ops, 3), "traffic": None},
+            "clocks": clocks}
+
+
+def run_chain(args):
+    """The chained-task search alone (its own line; the default run carries
+    the same measurement as the `chain` key)."""
+    import torch
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    leg = chain_leg(args, log, groups=args.groups or CHAIN_GROUPS, steps=min(args.steps, 50))
+    out = {"metric": "orderings evaluated/s (exact model, chained tasks)", "n_gpus": 1,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": leg.pop("workload"), "l2": leg.pop("l2")},
+           "gpu_launches": 3 * leg["steps"], **leg}
+    print(json.dumps(out))
+    return 0
+
 
 def run_tm(args):
     import torch
@@ -559,6 +806,11 @@ def run_tm(args):
         }
         if ws_total == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(b, 1 if args.workload == "dkdt32x12" else 2)
+        if ws_total == 1 and args.workload == "dkdt64x10" and not args.no_secondary:
+            log = lambda m: print(m, file=sys.stderr, flush=True)
+            result["n12"] = n12_leg(args, log)
+            result["learned"] = learned_leg(args, log)
+            result["chain"] = chain_leg(args, log)
         print(json.dumps(result))
     if dist is not None:
         dist.barrier()
@@ -612,8 +864,9 @@ def run_beam12(args):
     d_orders = torch.zeros(T, dtype=torch.int32, device="cuda")
     d_ms = torch.zeros(G, dtype=torch.int32, device="cuda")
     d_won = torch.zeros(G, dtype=torch.int32, device="cuda")
-    step = lambda: tm.tm_beam_batch_dev(ranker, d_tasks, d_offsets, test.offsets, d_devs, 64,
-                                        d_orders, d_ms, d_beam_won=d_won)
+    step = lambda: tm.tm_beam_batch_dev(ranker, d_tasks, d_offsets, test.offsets, d_devs,
+                                        BEAM_WIDTH, d_orders, d_ms, d_beam_won=d_won,
+                                        refine_starts=REFINE_STARTS)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -650,7 +903,7 @@ def run_beam12(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / 5
     # the ranker's forward kernel alone on the beam's row count, for its roofline
-    rows = sum(G * 64 * (12 - p) for p in range(12))
+    rows = sum(G * BEAM_WIDTH * (12 - p) for p in range(12))
     chunk = min(rows, 1 << 22)
     X = torch.zeros(chunk * 32, dtype=torch.int16, device="cuda")
     lg = torch.zeros(chunk, dtype=torch.float32, device="cuda")
@@ -671,7 +924,8 @@ def run_beam12(args):
         "warmup": args.warmup, "ms_per_step": 1000 * beam_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 ranker, int32 model",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS["beam12"], "groups": G, "beam": 64,
+        "config": {"workload": WORKLOADS["beam12"], "groups": G, "beam": BEAM_WIDTH,
+                   "refine_starts": REFINE_STARTS,
                    "l2": "inputs < L2; no flush (ranker weights stay resident by design)"},
         "gap_mean": float(gap.mean()), "gap_p99": float(np.quantile(gap, 0.99)),
         "gap_max": float(gap.max()),
@@ -706,8 +960,8 @@ def run_serve(args):
     b = inputs.training_groups(G, 4, 16, seed=4)
     rng = np.random.default_rng(4)
     arrivals = np.cumsum(rng.exponential(1e9 / rate, G)).astype(np.int64)
-    srv = tm.Server(exact_max_n=args.exact_max_n, beam_width=64, ranker=ranker, lanes=4,
-                    lane_groups=1024, lane_subsets=1024 * 64)
+    srv = tm.Server(exact_max_n=args.exact_max_n, beam_width=BEAM_WIDTH, ranker=ranker, lanes=4,
+                    lane_groups=1024, lane_subsets=1024 * 64, refine_starts=REFINE_STARTS)
     warm = min(G, 2000)
     srv.replay(b.tasks[:b.offsets[warm]], b.offsets[:warm + 1], b.dma[:warm],
                arrivals[:warm] - arrivals[0])
@@ -736,7 +990,8 @@ def run_serve(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 model, bf16 ranker",
         "data": "synthetic",
         "config": {"workload": WORKLOADS["serve20k"], "groups": G,
-                   "exact_max_n": args.exact_max_n, "lanes": 4, "lane_groups": 1024},
+                   "exact_max_n": args.exact_max_n, "lanes": 4, "lane_groups": 1024,
+                   "beam": BEAM_WIDTH, "refine_starts": REFINE_STARTS},
         "p50_ms": float(np.quantile(lat_ms, 0.5)), "p90_ms": float(np.quantile(lat_ms, 0.9)),
         "p99_ms": float(np.quantile(lat_ms, 0.99)), "max_ms": float(lat_ms.max()),
         "groups_per_s": G / span_s, "offered_groups_per_s": rate,
@@ -1103,6 +1358,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["tm", "reference"], default="tm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the 12-task, learned-path and chained legs")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dkdt64x10")
     ap.add_argument("--graph", action="store_true", help="replay each step as one CUDA graph")
     ap.add_argument("--tuning", default="",
@@ -1129,6 +1386,8 @@ def main(argv=None):
         return run_heuristic(args)
     if args.workload == "single6":
         return run_single(args)
+    if args.workload == "chain4x4":
+        return run_chain(args)
     return run_tm(args)
 
 
