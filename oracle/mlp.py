@@ -97,9 +97,10 @@ def loss_and_grads(theta, x, state_off, target_row, bf16=False, bf16_deltas=Fals
 # The kernels compute the same roundings (x, weights, activations and, in
 # training, the deltas, to bfloat16) but accumulate in float32, in an order
 # of their own.  Products of two bfloat16 values are exact in float32, so a
-# dot product of K terms (plus a bias) differs from the exact value by at
-# most (K + 1) u sum |terms|; u = 2^-22 here, two bits above float32's unit
-# roundoff, for tensor-core accumulation.  A bfloat16 rounding after it is
+# dot product of K terms plus a bias differs from the exact value by at most
+# (K + 4) u sum |terms| (the bias may enter as up to three exact bfloat16
+# parts, as in the tensor-core kernel); u = 2^-22 here, two bits above
+# float32's unit roundoff, for tensor-core accumulation.  A bfloat16 rounding after it is
 # monotone, so if the exact input is v and the float32 one lies within eta
 # of v, the two rounded values differ by at most
 #     cell(v, eta) = max(r(v + eta) - r(v), r(v) - r(v - eta)),
@@ -136,7 +137,7 @@ def forward_bound(theta, x):
         Wb, bias = to_bf16(p[W]), p[bname]
         K = Wb.shape[0]
         z = a[-1] @ Wb + bias
-        eps = dl[-1] @ np.abs(Wb) + U_ACC * (K + 1) * ((np.abs(a[-1]) + dl[-1]) @ np.abs(Wb)
+        eps = dl[-1] @ np.abs(Wb) + U_ACC * (K + 4) * ((np.abs(a[-1]) + dl[-1]) @ np.abs(Wb)
                                                      + np.abs(bias))
         act, d, lo, hi = relu_cell(z, eps)
         dl.append(d)
@@ -145,8 +146,8 @@ def forward_bound(theta, x):
         info.append({"z": z, "eps": eps, "mask_sure": (lo > 0) | (hi == 0)})
     w4 = to_bf16(p["w4"])
     logit = a[3] @ w4 + p["b4"][0]
-    E = dl[3] @ np.abs(w4) + U_ACC * (129) * ((np.abs(a[3]) + dl[3]) @ np.abs(w4)
-                                             + abs(p["b4"][0]))
+    E = dl[3] @ np.abs(w4) + U_ACC * 132 * ((np.abs(a[3]) + dl[3]) @ np.abs(w4)
+                                           + abs(p["b4"][0]))
     return logit, E, {"a": a, "delta": dl, "layers": info}
 
 
@@ -159,19 +160,19 @@ def layer_bound(theta, a_in, layer):
     Wb, bias = to_bf16(p[f"W{layer}"]), p[f"b{layer}"]
     a_in = np.asarray(a_in, dtype=np.float64)
     z = a_in @ Wb + bias
-    eps = U_ACC * (Wb.shape[0] + 1) * (np.abs(a_in) @ np.abs(Wb) + np.abs(bias))
+    eps = U_ACC * (Wb.shape[0] + 4) * (np.abs(a_in) @ np.abs(Wb) + np.abs(bias))
     act, d, _, _ = relu_cell(z, eps)
     return act, d
 
 
 def head_bound(theta, a3):
     """The logits from the kernels' own a3, and the per-row bound of a float32
-    evaluation (129 terms: 128 products and the bias)."""
+    evaluation (128 products and the bias, which may enter as three parts)."""
     p = unpack(theta)
     w4 = to_bf16(p["w4"])
     a3 = np.asarray(a3, dtype=np.float64)
     logit = a3 @ w4 + p["b4"][0]
-    return logit, U_ACC * 129 * (np.abs(a3) @ np.abs(w4) + abs(p["b4"][0]))
+    return logit, U_ACC * 132 * (np.abs(a3) @ np.abs(w4) + abs(p["b4"][0]))
 
 
 def backward_bound(theta, x, acts, logits, state_off, target_row):

@@ -39,15 +39,26 @@ constexpr int kGroups = 4;                 // warpgroups per CTA
 constexpr int kThreads = 128 * kGroups;
 
 // Global weight image == the first kImgBytes of the CTA's shared memory.
+// Each layer's bias enters the accumulator through one extra MMA of K = 16
+// issued first (accumulate off): A = a constant tile whose first three
+// columns are 1, B = a block holding the float32 bias split exactly into
+// three bfloat16 parts (hi + mid + lo carry all 24 significand bits), so the
+// accumulator starts at the bias and the epilogue adds nothing.
 constexpr int kImgW1 = 0;                            // [128 n x 32 k] core layout
 constexpr int kImgW2 = kImgW1 + kH * kF * 2;         // [128 x 128]
 constexpr int kImgW3 = kImgW2 + kH * kH * 2;
-constexpr int kImgB1 = kImgW3 + kH * kH * 2;         // float[128] each
-constexpr int kImgB2 = kImgB1 + kH * 4;
-constexpr int kImgB3 = kImgB2 + kH * 4;
-constexpr int kImgW4 = kImgB3 + kH * 4;              // w4 rounded to bf16, as float
-constexpr int kImgB4 = kImgW4 + kH * 4;
-constexpr int kImgBytes = kImgB4 + 16;               // b4 + padding to 16 bytes
+constexpr int kBiasK = 16;
+constexpr int kImgOnes = kImgW3 + kH * kH * 2;       // [128 rows x 16 k]: 1, 1, 1, 0, ...
+constexpr int kImgB1 = kImgOnes + kTile * kBiasK * 2;   // [128 n x 16 k]: hi, mid, lo, 0, ...
+constexpr int kImgB2 = kImgB1 + kH * kBiasK * 2;
+constexpr int kImgB3 = kImgB2 + kH * kBiasK * 2;
+// The head (logit = a3 . w4 + b4) is one more layer on the tensor cores with
+// N = 16: B holds w4 (bfloat16) in its row 0 and zeros below; its bias block
+// holds b4's three parts in row 0; the logit is accumulator column 0.
+constexpr int kHeadN = 16;
+constexpr int kImgW4 = kImgB3 + kH * kBiasK * 2;     // [16 n x 128 k]
+constexpr int kImgB4 = kImgW4 + kHeadN * kH * 2;     // [16 n x 16 k]
+constexpr int kImgBytes = kImgB4 + kHeadN * kBiasK * 2;
 constexpr int kActOff = (kImgBytes + 127) / 128 * 128;
 constexpr int kActBytes = kTile * kH * 2;            // per warpgroup
 constexpr int kBarOff = kActOff + kGroups * kActBytes;
@@ -78,6 +89,8 @@ __device__ __forceinline__ uint64_t mat_desc(uint32_t addr, uint32_t lbo, uint32
 // bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
                             ((uint32_t)(kTile >> 4) << 24);
+constexpr uint32_t kIdescHead = (1u << 4) | (1u << 7) | (1u << 10) |
+                                ((uint32_t)(kHeadN >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -188,6 +201,16 @@ __device__ __forceinline__ bool wg_sync_and(int g, bool v)
 
 // 32 consecutive f32 columns of this thread's accumulator row (warp w reads
 // TMEM lanes 32 w .. 32 w + 31).
+// Two float32 values rounded to bfloat16 and clamped at zero (relu after the
+// rounding: the same value as rounding after relu, up to the sign of zero),
+// packed with `lo` in the low half.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -196,15 +219,33 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32])
                  : "memory");
 }
 
-// Issues one layer: D (TMEM) = A (activation tile, K columns) x W^T.
-__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_base, uint32_t w_base, int K)
+// Issues one layer: D (TMEM) = ones x bias-block^T (the bias, accumulate
+// off), then D += A (activation tile, K columns) x W^T.
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_base, uint32_t w_base, int K,
+                                            uint32_t ones, uint32_t bias_blk, uint32_t idesc)
 {
+    constexpr uint32_t sbo_b = (uint32_t)(kBiasK / 8) * 128u;
+    tc_mma(tmem, mat_desc(ones, 128u, sbo_b), mat_desc(bias_blk, 128u, sbo_b), idesc, 0u);
     const uint32_t sbo = (uint32_t)(K / 8) * 128u;
     for (int s = 0; s < K / 16; ++s) {
         const uint64_t a = mat_desc(a_base + (uint32_t)s * 256u, 128u, sbo);
         const uint64_t b = mat_desc(w_base + (uint32_t)s * 256u, 128u, sbo);
-        tc_mma(tmem, a, b, kIdesc, s > 0 ? 1u : 0u);
+        tc_mma(tmem, a, b, idesc, 1u);
     }
+}
+
+__device__ __forceinline__ void tc_ld1(uint32_t taddr, uint32_t& r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+}
+
+// The three bfloat16 parts of a float32 value (hi + mid + lo == v exactly).
+__device__ __forceinline__ void split3(float v, bf16& hi, bf16& mid, bf16& lo)
+{
+    hi = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r1);
+    lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
 }
 
 __global__ void image_kernel(const float* __restrict__ P, const bf16* __restrict__ Wb,
@@ -221,13 +262,32 @@ __global__ void image_kernel(const float* __restrict__ P, const bf16* __restrict
         *reinterpret_cast<bf16*>(img + kImgW2 + core_off(n, k, kH)) = Wb[kBfW2 + i];
         *reinterpret_cast<bf16*>(img + kImgW3 + core_off(n, k, kH)) = Wb[kBfW3 + i];
     }
-    if (i < kH) {
-        reinterpret_cast<float*>(img + kImgB1)[i] = P[kOffB1 + i];
-        reinterpret_cast<float*>(img + kImgB2)[i] = P[kOffB2 + i];
-        reinterpret_cast<float*>(img + kImgB3)[i] = P[kOffB3 + i];
-        reinterpret_cast<float*>(img + kImgW4)[i] = __bfloat162float(Wb[kBfW4 + i]);
+    if (i < kTile * kBiasK) {
+        const int r = i / kBiasK, k = i - r * kBiasK;
+        *reinterpret_cast<bf16*>(img + kImgOnes + core_off(r, k, kBiasK)) =
+            __float2bfloat16_rn(k < 3 ? 1.0f : 0.0f);
+        const int offs[3] = {kImgB1, kImgB2, kImgB3};
+        const int src[3] = {kOffB1, kOffB2, kOffB3};
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            bf16 parts[3];
+            split3(P[src[l] + r], parts[0], parts[1], parts[2]);
+            *reinterpret_cast<bf16*>(img + offs[l] + core_off(r, k, kBiasK)) =
+                k < 3 ? parts[k] : __float2bfloat16_rn(0.0f);
+        }
     }
-    if (i < 4) reinterpret_cast<float*>(img + kImgB4)[i] = i == 0 ? P[kOffB4] : 0.0f;
+    if (i < kHeadN * kH) {
+        const int n = i / kH, k = i - n * kH;
+        *reinterpret_cast<bf16*>(img + kImgW4 + core_off(n, k, kH)) =
+            n == 0 ? Wb[kBfW4 + k] : __float2bfloat16_rn(0.0f);
+    }
+    if (i < kHeadN * kBiasK) {
+        const int n = i / kBiasK, k = i - n * kBiasK;
+        bf16 parts[3];
+        split3(P[kOffB4], parts[0], parts[1], parts[2]);
+        *reinterpret_cast<bf16*>(img + kImgB4 + core_off(n, k, kBiasK)) =
+            (n == 0 && k < 3) ? parts[k] : __float2bfloat16_rn(0.0f);
+    }
 }
 
 // KEEP: also store the three hidden layers' bfloat16 activations, row-major,
@@ -244,10 +304,6 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
     const uint32_t s_base = smem_u32(sm);
     const uint32_t bar_w = s_base + kBarOff, bar_mma = s_base + kBarOff + 8 * (1 + grp);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kBarOff + 8 * (1 + kGroups));
-    const float* b1 = reinterpret_cast<const float*>(sm + kImgB1);
-    const float* b2 = reinterpret_cast<const float*>(sm + kImgB2);
-    const float* b3 = reinterpret_cast<const float*>(sm + kImgB3);
-    const float* w4 = reinterpret_cast<const float*>(sm + kImgW4);
 
     if (warp == 0) {
         tc_alloc(smem_u32(s_tmem), kGroups * kH);   // one 128-column accumulator per warpgroup
@@ -302,40 +358,31 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
         tc_fence_before();
         wg_sync(grp);
         tc_fence_after();
-        float logit = 0.0f;
 #pragma unroll 1
         for (int layer = 0; layer < 3 && ok; ++layer) {
             const int K = layer == 0 ? kF : kH;
             const uint32_t w = s_base + (layer == 0 ? kImgW1 : layer == 1 ? kImgW2 : kImgW3);
             if (leader) {
-                issue_layer(tmem, act, w, K);
+                const uint32_t bias_blk =
+                    s_base + (layer == 0 ? kImgB1 : layer == 1 ? kImgB2 : kImgB3);
+                issue_layer(tmem, act, w, K, s_base + kImgOnes, bias_blk, kIdesc);
                 tc_commit(bar_mma);
             }
             ok = wg_sync_and(grp, mbar_wait(bar_mma, phase));
             phase ^= 1u;
             if (!ok) break;
             tc_fence_after();
-            const float* bias = layer == 0 ? b1 : layer == 1 ? b2 : b3;
 #pragma unroll 1
             for (int c = 0; c < kH / 32; ++c) {
                 uint32_t r[32];
                 tc_ld32(t_row + (uint32_t)(32 * c), r);
                 tc_wait_ld();
-                float bv[32];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 b4v = reinterpret_cast<const float4*>(bias + 32 * c)[q];
-                    bv[4 * q] = b4v.x; bv[4 * q + 1] = b4v.y; bv[4 * q + 2] = b4v.z; bv[4 * q + 3] = b4v.w;
-                }
-                if (layer < 2) {
+                {
                     uint32_t packed[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float lo = fmaxf(__uint_as_float(r[2 * j]) + bv[2 * j], 0.0f);
-                        const float hi = fmaxf(__uint_as_float(r[2 * j + 1]) + bv[2 * j + 1], 0.0f);
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
-                        packed[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        packed[j] = relu_bf16x2(__uint_as_float(r[2 * j]),
+                                                __uint_as_float(r[2 * j + 1]));
                     // 32 columns = 4 core matrices along K of this row
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -350,21 +397,6 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                             dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1],
                                                 packed[4 * q + 2], packed[4 * q + 3]);
                     }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 wq = reinterpret_cast<const float4*>(w4 + 32 * c)[q];
-                        const float wv[4] = {wq.x, wq.y, wq.z, wq.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int j = 4 * q + e;
-                            const float h = fmaxf(__uint_as_float(r[j]) + bv[j], 0.0f);
-                            const bf16 hb = __float2bfloat16_rn(h);
-                            logit += __bfloat162float(hb) * wv[e];
-                            if (KEEP && r0 + row < M)
-                                keep[((size_t)2 * M + r0 + row) * kH + 32 * c + j] = hb;
-                        }
-                    }
                 }
             }
             // the next layer's MMAs read the tile this layer just wrote, and
@@ -375,7 +407,20 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
             tc_fence_after();
         }
         if (!ok) break;
-        if (r0 + row < M) logits[r0 + row] = logit + *reinterpret_cast<const float*>(sm + kImgB4);
+        // the head: a3 (now in the activation tile) x w4 + b4, column 0
+        if (leader) {
+            issue_layer(tmem, act, s_base + kImgW4, kH, s_base + kImgOnes, s_base + kImgB4,
+                        kIdescHead);
+            tc_commit(bar_mma);
+        }
+        ok = wg_sync_and(grp, mbar_wait(bar_mma, phase));
+        phase ^= 1u;
+        if (!ok) break;
+        tc_fence_after();
+        uint32_t lv;
+        tc_ld1(t_row, lv);
+        tc_wait_ld();
+        if (r0 + row < M) logits[r0 + row] = __uint_as_float(lv);
     }
     if (!ok) {
         // a wait expired: report, mark this tile's scores, let in-flight
