@@ -29,8 +29,15 @@
 // position only, from per-position snapshots.  Per-thread best / worst with
 // the first rank and the exact sum go to per-group 64-bit key atomics.
 //
+// Groups of 2 <= T <= 4 workers and at least two rounds take a faster path
+// (chain_small_kernel): there the tail is the whole last round, so its rows
+// and release times sit in registers under compile-time indices, and a unit
+// of work is one prefix of the first R - 2 rounds, (T!)^2 orders, with round
+// R - 2's permutations read from a table.
+//
 //   chain_prep_kernel      per group: checks, reduction words
-//   chain_enum_kernel      every order of every group
+//   chain_enum_kernel      every order of every other group
+//   chain_small_kernel<T>  every order of the groups of T = 2, 3, 4 workers
 //   chain_finalize_kernel  reduction words -> tm_stats (orders unranked)
 //   chain_predict_kernel   one given order per group
 #include <algorithm>
@@ -275,6 +282,22 @@ __device__ __forceinline__ void tail4(Eng s, const int4* __restrict__ last, int 
     tail3(step_c(s, r3.w, r3), last, x0, x1, x2, a, rank + 18);
 }
 
+// The same tails with the rows in registers.
+__device__ __forceinline__ void tail2_regs(Eng s, int4 ru, int4 rv, ChainAcc& a, uint32_t rank)
+{
+    const int32_t m_uv = step_c(step_c(s, ru.w, ru), rv.w, rv).d;
+    const int32_t m_vu = step_c(step_c(s, rv.w, rv), ru.w, ru).d;
+    take_pair(a, m_uv, m_vu, rank);
+}
+
+__device__ __forceinline__ void tail3_regs(Eng s, int4 r0, int4 r1, int4 r2, ChainAcc& a,
+                                           uint32_t rank)
+{
+    tail2_regs(step_c(s, r0.w, r0), r1, r2, a, rank);
+    tail2_regs(step_c(s, r1.w, r1), r0, r2, a, rank + 2);
+    tail2_regs(step_c(s, r2.w, r2), r0, r1, a, rank + 4);
+}
+
 __device__ void flush(ChainAcc& a, unsigned long long* __restrict__ acc, int g)
 {
     if (a.best == INT32_MAX) return;
@@ -387,6 +410,210 @@ chain_enum_kernel(const unsigned long long* __restrict__ block_base, int G,
     }
 }
 
+// ---- fast path: 2 <= T <= 4 workers, R >= 2 rounds --------------------------
+//
+// With T <= 4 the tail is the whole last round, so its workers are 0 .. T-1
+// in every block: the last round's rows and release times can live in
+// registers under compile-time indices.  A unit of work is one prefix of the
+// first R - 2 rounds; the thread replays it once, then walks the T!
+// permutations of round R - 2 in lexicographic order from a table (each
+// recomputes only from the first position that differs from the previous
+// one) and, for each, the T! orders of the last round straight-line:
+// (T!)^2 consecutive ranks per unit.
+
+// Permutations of 0 .. T-1 in lexicographic order (nibbles), the first
+// position where each differs from the one before, and their inverses.
+struct SmallPerms {
+    uint16_t perm[3][24], inv[3][24];
+    uint8_t pivot[3][24];
+};
+constexpr SmallPerms make_small_perms()
+{
+    SmallPerms t{};
+    for (int T = 2; T <= 4; ++T) {
+        int a[4] = {0, 1, 2, 3};
+        int prev[4] = {0, 1, 2, 3};
+        for (int q = 0;; ++q) {
+            uint16_t pw = 0, iw = 0;
+            int piv = 0;
+            for (int i = 0; i < T; ++i) {
+                pw |= (uint16_t)(a[i] << (4 * i));
+                iw |= (uint16_t)(i << (4 * a[i]));
+            }
+            if (q > 0) {
+                piv = T;
+                for (int i = T - 1; i >= 0; --i)
+                    if (a[i] != prev[i]) piv = i;
+            }
+            t.perm[T - 2][q] = pw;
+            t.inv[T - 2][q] = iw;
+            t.pivot[T - 2][q] = (uint8_t)piv;
+            for (int i = 0; i < T; ++i) prev[i] = a[i];
+            // next permutation
+            int i = T - 2;
+            while (i >= 0 && a[i] >= a[i + 1]) --i;
+            if (i < 0) break;
+            int j = T - 1;
+            while (a[j] <= a[i]) --j;
+            const int x = a[i]; a[i] = a[j]; a[j] = x;
+            for (int l = i + 1, r = T - 1; l < r; ++l, --r) { const int y = a[l]; a[l] = a[r]; a[r] = y; }
+        }
+    }
+    return t;
+}
+__constant__ SmallPerms c_small = make_small_perms();
+
+// Element w (0 <= w < T) of a register array, by selects.
+template <int T>
+__device__ __forceinline__ int32_t pick(const int32_t (&v)[T], int w)
+{
+    int32_t r = v[0];
+#pragma unroll
+    for (int i = 1; i < T; ++i) r = w == i ? v[i] : r;
+    return r;
+}
+
+template <int T>
+__device__ __forceinline__ int4 pick4(const int4 (&v)[T], int w)
+{
+    int4 r = v[0];
+#pragma unroll
+    for (int i = 1; i < T; ++i) r = w == i ? v[i] : r;
+    return r;
+}
+
+// The T! orders of the last round's workers 0 .. T-1 from state s, in
+// lexicographic order: ranks rank, rank + 1, ...
+template <int T>
+__device__ __forceinline__ void tail_static(Eng s, const int4 (&lr)[T], ChainAcc& a, uint32_t rank)
+{
+    if constexpr (T == 2) {
+        const int32_t m01 = step_c(step_c(s, lr[0].w, lr[0]), lr[1].w, lr[1]).d;
+        const int32_t m10 = step_c(step_c(s, lr[1].w, lr[1]), lr[0].w, lr[0]).d;
+        take_pair(a, m01, m10, rank);
+    } else if constexpr (T == 3) {
+        const int4 x[3] = {lr[0], lr[1], lr[2]};
+        tail2_regs(step_c(s, x[0].w, x[0]), x[1], x[2], a, rank);
+        tail2_regs(step_c(s, x[1].w, x[1]), x[0], x[2], a, rank + 2);
+        tail2_regs(step_c(s, x[2].w, x[2]), x[0], x[1], a, rank + 4);
+    } else {
+        tail3_regs(step_c(s, lr[0].w, lr[0]), lr[1], lr[2], lr[3], a, rank);
+        tail3_regs(step_c(s, lr[1].w, lr[1]), lr[0], lr[2], lr[3], a, rank + 6);
+        tail3_regs(step_c(s, lr[2].w, lr[2]), lr[0], lr[1], lr[3], a, rank + 12);
+        tail3_regs(step_c(s, lr[3].w, lr[3]), lr[0], lr[1], lr[2], a, rank + 18);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kChainBlock)
+chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
+                   const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
+                   unsigned long long* __restrict__ acc, unsigned long long per_thread)
+{
+    constexpr int F = T == 2 ? 2 : T == 3 ? 6 : 24;
+    const unsigned long long total = unit_base[G];
+    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long u = t * per_thread;
+    const unsigned long long u_end = min(total, u + per_thread);
+    if (u >= u_end) return;
+    int g = 0;
+    {
+        int lo = 0, hi = G;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (unit_base[mid] <= u) lo = mid; else hi = mid;
+        }
+        g = lo;
+    }
+    ChainAcc a{INT32_MAX, -1, 0u, 0u, 0ull};
+    while (u < u_end) {
+        while (u >= unit_base[g + 1]) ++g;
+        const ChainInfo ci = info[g];
+        const unsigned long long g_end = min(u_end, (unsigned long long)unit_base[g + 1]);
+        if (ci.status != 0 || ci.T != T || ci.R < 2) {   // rejected by the prep kernel
+            u = g_end;
+            continue;
+        }
+        const int R = ci.R;
+        // the penultimate and last rounds' rows
+        int4 prow[T], lrow[T];
+        int32_t sh_pen = 0, sh_last = 0;
+#pragma unroll
+        for (int w = 0; w < T; ++w) {
+            const tm_task p = tasks[ci.off + (R - 2) * T + w];
+            const tm_task l = tasks[ci.off + (R - 1) * T + w];
+            prow[w] = make_int4(p.htd, p.k, p.dth, 0);
+            lrow[w] = make_int4(l.htd, l.k, l.dth, 0);
+            sh_pen += p.htd;
+            sh_last += l.htd;
+        }
+        for (; u < g_end; ++u) {
+            const uint32_t o = (uint32_t)(u - unit_base[g]);
+            // replay rounds 0 .. R-3 of prefix o (digits base T!, round 0 first)
+            Eng s{0, 0, 0};
+            int32_t c[T];
+#pragma unroll
+            for (int w = 0; w < T; ++w) c[w] = 0;
+            {
+                uint32_t digits[TM_MAX_TASKS];
+                uint32_t q = o;
+                for (int r = R - 3; r >= 0; --r) { digits[r] = q % F; q /= F; }
+                for (int r = 0; r <= R - 3; ++r) {
+                    const uint32_t pw = c_small.perm[T - 2][digits[r]];
+                    const uint32_t iw = c_small.inv[T - 2][digits[r]];
+                    if (ci.dma == 1) {
+                        s.h = s.d;
+                        for (int w = 0; w < T; ++w) s.d += tasks[ci.off + r * T + w].htd;
+                    }
+                    int32_t dend[T];
+#pragma unroll
+                    for (int i = 0; i < T; ++i) {
+                        const int w = (int)((pw >> (4 * i)) & 0xF);
+                        const tm_task x = tasks[ci.off + r * T + w];
+                        s = step_c(s, pick<T>(c, w), make_int4(x.htd, x.k, x.dth, 0));
+                        dend[i] = s.d;
+                    }
+#pragma unroll
+                    for (int w = 0; w < T; ++w) c[w] = pick<T>(dend, (int)((iw >> (4 * w)) & 0xF));
+                }
+            }
+            // the penultimate round's rows with their release times
+            int4 pr[T];
+#pragma unroll
+            for (int w = 0; w < T; ++w) pr[w] = make_int4(prow[w].x, prow[w].y, prow[w].z, c[w]);
+            Eng s0 = s;                       // entering the penultimate round
+            if (ci.dma == 1) { s0.h = s0.d; s0.d += sh_pen; }
+            Eng st[T];
+            int32_t dend[T];
+            uint32_t rank = o * (uint32_t)(F * F);
+            for (int q = 0; q < F; ++q) {
+                const uint32_t pw = c_small.perm[T - 2][q];
+                const int piv = c_small.pivot[T - 2][q];
+#pragma unroll
+                for (int i = 0; i < T; ++i) {
+                    if (i >= piv) {
+                        const int4 x = pick4<T>(pr, (int)((pw >> (4 * i)) & 0xF));
+                        st[i] = step_c(i == 0 ? s0 : st[i > 0 ? i - 1 : 0], x.w, x);
+                        dend[i] = st[i].d;
+                    }
+                }
+                // the last round: release times from this round's DtH ends
+                const uint32_t iw = c_small.inv[T - 2][q];
+                int4 lr[T];
+#pragma unroll
+                for (int w = 0; w < T; ++w)
+                    lr[w] = make_int4(lrow[w].x, lrow[w].y, lrow[w].z,
+                                      pick<T>(dend, (int)((iw >> (4 * w)) & 0xF)));
+                Eng s1 = st[T - 1];
+                if (ci.dma == 1) { s1.h = s1.d; s1.d += sh_last; }
+                tail_static<T>(s1, lr, a, rank);
+                rank += F;
+            }
+        }
+        flush(a, acc, g);
+    }
+}
+
 // Order of rank `rank` of a chained group as task indices, and its makespan.
 __device__ int32_t chain_order_of_rank(const tm_task* __restrict__ tasks, const ChainInfo& ci,
                                        uint32_t rank, uint8_t* order_out)
@@ -493,8 +720,32 @@ struct ChainScratch {
     void* p = nullptr;
     size_t cap = 0;
     int device = -1;
-    std::vector<unsigned long long> h_base;
+    std::vector<unsigned long long> h_base;   // generic blocks, then fast-path units per T
 };
+
+// Groups the fast path takes: 2 <= T <= 4 workers and at least two rounds.
+inline bool chain_fast(int n, int T) { return T >= 2 && T <= 4 && n % T == 0 && n / T >= 2 && n <= TM_MAX_TASKS; }
+
+template <int T>
+cudaError_t launch_small(const unsigned long long* d_base, const unsigned long long* h_base, int G,
+                         const ChainInfo* d_info, const tm_task* d_tasks, unsigned long long* d_acc,
+                         int dev, cudaStream_t s)
+{
+    const unsigned long long total = h_base[G];
+    if (total == 0) return cudaSuccess;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain_small_kernel<T>, kChainBlock,
+                                                      0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const unsigned long long resident = (unsigned long long)std::max(sms, 1) * per_sm * kChainBlock;
+    const unsigned long long threads = std::min(total, resident);
+    const unsigned long long per_thread = (total + threads - 1) / threads;
+    const unsigned long long used = (total + per_thread - 1) / per_thread;
+    chain_small_kernel<T><<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
+        d_base, G, d_info, d_tasks, d_acc, per_thread);
+    return cudaGetLastError();
+}
 thread_local ChainScratch t_chain;
 
 }  // namespace
@@ -509,8 +760,10 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t b_base = al((size_t)(G + 1) * 8), b_info = al((size_t)G * sizeof(ChainInfo)),
+    // four prefix tables: the generic kernel's blocks, the fast path's units for T = 2, 3, 4
+    const size_t b_base = 4 * al((size_t)(G + 1) * 8), b_info = al((size_t)G * sizeof(ChainInfo)),
                  b_acc = al((size_t)G * 32);
+    const size_t base_stride = al((size_t)(G + 1) * 8) / 8;
     const size_t need = b_base + b_info + b_acc;
     if (sc.device != dev || sc.cap < need) {
         if (sc.p && sc.device == dev) {
@@ -527,19 +780,32 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     unsigned long long* d_base = reinterpret_cast<unsigned long long*>(p);
     ChainInfo* d_info = reinterpret_cast<ChainInfo*>(p + b_base);
     unsigned long long* d_acc = reinterpret_cast<unsigned long long*>(p + b_base + b_info);
-    // blocks of m! orders per group (0 for a shape the prep kernel rejects)
-    sc.h_base.assign((size_t)G + 1, 0ull);
+    // blocks of m! orders per group for the generic kernel (0 for a shape the
+    // prep kernel rejects, and for the fast path's groups); units of (T!)^2
+    // orders per fast-path group, one table per T
+    sc.h_base.assign(4 * base_stride, 0ull);
+    unsigned long long* hb[4] = {sc.h_base.data(), sc.h_base.data() + base_stride,
+                                 sc.h_base.data() + 2 * base_stride,
+                                 sc.h_base.data() + 3 * base_stride};
     for (int g = 0; g < G; ++g) {
         const int n = h_offsets[g + 1] - h_offsets[g], T = h_workers[g];
         const uint64_t orders = (T >= 1 && n % T == 0) ? chain_orders(T, n / T) : 0;
-        sc.h_base[g + 1] = sc.h_base[g] + (orders ? orders / factorial_u64(chain_tail(T)) : 0);
+        const bool fast = orders && chain_fast(n, T);
+        for (int k = 0; k < 4; ++k) hb[k][g + 1] = hb[k][g];
+        if (!orders) continue;
+        if (fast) {
+            const uint64_t f = factorial_u64(T);
+            hb[T - 1][g + 1] += orders / (f * f);
+        } else {
+            hb[0][g + 1] += orders / factorial_u64(chain_tail(T));
+        }
     }
-    if (cudaMemcpyAsync(d_base, sc.h_base.data(), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s) !=
+    if (cudaMemcpyAsync(d_base, sc.h_base.data(), 4 * base_stride * 8, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return TM_ECUDA;
     chain_prep_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_tasks, d_offsets, d_workers, G, d_devs,
                                                      d_info, d_acc, d_status);
-    const unsigned long long total = sc.h_base[G];
+    const unsigned long long total = hb[0][G];
     if (total > 0) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -553,6 +819,13 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
         chain_enum_kernel<<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
             d_base, G, d_info, d_tasks, d_acc, per_thread);
     }
+    if (launch_small<2>(d_base + base_stride, hb[1], G, d_info, d_tasks, d_acc, dev, s) !=
+            cudaSuccess ||
+        launch_small<3>(d_base + 2 * base_stride, hb[2], G, d_info, d_tasks, d_acc, dev, s) !=
+            cudaSuccess ||
+        launch_small<4>(d_base + 3 * base_stride, hb[3], G, d_info, d_tasks, d_acc, dev, s) !=
+            cudaSuccess)
+        return TM_ECUDA;
     chain_finalize_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_info, d_tasks, G, d_acc, d_stats,
                                                          d_status);
     return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
