@@ -583,12 +583,17 @@ def learned_leg(args, log) -> dict:
 
 def chain_ops_per_order(T: int) -> float:
     """Integer operations per order of the chained search's tail, the part
-    every order needs: the last m = min(T, 4) positions walked depth-first
-    (64 / 15 / 4 / 1 steps for m! = 24 / 6 / 2 / 1 orders, 6 operations per
-    step: three maxima, three additions) and the reduction (7 operations
-    per pair of orders: min, max, 32-bit add, 64-bit add, two compares; 4
-    for a single order).  The head positions recomputed between blocks are
-    not counted."""
+    every order needs.  Four workers (the fast path): 16 recurrence steps
+    for the first two positions (6 operations each: three maxima, three
+    additions), then each order's last two positions in closed form,
+    max(d + A, k + P, h + Q, R) (6 operations), R for each pair of orders (4)
+    and its four E terms, and the reduction (7 per pair of orders: min, max,
+    32-bit add, 64-bit add, two compares): 376 per 24 orders.  Otherwise the
+    last m = min(T, 4) positions walked step by step (64 / 15 / 4 / 1 steps
+    for m! = 24 / 6 / 2 / 1 orders) plus the same reduction (4 for a single
+    order).  The head positions recomputed between blocks are not counted."""
+    if T == 4:
+        return (6 * 16 + 4 + 12 * 4 + 24 * 6 + 12 * 7) / 24
     m = min(T, 4)
     steps = {4: 64, 3: 15, 2: 4, 1: 1}[m]
     red = {4: 12 * 7, 3: 3 * 7, 2: 7, 1: 4}[m]

@@ -482,6 +482,103 @@ __device__ __forceinline__ int4 pick4(const int4 (&v)[T], int w)
     return r;
 }
 
+// The fast path's additions run as multiply-adds by `one` (a kernel
+// parameter, always 1), so that they issue on the FMA pipe beside the ALU
+// pipe's maxima; the values are those of plain additions.
+__device__ __forceinline__ int32_t fadd(int32_t x, int32_t y, uint32_t one)
+{
+    return (int32_t)((uint32_t)x * one + (uint32_t)y);
+}
+
+__device__ __forceinline__ Eng step_f(Eng s, int32_t c, int4 t, uint32_t one)
+{
+    Eng r;
+    r.h = fadd(max(s.h, c), t.x, one);
+    r.k = fadd(max(s.k, r.h), t.y, one);
+    r.d = fadd(max(s.d, r.k), t.z, one);
+    return r;
+}
+
+// The last two positions in closed form.  From state (h, k, d), appending
+// worker x then worker y (release times c_x, c_y) ends at
+//     max(d + A_xy, k + P_xy, h + Q_xy, R_xy)
+// with A_xy = D_x + D_y, P_xy = K_x + max(D_x, K_y) + D_y,
+// Q_xy = H_x + max(P_xy, C_y), C_y = H_y + K_y + D_y, and
+// R_xy = max(c_x + Q_xy, c_y + C_y): the two recurrence steps written as the
+// longest of the paths through them.  A, P and Q depend only on the group's
+// last round; R on the release times.
+struct Pair4 {
+    int32_t A[4][4], P[4][4], Q[4][4], C[4];
+};
+
+__device__ __forceinline__ void pair4_setup(const int4 (&lr)[4], Pair4& q)
+{
+#pragma unroll
+    for (int y = 0; y < 4; ++y) q.C[y] = lr[y].x + lr[y].y + lr[y].z;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            if (x == y) continue;
+            q.A[x][y] = lr[x].z + lr[y].z;
+            q.P[x][y] = lr[x].y + max(lr[x].z, lr[y].y) + lr[y].z;
+            q.Q[x][y] = lr[x].x + max(q.P[x][y], q.C[y]);
+        }
+}
+
+// The two orders of the last two workers x < y from state s.
+template <int X, int Y>
+__device__ __forceinline__ void tail2_pair(Eng s, const Pair4& q, const int32_t (&E)[4],
+                                           const int32_t (&c)[4], ChainAcc& a, uint32_t rank,
+                                           uint32_t one)
+{
+    const int32_t r_xy = max(fadd(c[X], q.Q[X][Y], one), E[Y]);
+    const int32_t r_yx = max(fadd(c[Y], q.Q[Y][X], one), E[X]);
+    const int32_t m_xy = max(max(fadd(s.d, q.A[X][Y], one), fadd(s.k, q.P[X][Y], one)),
+                             max(fadd(s.h, q.Q[X][Y], one), r_xy));
+    const int32_t m_yx = max(max(fadd(s.d, q.A[Y][X], one), fadd(s.k, q.P[Y][X], one)),
+                             max(fadd(s.h, q.Q[Y][X], one), r_yx));
+    take_pair(a, m_xy, m_yx, rank);
+}
+
+// The 24 orders of the last round's four workers from state s (rows with
+// release times in lr; E[y] = c_y + C_y).
+__device__ __forceinline__ void tail4_pair(Eng s, const int4 (&lr)[4], const Pair4& q,
+                                           ChainAcc& a, uint32_t rank, uint32_t one)
+{
+    int32_t c[4], E[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        c[w] = lr[w].w;
+        E[w] = fadd(c[w], q.C[w], one);
+    }
+    // first worker 0
+    {
+        const Eng s0 = step_f(s, c[0], lr[0], one);
+        tail2_pair<2, 3>(step_f(s0, c[1], lr[1], one), q, E, c, a, rank, one);
+        tail2_pair<1, 3>(step_f(s0, c[2], lr[2], one), q, E, c, a, rank + 2, one);
+        tail2_pair<1, 2>(step_f(s0, c[3], lr[3], one), q, E, c, a, rank + 4, one);
+    }
+    {
+        const Eng s1 = step_f(s, c[1], lr[1], one);
+        tail2_pair<2, 3>(step_f(s1, c[0], lr[0], one), q, E, c, a, rank + 6, one);
+        tail2_pair<0, 3>(step_f(s1, c[2], lr[2], one), q, E, c, a, rank + 8, one);
+        tail2_pair<0, 2>(step_f(s1, c[3], lr[3], one), q, E, c, a, rank + 10, one);
+    }
+    {
+        const Eng s2 = step_f(s, c[2], lr[2], one);
+        tail2_pair<1, 3>(step_f(s2, c[0], lr[0], one), q, E, c, a, rank + 12, one);
+        tail2_pair<0, 3>(step_f(s2, c[1], lr[1], one), q, E, c, a, rank + 14, one);
+        tail2_pair<0, 1>(step_f(s2, c[3], lr[3], one), q, E, c, a, rank + 16, one);
+    }
+    {
+        const Eng s3 = step_f(s, c[3], lr[3], one);
+        tail2_pair<1, 2>(step_f(s3, c[0], lr[0], one), q, E, c, a, rank + 18, one);
+        tail2_pair<0, 2>(step_f(s3, c[1], lr[1], one), q, E, c, a, rank + 20, one);
+        tail2_pair<0, 1>(step_f(s3, c[2], lr[2], one), q, E, c, a, rank + 22, one);
+    }
+}
+
 // The T! orders of the last round's workers 0 .. T-1 from state s, in
 // lexicographic order: ranks rank, rank + 1, ...
 template <int T>
@@ -508,7 +605,8 @@ template <int T>
 __global__ void __launch_bounds__(kChainBlock)
 chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                    const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
-                   unsigned long long* __restrict__ acc, unsigned long long per_thread)
+                   unsigned long long* __restrict__ acc, unsigned long long per_thread,
+                   uint32_t one)
 {
     constexpr int F = T == 2 ? 2 : T == 3 ? 6 : 24;
     const unsigned long long total = unit_base[G];
@@ -547,6 +645,8 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
             sh_pen += p.htd;
             sh_last += l.htd;
         }
+        Pair4 pq;
+        if constexpr (T == 4) pair4_setup(reinterpret_cast<const int4 (&)[4]>(lrow), pq);
         for (; u < g_end; ++u) {
             const uint32_t o = (uint32_t)(u - unit_base[g]);
             // replay rounds 0 .. R-3 of prefix o (digits base T!, round 0 first)
@@ -606,7 +706,9 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                                       pick<T>(dend, (int)((iw >> (4 * w)) & 0xF)));
                 Eng s1 = st[T - 1];
                 if (ci.dma == 1) { s1.h = s1.d; s1.d += sh_last; }
-                tail_static<T>(s1, lr, a, rank);
+                if constexpr (T == 4)
+                    tail4_pair(s1, reinterpret_cast<const int4 (&)[4]>(lr), pq, a, rank, one);
+                else tail_static<T>(s1, lr, a, rank);
                 rank += F;
             }
         }
@@ -743,7 +845,7 @@ cudaError_t launch_small(const unsigned long long* d_base, const unsigned long l
     const unsigned long long per_thread = (total + threads - 1) / threads;
     const unsigned long long used = (total + per_thread - 1) / per_thread;
     chain_small_kernel<T><<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
-        d_base, G, d_info, d_tasks, d_acc, per_thread);
+        d_base, G, d_info, d_tasks, d_acc, per_thread, 1u);
     return cudaGetLastError();
 }
 thread_local ChainScratch t_chain;
