@@ -12,10 +12,12 @@
 // its unused tasks; row ((g * B + b) * R + slot) of the feature matrix holds
 // the features of "append the slot-th unused task", R = nmax - i (written by
 // the init kernel for i = 0 and by the previous selection after that).  The
-// ranker scores the rows; a block per group turns scores into log-softmax
-// over each beam's candidates, adds the beam's log-probability, keeps the
-// best B candidates (the best 64 of the B x R keys by warp-sorted runs and
-// pairwise merges; ties: lower beam, then lower slot) and applies them.
+// ranker scores the rows; a block per group (a warp per group for large
+// batches at widths up to 16) turns scores into log-softmax over each beam's
+// candidates, adds the beam's log-probability, keeps the best B candidates
+// (the best 64 of the B x R keys by warp-sorted runs and pairwise merges, or
+// B rounds of a warp-wide maximum; ties: lower beam, then lower slot) and
+// applies them.
 #include <cuda_bf16.h>
 
 #include "rank_features.cuh"
@@ -279,6 +281,129 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         if (slot < left && ns[b].alive)
             write_row(X, ((int64_t)g * B + b) * R1 + slot, tasks + off, n, ns[b], dma, sc, slot);
     }
+}
+
+// The selection for beam widths up to 16 with one warp per group, for large
+// batches (the next position's rows come from beam_features_kernel).  It
+// forms the same log-sum-exp and the same keys, with the same float
+// expressions in the same order, as beam_select_kernel; key i = b R + c sits
+// in lane i mod 32 (at most 16 x 16 keys, eight per lane).  Each lane sorts
+// its eight (a 19-comparator network, descending), then B rounds take the
+// warp-wide maximum of the lanes' heads -- the high words by one reduction,
+// the low words among the lanes that hold the top high word by a second --
+// and the lane that held it advances.  The keys are distinct, so the B kept
+// beams, and their order, are those of the block kernel.
+constexpr int kWarpSelectMaxB = 16;
+constexpr int kWarpSelectKeys = kWarpSelectMaxB * TM_MAX_TASKS / 32;
+static_assert(kWarpSelectKeys == 8, "the sorting network below is for eight keys");
+
+__device__ __forceinline__ void cx_desc(unsigned long long& a, unsigned long long& b)
+{
+    const unsigned long long hi = a > b ? a : b, lo = a > b ? b : a;
+    a = hi;
+    b = lo;
+}
+
+__global__ void __launch_bounds__(256)
+beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
+                        const float* __restrict__ logits, const BeamState* __restrict__ cur,
+                        BeamState* __restrict__ nxt, int G, int B, int R, int pos)
+{
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;   // whole warps
+    const int off = offsets[g], n = offsets[g + 1] - off;
+    const BeamState* cg = cur + (size_t)g * B;
+    BeamState* ng = nxt + (size_t)g * B;
+    if (pos >= n) {   // group already complete: carry the beams over
+        if (lane < B) ng[lane] = cg[lane];
+        return;
+    }
+    const int cands = n - pos;
+    const float* lg0 = logits + (size_t)g * B * R;
+    // lane b < B: beam b's log-sum-exp
+    float lse = 0.0f, logp = 0.0f;
+    int alive = 0;
+    if (lane < B) {
+        const BeamState s = cg[lane];
+        float mx = -INFINITY, z = 0.0f;
+        if (s.alive) {
+            const float* lg = lg0 + (size_t)lane * R;
+            float v[TM_MAX_TASKS];
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c) v[c] = c < cands ? lg[c] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c)
+                if (c < cands) mx = fmaxf(mx, v[c]);
+#pragma unroll
+            for (int c = 0; c < TM_MAX_TASKS; ++c)
+                if (c < cands) z += expf(v[c] - mx);
+        }
+        lse = s.alive ? mx + logf(z) : 0.0f;
+        logp = s.logp;
+        alive = s.alive;
+    }
+    unsigned long long key[kWarpSelectKeys];
+#pragma unroll
+    for (int q = 0; q < kWarpSelectKeys; ++q) {
+        const int i = 32 * q + lane;
+        const int b = (int)((unsigned)i / (unsigned)R), c = i - b * R;
+        const float lb = __shfl_sync(kFull, lse, b & 31);
+        const float lp = __shfl_sync(kFull, logp, b & 31);
+        const int al = __shfl_sync(kFull, alive, b & 31);
+        key[q] = 0ull;
+        if (b < B && c < cands && al) {
+            const float score = lp + (lg0[(size_t)b * R + c] - lb);
+            key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
+        }
+    }
+    cx_desc(key[0], key[2]); cx_desc(key[1], key[3]); cx_desc(key[4], key[6]); cx_desc(key[5], key[7]);
+    cx_desc(key[0], key[4]); cx_desc(key[1], key[5]); cx_desc(key[2], key[6]); cx_desc(key[3], key[7]);
+    cx_desc(key[0], key[1]); cx_desc(key[2], key[3]); cx_desc(key[4], key[5]); cx_desc(key[6], key[7]);
+    cx_desc(key[2], key[4]); cx_desc(key[3], key[5]);
+    cx_desc(key[1], key[4]); cx_desc(key[3], key[6]);
+    cx_desc(key[1], key[2]); cx_desc(key[3], key[4]); cx_desc(key[5], key[6]);
+    unsigned long long mine = 0ull;   // lane r: the r-th best key (0: none)
+    for (int r = 0; r < B; ++r) {
+        const uint32_t hi = (uint32_t)(key[0] >> 32), lo = (uint32_t)key[0];
+        const uint32_t mhi = __reduce_max_sync(kFull, hi);
+        if (mhi == 0u) break;   // no keys left: the remaining beams die
+        const uint32_t mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+        if (lane == r) mine = ((unsigned long long)mhi << 32) | mlo;
+        if (hi == mhi && lo == mlo) {
+#pragma unroll
+            for (int q = 0; q + 1 < kWarpSelectKeys; ++q) key[q] = key[q + 1];
+            key[kWarpSelectKeys - 1] = 0ull;
+        }
+    }
+    // the kept candidate's beam pb and slot c, and pb's log-sum-exp
+    int pb = 0, c = 0;
+    if (mine != 0ull) {
+        const int i = (int)(0xFFFFu - (uint32_t)(mine & 0xFFFFu));
+        pb = i / R;
+        c = i - pb * R;
+    }
+    const float plse = __shfl_sync(kFull, lse, pb);
+    if (lane >= B) return;
+    BeamState s;
+    if (mine == 0ull) {
+        s.alive = 0;
+        s.h = s.k = s.d = 0;
+        s.used = 0;
+        s.order = 0;
+        s.logp = 0.0f;
+    } else {
+        const BeamState p = cg[pb];
+        const int j = slot_task(p.used, n, c);
+        const tm_task t = tasks[off + j];
+        const Eng e = step(Eng{p.h, p.k, p.d}, t.htd, t.k, t.dth);
+        s.h = e.h; s.k = e.k; s.d = e.d;
+        s.used = p.used | (1u << j);
+        s.order = p.order | ((unsigned long long)j << (4 * pos));
+        s.logp = p.logp + (lg0[(size_t)pb * R + c] - plse);
+        s.alive = 1;
+    }
+    ng[lane] = s;
 }
 
 // Best finished beam vs the heuristic's order, which is already in `orders`
@@ -564,7 +689,11 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
     const BeamState* c = static_cast<const BeamState*>(cur);
     BeamState* nx = static_cast<BeamState*>(nxt);
     __nv_bfloat16* x = reinterpret_cast<__nv_bfloat16*>(X);
-    if (G > 1024) {
+    if (!X && B <= kWarpSelectMaxB) {
+        const int64_t threads = (int64_t)G * 32;
+        beam_select_warp_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            offsets, tasks, logits, c, nx, G, B, R, pos);
+    } else if (G > 1024) {
         if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, x);
         else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, nullptr);
     } else {

@@ -327,6 +327,27 @@ def test_beam_large_batch_equals_small_batches():
     assert np.array_equal(big[3][:25], small[3]) and (big[2] == 0).all()
 
 
+@pytest.mark.parametrize("width", [16, 7, 1])
+def test_beam_warp_selection_equals_block_selection(width):
+    # Ragged groups of 1..16 tasks, enough of them that the first position
+    # has more than 2^19 rows (the separate row kernel and, for widths up to
+    # 16, the one-warp-per-group selection); 40 of them alone take the fused
+    # block selection.  The kept beams, so the orders, makespans and winners,
+    # must agree exactly.
+    rng = np.random.default_rng(21)
+    sizes = rng.integers(1, 17, (1 << 19) // (16 * width) + 200)
+    sizes[0] = 16
+    b = inputs.random_groups(22, sizes, hi=3_000_000)
+    r = tm.Ranker(seed=8)
+    big = run_beam(b, r, width)
+    sub = inputs.make_batch([b.group(g) for g in range(40)], b.dma[:40])
+    small = run_beam(sub, r, width)
+    T = int(sub.offsets[-1])
+    assert (big[2] == 0).all() and (small[2] == 0).all()
+    assert np.array_equal(big[0][:T], small[0]) and np.array_equal(big[1][:40], small[1])
+    assert np.array_equal(big[3][:40], small[3])
+
+
 def test_beam_is_exhaustive_when_wide_enough():
     # n <= 4 and width 24 >= n!: every partial order survives every step
     rng = np.random.default_rng(14)
