@@ -180,7 +180,11 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  size); 2: as a loop (less code: faster on batches that
  *                  mix group sizes); 3: as 1, with each order's addition
  *                  on the FMA pipe too; 4: as 3, compiled for four
- *                  resident blocks per SM (at most 128 registers);
+ *                  resident blocks per SM (at most 128 registers); 5: as
+ *                  3, and a prefix whose 24 completions all end on one
+ *                  engine's path (the DtH engine's, the kernel engine's or
+ *                  the HtD engine's, on every lane of the warp) takes the
+ *                  closed form of their minimum, maximum and sum;
  *                  0: default 2 */
 typedef struct tm_tuning {
     int32_t pdmax;

@@ -11,7 +11,8 @@
 // Step i (the i-th position): every live beam b of group g proposes each of
 // its unused tasks; row ((g * B + b) * R + slot) of the feature matrix holds
 // the features of "append the slot-th unused task", R = nmax - i (written by
-// the init kernel for i = 0 and by the previous selection after that).  The
+// the previous selection or the row kernel; at i = 0 the init kernel writes
+// beam 0's rows alone, row g R + slot, the only live beam there).  The
 // ranker scores the rows; a block per group (a warp per group for large
 // batches at widths up to 16) turns scores into log-softmax over each beam's
 // candidates, adds the beam's log-probability, keeps the best B candidates
@@ -72,7 +73,8 @@ __device__ __forceinline__ void write_row(__nv_bfloat16* __restrict__ X, int64_t
 }
 
 // Initial beams (only beam 0 live, empty prefix) and the candidate rows of
-// position 0 (R rows per beam; rows of dead beams are never read).
+// position 0: beam 0's alone, R per group (row g R + slot), since no other
+// beam has candidates there.
 __global__ void beam_init_kernel(const int32_t* __restrict__ offsets,
                                  const int32_t* __restrict__ status, const tm_task* __restrict__ tasks,
                                  const tm_device* __restrict__ devs, int G, int B, int R,
@@ -100,7 +102,7 @@ __global__ void beam_init_kernel(const int32_t* __restrict__ offsets,
         scale[g] = sc;
         if (s.alive)
             for (int slot = 0; slot < n; ++slot)
-                write_row(X, (int64_t)t * R + slot, tasks + off, n, s, devs[g].dma_engines, sc, slot);
+                write_row(X, (int64_t)g * R + slot, tasks + off, n, s, devs[g].dma_engines, sc, slot);
     }
     st[t] = s;
 }
@@ -135,13 +137,14 @@ __device__ __forceinline__ uint32_t orderable(float v)
 // (R - 1 rows per beam) from the new beams, so that each position costs two
 // launches: the scores and this selection (small batches, where launches
 // dominate).
-// NT (512 or 1024) threads per block; the first 512 hold the keys.
+// NT (512 or 1024) threads per block; the first 512 hold the keys.  Beam
+// b's R logits start at g GS + b R (GS = B R, or R at position 0).
 template <bool WRITE_NEXT, int NT>
 __global__ void __launch_bounds__(NT)
 beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
                    const tm_device* __restrict__ devs, const float* __restrict__ scale,
                    const float* __restrict__ logits, const BeamState* __restrict__ cur,
-                   BeamState* __restrict__ nxt, int B, int R, int pos,
+                   BeamState* __restrict__ nxt, int B, int R, int GS, int pos,
                    __nv_bfloat16* __restrict__ X)
 {
     const int g = blockIdx.x;
@@ -162,7 +165,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
         const BeamState s = cur[(size_t)g * B + b];
         float mx = -INFINITY, z = 0.0f;
         if (s.alive) {
-            const float* lg = logits + ((size_t)g * B + b) * R;
+            const float* lg = logits + (size_t)g * GS + (size_t)b * R;
             float v[TM_MAX_TASKS];
 #pragma unroll
             for (int c = 0; c < TM_MAX_TASKS; ++c) v[c] = c < cands ? lg[c] : 0.0f;
@@ -189,7 +192,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
             const int b = i / R, c = i - (i / R) * R;
             if (b < B && c < cands && cur[(size_t)g * B + b].alive) {
                 const float score = cur[(size_t)g * B + b].logp +
-                                    (logits[((size_t)g * B + b) * R + c] - lse[b]);
+                                    (logits[(size_t)g * GS + (size_t)b * R + c] - lse[b]);
                 key[q] = ((unsigned long long)orderable(score) << 32) | (0xFFFFu - (uint32_t)i);
             }
         }
@@ -264,7 +267,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
             s.h = e.h; s.k = e.k; s.d = e.d;
             s.used = p.used | (1u << j);
             s.order = p.order | ((unsigned long long)j << (4 * pos));
-            s.logp = p.logp + (logits[((size_t)g * B + pb) * R + c] - lse[pb]);
+            s.logp = p.logp + (logits[(size_t)g * GS + (size_t)pb * R + c] - lse[pb]);
             s.alive = 1;
         }
         nxt[(size_t)g * B + b] = s;
@@ -307,7 +310,7 @@ __device__ __forceinline__ void cx_desc(unsigned long long& a, unsigned long lon
 __global__ void __launch_bounds__(256)
 beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
                         const float* __restrict__ logits, const BeamState* __restrict__ cur,
-                        BeamState* __restrict__ nxt, int G, int B, int R, int pos)
+                        BeamState* __restrict__ nxt, int G, int B, int R, int GS, int pos)
 {
     const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -320,7 +323,7 @@ beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __re
         return;
     }
     const int cands = n - pos;
-    const float* lg0 = logits + (size_t)g * B * R;
+    const float* lg0 = logits + (size_t)g * GS;
     // lane b < B: beam b's log-sum-exp
     float lse = 0.0f, logp = 0.0f;
     int alive = 0;
@@ -683,6 +686,8 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
                         const float* scale, const float* logits, const void* cur, void* nxt, int G,
                         int B, int R, int pos, bf16_raw* X, cudaStream_t s)
 {
+    // the logits of position 0 are beam 0's alone (beam_init_kernel)
+    const int GS = pos == 0 ? R : B * R;
     // X == nullptr: the caller writes the next position's rows itself.
     // Large batches: 512 threads per group (more blocks per SM); small ones:
     // 1024 (more threads for the log-softmax and the next position's rows).
@@ -692,13 +697,13 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
     if (!X && B <= kWarpSelectMaxB) {
         const int64_t threads = (int64_t)G * 32;
         beam_select_warp_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            offsets, tasks, logits, c, nx, G, B, R, pos);
+            offsets, tasks, logits, c, nx, G, B, R, GS, pos);
     } else if (G > 1024) {
-        if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, x);
-        else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, nullptr);
+        if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, x);
+        else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, nullptr);
     } else {
-        if (X) beam_select_kernel<true, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, x);
-        else beam_select_kernel<false, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, pos, nullptr);
+        if (X) beam_select_kernel<true, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, x);
+        else beam_select_kernel<false, 1024><<<G, 1024, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, nullptr);
     }
     return cudaGetLastError();
 }

@@ -290,14 +290,6 @@ __device__ __forceinline__ void tail2_regs(Eng s, int4 ru, int4 rv, ChainAcc& a,
     take_pair(a, m_uv, m_vu, rank);
 }
 
-__device__ __forceinline__ void tail3_regs(Eng s, int4 r0, int4 r1, int4 r2, ChainAcc& a,
-                                           uint32_t rank)
-{
-    tail2_regs(step_c(s, r0.w, r0), r1, r2, a, rank);
-    tail2_regs(step_c(s, r1.w, r1), r0, r2, a, rank + 2);
-    tail2_regs(step_c(s, r2.w, r2), r0, r1, a, rank + 4);
-}
-
 __device__ void flush(ChainAcc& a, unsigned long long* __restrict__ acc, int g)
 {
     if (a.best == INT32_MAX) return;
@@ -580,24 +572,20 @@ __device__ __forceinline__ void tail4_pair(Eng s, const int4 (&lr)[4], const Pai
 }
 
 // The T! orders of the last round's workers 0 .. T-1 from state s, in
-// lexicographic order: ranks rank, rank + 1, ...
+// lexicographic order: ranks rank, rank + 1, ...  (T = 4 takes tail4_pair.)
 template <int T>
 __device__ __forceinline__ void tail_static(Eng s, const int4 (&lr)[T], ChainAcc& a, uint32_t rank)
 {
+    static_assert(T == 2 || T == 3, "two or three workers");
     if constexpr (T == 2) {
         const int32_t m01 = step_c(step_c(s, lr[0].w, lr[0]), lr[1].w, lr[1]).d;
         const int32_t m10 = step_c(step_c(s, lr[1].w, lr[1]), lr[0].w, lr[0]).d;
         take_pair(a, m01, m10, rank);
-    } else if constexpr (T == 3) {
+    } else {
         const int4 x[3] = {lr[0], lr[1], lr[2]};
         tail2_regs(step_c(s, x[0].w, x[0]), x[1], x[2], a, rank);
         tail2_regs(step_c(s, x[1].w, x[1]), x[0], x[2], a, rank + 2);
         tail2_regs(step_c(s, x[2].w, x[2]), x[0], x[1], a, rank + 4);
-    } else {
-        tail3_regs(step_c(s, lr[0].w, lr[0]), lr[1], lr[2], lr[3], a, rank);
-        tail3_regs(step_c(s, lr[1].w, lr[1]), lr[0], lr[2], lr[3], a, rank + 6);
-        tail3_regs(step_c(s, lr[2].w, lr[2]), lr[0], lr[1], lr[3], a, rank + 12);
-        tail3_regs(step_c(s, lr[3].w, lr[3]), lr[0], lr[1], lr[2], a, rank + 18);
     }
 }
 

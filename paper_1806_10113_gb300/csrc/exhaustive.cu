@@ -509,10 +509,14 @@ __device__ __forceinline__ void flush_final(Acc& a, const Sink& k, int g)
     }
 }
 
-// Suffix constants of the current S, in registers.
+// Suffix constants of the current S, in registers.  The extremes, the
+// bounds of gamma - beta and the 32-bit sums serve the dominance test of
+// walk mode 5 (dominated()).
 struct Sfx {
     int32_t b[24], c[24];
     int32_t alpha, bmax, cmax;
+    int32_t bmin, cmin, tmin, tmax;   // tmin / tmax: min / max over sigma of gamma - beta
+    uint32_t bsum, csum;              // sums of beta and gamma mod 2^32
     uint32_t one;   // 1, read from a kernel parameter (see leaves)
 };
 
@@ -554,15 +558,71 @@ __device__ __forceinline__ int first_completion(int32_t k, int32_t d, int32_t v,
 // FMA-pipe sum; 2 every level as a loop (ALU sum); 3 as 1, and each order's
 // addition k + beta as a multiply-add by S.one, so that it too issues on the
 // FMA pipe beside the ALU pipe's maxima and minima; 4 as 3, compiled for four
-// resident blocks per SM (at most 128 registers) instead of three.
+// resident blocks per SM (at most 128 registers) instead of three; 5 as 3,
+// with the dominance test (dominated()) before each prefix's 24 orders.
 __host__ __device__ constexpr bool mode_straight(int mode) { return mode != 2; }
 __host__ __device__ constexpr bool mode_fma_add(int mode) { return mode >= 3; }
 __host__ __device__ constexpr int mode_min_blocks(int mode) { return mode == 4 ? 4 : TM_ENUM_MIN_BLOCKS; }
+__host__ __device__ constexpr bool mode_dominance(int mode) { return mode == 5; }
 
-template <bool SUM32, int MODE>
+// One engine's path ends all 24 orders of S after a prefix with engine
+// times (k, d) in three cases, each with a closed form for the minimum, the
+// maximum and the sum of the 24 makespans max(c0, gamma_j, k + beta_j),
+// c0 = d + alpha:
+//   the DtH engine's: c0 >= every gamma_j and every k + beta_j, i.e.
+//     c0 >= max(cmax, k + bmax): all 24 equal c0;
+//   the K engine's: k + beta_j >= gamma_j for every j (k >= tmax) and
+//     k + bmin >= c0: makespan j is k + beta_j;
+//   the HtD engine's: gamma_j >= k + beta_j for every j (k <= tmin) and
+//     cmin >= c0: makespan j is gamma_j.
+// The sums are exact in 32 bits where the group's 24-order sums fit (SUM32);
+// other groups take the first case only, with a 64-bit sum.
+struct Dom {
+    bool ok;
+    int32_t mn, mx;
+    unsigned long long sum;
+};
+
+template <bool SUM32>
+__device__ __forceinline__ Dom dominated(int32_t k, int32_t d, const Sfx& S)
+{
+    const int32_t c0 = d + S.alpha, kmin = k + S.bmin, kmax = k + S.bmax;
+    const bool all_d = c0 >= max(kmax, S.cmax);
+    const bool all_k = SUM32 && k >= S.tmax && c0 <= kmin;
+    const bool all_c = SUM32 && k <= S.tmin && c0 <= S.cmin;
+    Dom r;
+    r.ok = all_d || all_k || all_c;
+    r.mn = all_d ? c0 : all_k ? kmin : S.cmin;
+    r.mx = all_d ? c0 : all_k ? kmax : S.cmax;
+    if (SUM32)
+        r.sum = all_d ? 24u * (uint32_t)c0 : all_k ? 24u * (uint32_t)k + S.bsum : S.csum;
+    else
+        r.sum = 24ull * (uint32_t)c0;
+    return r;
+}
+
+// The walk's bookkeeping for one prefix whose 24 orders reach pmin / pmax.
+__device__ __forceinline__ void note_prefix(int32_t pmin, int32_t pmax, Acc& a)
+{
+    if (pmin < a.imin) { a.imin = pmin; a.imin_at = a.walked; }
+    if (pmax > a.imax) { a.imax = pmax; a.imax_at = a.walked; }
+    a.walked += 1;
+}
+
+// CHECK (walk mode 5): take the closed form when dominated() holds on every
+// active lane of the warp, so that the warp's lanes stay on one path.
+template <bool SUM32, int MODE, bool CHECK = mode_dominance(MODE)>
 __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& a)
 {
     constexpr bool FMA_SUM = mode_straight(MODE);
+    if constexpr (CHECK) {
+        const Dom q = dominated<SUM32>(k, d, S);
+        if (__all_sync(__activemask(), q.ok)) {
+            a.sum += q.sum;
+            note_prefix(q.mn, q.mx, a);
+            return;
+        }
+    }
     const int32_t c0 = d + S.alpha;
     int32_t m[24];
     if constexpr (mode_fma_add(MODE)) {
@@ -597,9 +657,7 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
         for (int i = 0; i < 12; ++i) a.sum += (uint32_t)m[2 * i] + (uint32_t)m[2 * i + 1];
     }
     const int32_t pmax = max3i(c0, k + S.bmax, S.cmax);
-    if (pmin < a.imin) { a.imin = pmin; a.imin_at = a.walked; }
-    if (pmax > a.imax) { a.imax = pmax; a.imax_at = a.walked; }
-    a.walked += 1;
+    note_prefix(pmin, pmax, a);
 }
 
 // The last two prefix positions, holding tasks x < y: orders (x, y), (y, x).
@@ -630,6 +688,55 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
         leaves<SUM32, MODE>(s1.k, s1.d, S, a);
     } else if constexpr (D == 2) {
         last_two<SUM32, MODE>(st, tbl[nib_get(rem, 0)], tbl[nib_get(rem, 1)], S, a);
+    } else if constexpr (D == 3 && mode_dominance(MODE)) {
+        // as below, with one dominance vote for all six prefixes: either all
+        // six take the closed form on every lane, or all six the full leaves
+        const int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)], t2 = tbl[nib_get(rem, 2)];
+        const Eng s0 = step(st, t0.x, t0.y, t0.z), s1 = step(st, t1.x, t1.y, t1.z),
+                  s2 = step(st, t2.x, t2.y, t2.z);
+        Eng e[6];
+        e[0] = step(step(s0, t1.x, t1.y, t1.z), t2.x, t2.y, t2.z);
+        e[1] = step(step(s0, t2.x, t2.y, t2.z), t1.x, t1.y, t1.z);
+        e[2] = step(step(s1, t0.x, t0.y, t0.z), t2.x, t2.y, t2.z);
+        e[3] = step(step(s1, t2.x, t2.y, t2.z), t0.x, t0.y, t0.z);
+        e[4] = step(step(s2, t0.x, t0.y, t0.z), t1.x, t1.y, t1.z);
+        e[5] = step(step(s2, t1.x, t1.y, t1.z), t0.x, t0.y, t0.z);
+        // the vote carries one bit; the closed forms are formed after it,
+        // so that the full path does not hold them
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) ok = ok && dominated<SUM32>(e[i].k, e[i].d, S).ok;
+        if (__all_sync(__activemask(), ok)) {
+            // the six prefixes' minima, maxima and sums by shallow trees;
+            // the first prefix reaching a new item minimum (maximum) is
+            // only looked for when there is one, which is rare
+            Dom q[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) q[i] = dominated<SUM32>(e[i].k, e[i].d, S);
+            a.sum += ((q[0].sum + q[1].sum) + (q[2].sum + q[3].sum)) + (q[4].sum + q[5].sum);
+            const int32_t mn = min(min3i(q[0].mn, q[1].mn, q[2].mn), min3i(q[3].mn, q[4].mn, q[5].mn));
+            const int32_t mx = max(max3i(q[0].mx, q[1].mx, q[2].mx), max3i(q[3].mx, q[4].mx, q[5].mx));
+            if (mn < a.imin) {
+                int at = 5;
+#pragma unroll
+                for (int i = 4; i >= 0; --i)
+                    if (q[i].mn == mn) at = i;
+                a.imin = mn;
+                a.imin_at = a.walked + (uint32_t)at;
+            }
+            if (mx > a.imax) {
+                int at = 5;
+#pragma unroll
+                for (int i = 4; i >= 0; --i)
+                    if (q[i].mx == mx) at = i;
+                a.imax = mx;
+                a.imax_at = a.walked + (uint32_t)at;
+            }
+            a.walked += 6;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) leaves<SUM32, MODE, false>(e[i].k, e[i].d, S, a);
+        }
     } else if constexpr (D == 3 && mode_straight(MODE)) {
         // the three tasks' rows loaded once; their six orders in
         // lexicographic order (the list is ascending)
@@ -808,6 +915,27 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
             }
             S.bmax = max3i(max3i(bm[0], bm[1], bm[2]), max3i(bm[3], bm[4], bm[5]), max(bm[6], bm[7]));
             S.cmax = max3i(max3i(cm[0], cm[1], cm[2]), max3i(cm[3], cm[4], cm[5]), max(cm[6], cm[7]));
+            if constexpr (mode_dominance(MODE)) {
+                int32_t bn[8], cn[8], tn[8], tx[8];
+                uint32_t bs = 0u, cs = 0u;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    bn[q] = min3i(S.b[3 * q], S.b[3 * q + 1], S.b[3 * q + 2]);
+                    cn[q] = min3i(S.c[3 * q], S.c[3 * q + 1], S.c[3 * q + 2]);
+                    const int32_t u0 = S.c[3 * q] - S.b[3 * q], u1 = S.c[3 * q + 1] - S.b[3 * q + 1],
+                                  u2 = S.c[3 * q + 2] - S.b[3 * q + 2];
+                    tn[q] = min3i(u0, u1, u2);
+                    tx[q] = max3i(u0, u1, u2);
+                    bs += (uint32_t)S.b[3 * q] + (uint32_t)S.b[3 * q + 1] + (uint32_t)S.b[3 * q + 2];
+                    cs += (uint32_t)S.c[3 * q] + (uint32_t)S.c[3 * q + 1] + (uint32_t)S.c[3 * q + 2];
+                }
+                S.bmin = min3i(min3i(bn[0], bn[1], bn[2]), min3i(bn[3], bn[4], bn[5]), min(bn[6], bn[7]));
+                S.cmin = min3i(min3i(cn[0], cn[1], cn[2]), min3i(cn[3], cn[4], cn[5]), min(cn[6], cn[7]));
+                S.tmin = min3i(min3i(tn[0], tn[1], tn[2]), min3i(tn[3], tn[4], tn[5]), min(tn[6], tn[7]));
+                S.tmax = max3i(max3i(tx[0], tx[1], tx[2]), max3i(tx[3], tx[4], tx[5]), max(tx[6], tx[7]));
+                S.bsum = bs;
+                S.csum = cs;
+            }
             sc = 0;
             for (int e = 0, cnt = 0; e < gi.n; ++e)
                 if (!((mask >> e) & 1u)) sc |= (uint64_t)e << (4 * cnt++);
@@ -913,6 +1041,7 @@ cudaError_t enum_occupancy_mode(int mode, int* per_sm)
     case 2: return enum_occupancy<PDMAX, 2>(per_sm);
     case 3: return enum_occupancy<PDMAX, 3>(per_sm);
     case 4: return enum_occupancy<PDMAX, 4>(per_sm);
+    case 5: return enum_occupancy<PDMAX, 5>(per_sm);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -925,6 +1054,7 @@ cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, cudaStream_t strea
     case 2: return launch_enum<PDMAX, 2>(p, sink, stream);
     case 3: return launch_enum<PDMAX, 3>(p, sink, stream);
     case 4: return launch_enum<PDMAX, 4>(p, sink, stream);
+    case 5: return launch_enum<PDMAX, 5>(p, sink, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -937,7 +1067,8 @@ cudaError_t preload_modes()
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 1>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 2>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 3>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 4>);
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 4>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 5>);
 }
 
 int resident_threads(int pdmax, int mode, int device, int blocks_per_sm)

@@ -104,7 +104,8 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
         const bool fused = (int64_t)gc * B * nm <= kBeamFusedRows;
         for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
             const int R = nm - pos;
-            const int64_t rows = (int64_t)gc * B * R;
+            // position 0: beam 0's rows alone (the other beams start dead)
+            const int64_t rows = (int64_t)gc * (pos == 0 ? 1 : B) * R;
             if (!fused && pos > 0)
                 e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R,
                                   pos, sc.bx.as<bf16_raw>(), s);

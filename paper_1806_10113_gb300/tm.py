@@ -314,7 +314,8 @@ class Tuning(ctypes.Structure):
     """tm_tuning: pdmax (3..5), fuse_finalize (1 fused, 2 separate), blocks_per_sm,
     item_cost, chunks_per_thread (1 static split, 2..64 dynamic), unroll (1
     straight-line walk level, 2 loop, 3 straight-line with the per-order
-    additions on the FMA pipe, 4 as 3 at four blocks per SM); 0 = default."""
+    additions on the FMA pipe, 4 as 3 at four blocks per SM, 5 as 3 with the closed
+    form for prefixes whose completions one engine's path ends); 0 = default."""
     _fields_ = [("pdmax", ctypes.c_int32), ("fuse_finalize", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("item_cost", ctypes.c_int32),
                 ("chunks_per_thread", ctypes.c_int32), ("unroll", ctypes.c_int32)]

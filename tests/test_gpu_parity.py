@@ -152,14 +152,15 @@ def check_reported_orders(tm, b, stats, samples=64, seed=0):
             assert ms != s["worst"] or r >= s["worst_rank"]
 
 
-def scheduled_as_benched(tm, b):
+def scheduled_as_benched(tm, b, tuning=None):
     """The whole scheduling pass (exhaustive search + heuristic) the way the
-    benchmark runs it: tuning picked by the autotuner on this batch, one
-    tm_schedule_batch_dev call on device buffers."""
+    benchmark runs it: tuning picked by the autotuner on this batch (or the
+    one given), one tm_schedule_batch_dev call on device buffers."""
     import torch
     from paper_1806_10113_gb300 import autotune
     dev = torch.device("cuda")
-    tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
+    if tuning is None:
+        tuning = autotune.tune(b.tasks, b.offsets, b.dma, cache_path=None, reps=10)
     plan = tm.Plan(b.offsets, **tuning)
     d_tasks = torch.from_numpy(b.tasks).to(dev)
     d_dma = torch.from_numpy(b.dma).to(dev)
@@ -189,6 +190,32 @@ def test_exhaustive_full_size_sixty_four_groups(tm):
     assert (orders == ref_orders).all() and (hms == ref_ms).all()
     # the paper's heuristic can never beat the exhaustive best
     assert all(hms[g] >= stats[g]["best"] for g in range(b.G))
+
+
+@pytest.mark.parametrize("workload,tuning", [
+    ("dkdt64x10", dict(pdmax=5, fuse_finalize=2, unroll=5, item_cost=65536, chunks_per_thread=1)),
+    ("dkdt64x10", dict(pdmax=4, unroll=5, chunks_per_thread=3)),
+    ("ragged2048", dict(pdmax=5, fuse_finalize=2, blocks_per_sm=3, unroll=5, chunks_per_thread=3)),
+    ("ties", dict(pdmax=5, unroll=5)),
+])
+def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
+    """Walk mode 5 (closed forms for prefixes whose completions one engine's
+    path ends) against the oracle's full enumeration, whatever the tuner
+    picks elsewhere: the benchmark's 64 x 10 workload (all 128 x 10! orders),
+    2048 ragged groups, and tie-heavy groups (durations 0..3, where every
+    closed form meets equal makespans and the first rank decides)."""
+    if workload == "dkdt64x10":
+        b = inputs.dk_dt_groups(groups=64, n=10, seed=1)
+    elif workload == "ragged2048":
+        b = inputs.ragged_mixed(groups=2048, seed=4)
+    else:
+        b = inputs.random_groups(26, [9, 10, 8, 9, 7, 10], lo=0, hi=3)
+    stats, orders, hms, _ = scheduled_as_benched(tm, b, tuning)
+    ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(stats[g], ref[g], (g, tuning))
+    ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
+    assert (orders == ref_orders).all() and (hms == ref_ms).all()
 
 
 def oracle_full_by_prefixes(b, g):
@@ -397,7 +424,10 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
                                     dict(pdmax=5, unroll=3), dict(pdmax=3, unroll=3,
                                                                    chunks_per_thread=6),
                                     dict(pdmax=5, unroll=4), dict(pdmax=3, unroll=4),
-                                    dict(pdmax=4, unroll=4, chunks_per_thread=3)])
+                                    dict(pdmax=4, unroll=4, chunks_per_thread=3),
+                                    dict(pdmax=5, unroll=5), dict(pdmax=3, unroll=5),
+                                    dict(pdmax=4, unroll=5, chunks_per_thread=3),
+                                    dict(pdmax=5, unroll=5, item_cost=1)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
