@@ -102,6 +102,25 @@ def method_ops_per_order(n: int) -> float:
     return 5 + per_prefix / 24 + 960 / (math.factorial(P) * 24)
 
 
+def dominance_ops_per_order(n: int, full: float) -> float:
+    """Integer operations per order of walk mode 5 (tm_tuning.unroll 5), where
+    a fraction `full` of the prefixes had their 24 orders evaluated one by one
+    (tm_plan_walk_counts) and the others took the closed forms.
+
+    Per prefix, the dominance test: k + bmin, d + alpha, k + bmax, the
+    maximum of k + bmax and cmax, six compares, two ors (12).  A dominated
+    prefix then takes two selects for its minimum, two for its maximum, the
+    sum 24 c0 or 24 k + sum(beta) (2) and a select between those and
+    sum(gamma) (2), the item minimum and maximum (2) and the 64-bit sum (2):
+    12.  Any other prefix costs what method_ops_per_order counts (the 24
+    orders at 5 and the prefix's 6, of which d + alpha and k + bmax are the
+    test's: 124).  The walk and the suffix tables as in method_ops_per_order."""
+    P = n - 4
+    nodes = sum(math.factorial(P) // math.factorial(P - i) for i in range(1, P + 1))
+    per_prefix = 5 * nodes / math.factorial(P) + 12 + (1.0 - full) * 12 + full * 124
+    return per_prefix / 24 + 960 / (math.factorial(P) * 24)
+
+
 ALG_OPS_PER_ORDER = method_ops_per_order(N_TASKS)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
@@ -119,10 +138,25 @@ def workload(rank: int = 0, name: str = "dkdt64x10"):
     return inputs.dk_dt_groups(groups=GROUPS, n=N_TASKS, seed=SEED + 1000 * rank)
 
 
-def ops_per_order(b) -> float:
-    """method_ops_per_order weighted by each group's orders (groups n >= 4)."""
-    w = [(math.factorial(int(n)), method_ops_per_order(int(n))) for n in b.sizes() if n >= 4]
+def ops_per_order(b, full=None) -> float:
+    """method_ops_per_order weighted by each group's orders (groups n >= 4);
+    with `full` (walk mode 5: the fraction of prefixes evaluated order by
+    order, over the whole batch), dominance_ops_per_order instead."""
+    f = (lambda n: method_ops_per_order(n)) if full is None else \
+        (lambda n: dominance_ops_per_order(n, full))
+    w = [(math.factorial(int(n)), f(int(n))) for n in b.sizes() if n >= 4]
     return sum(a * o for a, o in w) / max(1, sum(a for a, _ in w))
+
+
+def walk_basis(plan, tuning) -> tuple:
+    """(fraction of prefixes evaluated order by order in the plan's last run,
+    or None outside walk mode 5; a one-line statement of the count's basis)."""
+    if int(tuning.get("unroll", 0)) != 5:
+        return None, "max-plus suffix decomposition (see method_ops_per_order)"
+    pre, full = plan.walk_counts()
+    f = full / pre if pre else 1.0
+    return f, (f"walk mode 5: {full} of {pre} prefixes ({100 * f:.1f}%) evaluated order by "
+               "order, the rest by closed forms (see dominance_ops_per_order)")
 
 
 def orders_per_step(b) -> int:
@@ -501,10 +535,11 @@ def n12_leg(args, log) -> dict:
     torch.cuda.synchronize()
     if (d_status.cpu().numpy() != 0).any():
         raise RuntimeError("12-task workload: device status errors")
+    full, basis = walk_basis(plan, tuning)
     plan.close()
     step_s = statistics.mean(ms) / 1000.0
     enum_s = statistics.mean(a.elapsed_time(c) for a, c in ek) / 1000.0
-    ops = ops_per_order(b)
+    ops = ops_per_order(b, full)
     achieved = ops * n_orders / enum_s / 1e12
     log(f"n12: {n_orders / step_s:.3e} orders/s")
     return {"workload": WORKLOADS["dkdt32x12"], "value": n_orders / step_s, "unit": UNIT,
@@ -515,7 +550,7 @@ def n12_leg(args, log) -> dict:
                          "unit": "Tops/s (int32)", "frac": achieved / INT32_PEAK_TOPS,
                          "kernel": "enum_kernel (exhaustive enumeration)",
                          "kernel_ms": 1000 * enum_s, "ops_per_order": round(ops, 3),
-                         "traffic": None},
+                         "ops_basis": basis, "traffic": None},
             "clocks": clocks}
 
 
@@ -769,11 +804,13 @@ def run_tm(args):
 
     ws_total = ws
     result = None
+    full, basis = walk_basis(plan, tuning)
     if rank == 0:
         enum_avg_s = statistics.mean(enum_ms) / 1000.0
-        ops_order = ops_per_order(b)
+        ops_order = ops_per_order(b, full)
         alg_ops = ops_order * n_orders
         achieved = alg_ops / enum_avg_s / 1e12
+        maxplus_achieved = ops_per_order(b) * n_orders / enum_avg_s / 1e12
         stepwise_achieved = STEPWISE_OPS_PER_ORDER * n_orders / enum_avg_s / 1e12
         traffic = profiled_traffic()
         rates = tm.tm_measure_int32_rates()
@@ -798,7 +835,9 @@ def run_tm(args):
                          "kernel": "enum_kernel (exhaustive enumeration)",
                          "kernel_ms": 1000 * enum_avg_s,
                          "ops_per_order": round(ops_order, 3),
-                         "ops_basis": "max-plus suffix decomposition (see method_ops_per_order)",
+                         "ops_basis": basis,
+                         "maxplus_ops_per_order": round(ops_per_order(b), 3),
+                         "maxplus_frac": maxplus_achieved / INT32_PEAK_TOPS,
                          "stepwise_ops_per_order": round(STEPWISE_OPS_PER_ORDER, 3),
                          "stepwise_frac": stepwise_achieved / INT32_PEAK_TOPS,
                          "peak_basis": "152 SMs x 128 int32 lanes/clk x 2070 MHz (derived)",

@@ -260,6 +260,20 @@ int tm_plan_launches(const tm_plan* plan);
  * events; the caller keeps them alive while the hook is set. */
 int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
 
+/* Work counts of the plan's last run, for measuring it (the exhaustive
+ * search's decomposition: each order is a prefix of n - 4 tasks and one of
+ * the 24 orders of the other four; Sec. 1's brute force over every order).
+ * *prefixes: the prefixes one run walks, n! / 24 per group of n >= 4 tasks.
+ * *full: how many of them had their 24 completions evaluated one by one;
+ * under walk mode 5 (tm_tuning.unroll) the others took the closed form of
+ * their minimum, maximum and sum; every other mode evaluates all of them,
+ * and *full = *prefixes without a device read.  Mode 5 reads a counter in
+ * the plan's device memory (a synchronous copy): call it once the run has
+ * finished (its stream synchronized).  Returns TM_OK, TM_EINVAL (a NULL
+ * argument) or TM_ECUDA. */
+int tm_plan_walk_counts(const tm_plan* plan, unsigned long long* prefixes,
+                        unsigned long long* full);
+
 /* ---- exhaustive search without any allocation ---------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -420,6 +420,20 @@ int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after)
     return TM_OK;
 }
 
+int tm_plan_walk_counts(const tm_plan* plan, unsigned long long* prefixes,
+                        unsigned long long* full)
+{
+    if (!plan || !prefixes || !full) return TM_EINVAL;
+    *prefixes = plan->p.total_prefixes;
+    *full = plan->p.total_prefixes;
+    if (plan->p.unroll != 5 || !plan->p.d_full || plan->p.total_items == 0) return TM_OK;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, plan->p.d_full, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TM_ECUDA;
+    *full = v;
+    return TM_OK;
+}
+
 int tm_exhaustive_batch_dev(const tm_plan* plan, const tm_task* d_tasks, const tm_device* d_devs,
                             tm_stats* d_stats, int32_t* d_status, void* stream)
 {

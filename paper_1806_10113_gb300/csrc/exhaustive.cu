@@ -255,6 +255,7 @@ struct PrepArgs {
     int32_t* orders;              // heuristic outputs; null: no heuristic
     int32_t* makespans;
     uint32_t* next;               // dynamic chunk counter to zero, or null
+    unsigned long long* full;     // Plan::d_full, to zero (or null)
 };
 
 // Validation, GroupInfo, padded task table (and n <= 3 groups finished
@@ -383,7 +384,10 @@ __global__ void __launch_bounds__(kPrepMaxThreads) prep_kernel(PrepArgs a)
         return;
     }
     const int w = blockIdx.x;
-    if (a.next && w == 0 && tid == 0) *a.next = 0;
+    if (w == 0 && tid == 0) {
+        if (a.next) *a.next = 0;
+        if (a.full) *a.full = 0;
+    }
     const GroupPlan* __restrict__ gp = a.gp;
     const int off = gp[w].off, uoff = gp[w].uoff, user = gp[w].group;
     const int n = gp[w + 1].off - off;     // 1..TM_MAX_EXHAUSTIVE: the plan checked it
@@ -407,6 +411,9 @@ struct Acc {
     // keep the lowest-rank occurrence.
     int32_t imin, imax;
     uint32_t imin_at, imax_at, walked;
+    // Walk mode 5: prefixes of the thread's whole range evaluated order by
+    // order (not reset per group).
+    uint32_t full;
     __device__ __forceinline__ void reset()
     {
         best = INT32_MAX;
@@ -443,6 +450,7 @@ struct Sink {
     const uint32_t* target;
     uint32_t* done;
     uint32_t one;   // always 1 (the leaves' multiply-add sum)
+    unsigned long long* full;   // Plan::d_full (walk mode 5), or null
 };
 
 __device__ __forceinline__ void flush(const Acc& a, unsigned long long* acc, int g)
@@ -622,6 +630,7 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
             note_prefix(q.mn, q.mx, a);
             return;
         }
+        a.full += 1;
     }
     const int32_t c0 = d + S.alpha;
     int32_t m[24];
@@ -734,6 +743,7 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
             }
             a.walked += 6;
         } else {
+            a.full += 6;
 #pragma unroll
             for (int i = 0; i < 6; ++i) leaves<SUM32, MODE, false>(e[i].k, e[i].d, S, a);
         }
@@ -859,6 +869,7 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
     int g = search_group(G, i, [&](int j) { return (uint64_t)gp[j].item_base; });
     Acc a;
     a.reset();
+    a.full = 0;
     Sfx S;
     S.one = sink.one;
     GroupInfo gi;
@@ -960,6 +971,14 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
         if (a.imax > a.worst || (tie_w && low < a.worst_rank)) {
             uint32_t r = item_rank(a.imax_at, a.imax, hd, sc, f, pd, gi.n, gi.dinit, gt, tab);
             if (a.imax > a.worst || r < a.worst_rank) { a.worst = a.imax; a.worst_rank = r; }
+        }
+    }
+    if constexpr (mode_dominance(MODE)) {
+        if (sink.full) {   // one atomic per warp
+            const unsigned live = __activemask();
+            const uint32_t tot = __reduce_add_sync(live, a.full);
+            if ((int)(threadIdx.x & 31) == __ffs(live) - 1 && tot != 0)
+                atomicAdd(sink.full, (unsigned long long)tot);
         }
     }
     flush_final(a, sink, g);
@@ -1111,6 +1130,14 @@ void exhaustive_partition(Plan& p, int device, int blocks_per_sm)
     }
     if (p.chunks_per_thread > 1) {
         p.chunk = std::max<uint64_t>(1, p.leaves_per_thread / (uint64_t)p.chunks_per_thread);
+        if (p.uniform_n >= 4 && p.total_items > 0) {
+            // every item costs the same: chunks of whole items, so that each
+            // lane of a warp that takes 32 chunks walks the same number
+            const uint64_t c = p.total_leaves / p.total_items;
+            const uint64_t per_thread = std::max<uint64_t>(1, p.total_items / threads);
+            p.chunk = c * std::max<uint64_t>(1, (per_thread + p.chunks_per_thread / 2) /
+                                                    (uint64_t)p.chunks_per_thread);
+        }
         const uint64_t nch = (p.total_leaves + p.chunk - 1) / p.chunk;
         if (nch >= 0xFFFFFF00ull) {           // counter range: fall back to the static split
             p.chunks_per_thread = 1;
@@ -1156,6 +1183,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     pa.orders = d_orders;
     pa.makespans = d_makespans;
     pa.next = (p.chunks_per_thread > 1 && p.total_items > 0) ? p.d_next : nullptr;
+    pa.full = p.d_full;
     // a block per group: 512 threads when the batch's groups have many
     // (subset, order) pairs (n >= 9: >= 3,024), else 128
     const int prep_threads = p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128;
@@ -1169,7 +1197,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
-        Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done, 1u};
+        Sink sink{p.d_acc, p.d_info, p.d_tbl, d_stats, d_status, p.d_target, p.d_done, 1u, p.d_full};
         // Under stream capture, an external record becomes an event-record
         // node of the graph (a plain record would only order the capture).
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -90,6 +90,7 @@ struct Plan {
     uint32_t item_cost = 256;     // per-item overhead, in orders
     uint32_t total_units = 0;     // prep / suffix-table threads
     uint32_t total_subs = 0;      // suffix-table entries
+    uint64_t total_prefixes = 0;  // prefixes walked per run: n! / 24 per group of n >= 4
     int uniform_n = 0;            // the group size when every group has it, else 0
     uint32_t threads = 0;         // enumeration threads
     uint64_t leaves_per_thread = 0;
@@ -122,6 +123,10 @@ struct Plan {
     uint32_t* d_target = nullptr;         // [G]
     uint32_t* d_done = nullptr;           // [kDoneStride G]
     uint32_t* d_next = nullptr;           // dynamic chunk counter
+    // Prefixes of the last run whose 24 completions were evaluated order by
+    // order (walk mode 5 counts them; the others evaluate every prefix so);
+    // zeroed by the prep kernel; in d_next's 256-byte piece.
+    unsigned long long* d_full = nullptr;
     cudaEvent_t ev_before = nullptr;      // optional timing hook
     cudaEvent_t ev_after = nullptr;
 };
@@ -151,7 +156,7 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
         at += c;
     }
     for (int g = 0; g < G; ++g) gp[start[offsets[g + 1] - offsets[g]]++].group = g;
-    uint64_t cost = 0, items = 0, units = 0, subs = 0;
+    uint64_t cost = 0, items = 0, units = 0, subs = 0, prefixes = 0;
     int32_t toff = 0;
     for (int w = 0; w < G; ++w) {
         const int g = gp[w].group;
@@ -171,6 +176,7 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
             uint64_t heads = factorial_u64(P) / factorial_u64(pd);
             items += (uint64_t)c4 * heads;
             cost += (uint64_t)c4 * heads * (24ull * factorial_u64(pd) + item_cost);
+            prefixes += factorial_u64(n) / 24;
         }
         if (items >= 0xFFFFFFFFull || units >= 0xFFFFFFFFull) return TM_ETOOBIG;
     }
@@ -189,6 +195,7 @@ inline int plan_decompose(const int32_t* offsets, int G, int pdmax, uint32_t ite
     totals->total_leaves = cost;
     totals->total_units = (uint32_t)units;
     totals->total_subs = (uint32_t)subs;
+    totals->total_prefixes = prefixes;
     totals->uniform_n = 0;
     for (int nn = 1; nn <= TM_MAX_EXHAUSTIVE && G > 0; ++nn)
         if (start[nn] - (nn < TM_MAX_EXHAUSTIVE ? start[nn + 1] : 0u) == (uint32_t)G) totals->uniform_n = nn;
@@ -214,7 +221,8 @@ inline size_t plan_carve(Plan& p, unsigned char* base)
     p.d_sub = reinterpret_cast<SuffixTab*>(take(S1 * sizeof(SuffixTab)));
     p.d_acc = reinterpret_cast<unsigned long long*>(
         take(kAccStride * G1 * sizeof(unsigned long long)));
-    p.d_next = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t)));
+    p.d_next = reinterpret_cast<uint32_t*>(take(2 * sizeof(unsigned long long)));
+    p.d_full = base ? reinterpret_cast<unsigned long long*>(p.d_next) + 1 : nullptr;
     return off;
 }
 

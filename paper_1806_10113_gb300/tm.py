@@ -74,6 +74,8 @@ _SIGS = {
     "tm_plan_destroy": [_vp],
     "tm_plan_launches": [_vp],
     "tm_plan_set_timing": [_vp, _vp, _vp],
+    "tm_plan_walk_counts": [_vp, ctypes.POINTER(ctypes.c_ulonglong),
+                            ctypes.POINTER(ctypes.c_ulonglong)],
     "tm_plan_capture": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tm_plan_graph_launch": [_vp, _vp],
     "tm_plan_graph_set_timing": [_vp, _vp, _vp],
@@ -349,6 +351,15 @@ class Plan:
 
     def launches(self) -> int:
         return int(lib().tm_plan_launches(self._h))
+
+    def walk_counts(self):
+        """(prefixes walked per run, prefixes of the last run whose 24
+        completions were evaluated one by one): tm_plan_walk_counts; call it
+        after the run has finished."""
+        pre, full = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+        _check(lib().tm_plan_walk_counts(self._h, ctypes.byref(pre), ctypes.byref(full)),
+               "tm_plan_walk_counts")
+        return int(pre.value), int(full.value)
 
     def set_timing(self, event_before=None, event_after=None):
         """Records two CUDA events (e.g. torch.cuda.Event(enable_timing=True))

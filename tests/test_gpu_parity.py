@@ -218,6 +218,36 @@ def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
     assert (orders == ref_orders).all() and (hms == ref_ms).all()
 
 
+def test_walk_counts(tm):
+    """tm_plan_walk_counts: n!/24 prefixes per group; every prefix evaluated
+    order by order outside walk mode 5; under it, some (the benchmark's
+    dominant-transfer groups under two DMA engines mix the engines' paths)
+    but not all; and none where the DtH engine's path ends every order."""
+    import torch
+    dev = torch.device("cuda")
+
+    def run(b, unroll):
+        plan = tm.Plan(b.offsets, pdmax=5, unroll=unroll)
+        d_stats = torch.zeros(b.G * tm.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        d_status = torch.full((b.G,), 9, dtype=torch.int32, device=dev)
+        tm.tm_exhaustive_batch_dev(plan, torch.from_numpy(b.tasks).to(dev),
+                                   torch.from_numpy(b.dma).to(dev), d_stats, d_status)
+        torch.cuda.synchronize()
+        assert (d_status.cpu().numpy() == 0).all()
+        counts = plan.walk_counts()
+        plan.close()
+        return counts
+
+    b = inputs.dk_dt_groups(groups=64, n=10, seed=1)
+    pre3, full3 = run(b, 3)
+    pre5, full5 = run(b, 5)
+    assert pre3 == pre5 == 128 * math.factorial(10) // 24 and full3 == pre3
+    assert 0 < full5 < pre5
+    dth = inputs.make_batch([[[1, 1, 1_000_000]] * 8] * 6, [2, 1] * 3)
+    pre, full = run(dth, 5)
+    assert pre == 6 * math.factorial(8) // 24 and full == 0
+
+
 def oracle_full_by_prefixes(b, g):
     """Oracle statistics of group g from its two-task-prefix subtrees (all n!
     orders, spread evenly over the host cores)."""
