@@ -175,7 +175,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Barrier of one warpgroup (named barrier 1 + g, 128 threads), with a vote.
@@ -211,6 +210,16 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
     return d;
 }
 
+// tcgen05.wait::ld tied to the registers of the loads it waits for, so that
+// no use of them is scheduled before it.
+__device__ __forceinline__ void tc_wait_ld32(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -237,6 +246,11 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_base, uint
 __device__ __forceinline__ void tc_ld1(uint32_t taddr, uint32_t& r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_ld1(uint32_t& r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r) : : "memory");
 }
 
 // The three bfloat16 parts of a float32 value (hi + mid + lo == v exactly).
@@ -372,11 +386,15 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
             phase ^= 1u;
             if (!ok) break;
             tc_fence_after();
-#pragma unroll 1
+            // 32 columns at a time, the next chunk's TMEM load in flight
+            // while this one is converted and stored
+            uint32_t rb[2][32];
+            tc_ld32(t_row, rb[0]);
+            tc_wait_ld32(rb[0]);
+#pragma unroll
             for (int c = 0; c < kH / 32; ++c) {
-                uint32_t r[32];
-                tc_ld32(t_row + (uint32_t)(32 * c), r);
-                tc_wait_ld();
+                uint32_t (&r)[32] = rb[c & 1];
+                if (c + 1 < kH / 32) tc_ld32(t_row + (uint32_t)(32 * (c + 1)), rb[(c + 1) & 1]);
                 {
                     uint32_t packed[16];
 #pragma unroll
@@ -398,6 +416,7 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
                                                 packed[4 * q + 2], packed[4 * q + 3]);
                     }
                 }
+                if (c + 1 < kH / 32) tc_wait_ld32(rb[(c + 1) & 1]);
             }
             // the next layer's MMAs read the tile this layer just wrote, and
             // overwrite the accumulator this layer just read
@@ -419,7 +438,7 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
         tc_fence_after();
         uint32_t lv;
         tc_ld1(t_row, lv);
-        tc_wait_ld();
+        tc_wait_ld1(lv);
         if (r0 + row < M) logits[r0 + row] = __uint_as_float(lv);
     }
     if (!ok) {
