@@ -197,19 +197,27 @@ def test_exhaustive_full_size_sixty_four_groups(tm):
     ("dkdt64x10", dict(pdmax=4, unroll=5, chunks_per_thread=3)),
     ("ragged2048", dict(pdmax=5, fuse_finalize=2, blocks_per_sm=3, unroll=5, chunks_per_thread=3)),
     ("ties", dict(pdmax=5, unroll=5)),
+    ("ties_uniform", dict(pdmax=5, fuse_finalize=2, unroll=5)),
+    ("big_uniform", dict(pdmax=4, fuse_finalize=2, unroll=5)),
 ])
 def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
     """Walk mode 5 (closed forms for prefixes whose completions one engine's
     path ends) against the oracle's full enumeration, whatever the tuner
     picks elsewhere: the benchmark's 64 x 10 workload (all 128 x 10! orders),
     2048 ragged groups, and tie-heavy groups (durations 0..3, where every
-    closed form meets equal makespans and the first rank decides)."""
+    closed form meets equal makespans and the first rank decides), also as
+    batches of one group size (the static split of whole warps), one of them
+    with 24-order sums beyond 32 bits (the DtH engine's case only)."""
     if workload == "dkdt64x10":
         b = inputs.dk_dt_groups(groups=64, n=10, seed=1)
     elif workload == "ragged2048":
         b = inputs.ragged_mixed(groups=2048, seed=4)
-    else:
+    elif workload == "ties":
         b = inputs.random_groups(26, [9, 10, 8, 9, 7, 10], lo=0, hi=3)
+    elif workload == "ties_uniform":
+        b = inputs.random_groups(27, [9] * 12, lo=0, hi=3)
+    else:
+        b = inputs.random_groups(28, [9] * 6, hi=60_000_000)
     stats, orders, hms, _ = scheduled_as_benched(tm, b, tuning)
     ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
     for g in range(b.G):
