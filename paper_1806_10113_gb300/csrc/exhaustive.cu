@@ -238,8 +238,9 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 // n <= 3 outright) while all warps stride over the group's 4-subsets and
 // tabulate alpha / beta / gamma, taking the subset's tasks from the lanes
 // by shuffle.  A group that fails validation gets tables too, which
-// nothing reads.  When the heuristic is requested, blocks G.. of the same
-// launch run it, one warp per group.
+// nothing reads.  When the heuristic is requested and no enumeration launch
+// follows (no group of 4 or more tasks), blocks G.. of the same launch run
+// it, one warp per group.
 constexpr int kPrepMaxThreads = 512;
 
 struct PrepArgs {
@@ -989,8 +990,17 @@ __global__ void __launch_bounds__(kEnumBlock, mode_min_blocks(MODE))
 enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info,
             const int4* __restrict__ tbl, const SuffixTab* __restrict__ sub, int G,
             uint64_t per_thread, uint32_t item_cost, Sink sink, uint32_t* next, uint32_t nchunks,
-            uint64_t split_c, uint32_t split_warps, uint32_t split_hi, uint32_t split_klo)
+            uint64_t split_c, uint32_t split_warps, uint32_t split_hi, uint32_t split_klo,
+            uint32_t enum_blocks, PrepArgs heur)
 {
+    if (blockIdx.x >= enum_blocks) {
+        // Blocks after the enumeration's run the heuristic, a warp per group
+        // (heur.orders set): they start as enumeration blocks finish, on the
+        // SMs the enumeration's uneven tail leaves idle.
+        prep_heuristic(heur, (int)((blockIdx.x - enum_blocks) * (blockDim.x / 32) + (threadIdx.x >> 5)),
+                       threadIdx.x & 31);
+        return;
+    }
     if (!next) {   // static split: one range per thread
         const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         uint64_t x0, x1;
@@ -1015,33 +1025,27 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
 // ---- finalize ---------------------------------------------------------------
 
 // Separate finalize (when the plan has no completion counters): one warp
-// per group of n >= 4 tasks in blocks [0, fin_blocks); the prep kernel
-// handled the others.  Blocks fin_blocks.. run the heuristic, a warp per
-// group, when the launch carries it (a.orders set): it needs nothing from
-// the enumeration, and here it runs beside the finalize warps instead of
-// delaying the enumeration's start.
-__global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc, int fin_blocks)
+// per group of n >= 4 tasks; the prep kernel handled the others.  (The
+// heuristic, when requested, runs in the enumeration launch's last blocks.)
+__global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc)
 {
-    const int lane = threadIdx.x & 31;
-    if (blockIdx.x >= (unsigned)fin_blocks) {
-        prep_heuristic(a, (blockIdx.x - fin_blocks) * (blockDim.x / 32) + (threadIdx.x >> 5), lane);
-        return;
-    }
     const int g = (int)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (g >= a.G) return;
     const GroupInfo gi = a.info[g];
     if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, a.tbl, acc, a.stats, a.status);
 }
 
+// heur.orders set: the launch also runs the heuristic (enum_kernel).
 template <int PDMAX, int MODE>
-cudaError_t launch_enum(const Plan& p, const Sink& sink, cudaStream_t stream)
+cudaError_t launch_enum(const Plan& p, const Sink& sink, const PrepArgs& heur, cudaStream_t stream)
 {
-    uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
+    const uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
+    const uint32_t hblocks = heur.orders ? (uint32_t)(p.G + kEnumBlock / 32 - 1) / (kEnumBlock / 32) : 0u;
     const bool dyn = p.chunks_per_thread > 1;
-    enum_kernel<PDMAX, MODE><<<blocks, kEnumBlock, 0, stream>>>(
+    enum_kernel<PDMAX, MODE><<<blocks + hblocks, kEnumBlock, 0, stream>>>(
         p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
         sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u, dyn ? 0ull : p.split_c,
-        p.split_warps, p.split_hi, p.split_klo);
+        p.split_warps, p.split_hi, p.split_klo, blocks, heur);
     return cudaGetLastError();
 }
 
@@ -1066,14 +1070,15 @@ cudaError_t enum_occupancy_mode(int mode, int* per_sm)
 }
 
 template <int PDMAX>
-cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, cudaStream_t stream)
+cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, const PrepArgs& heur,
+                             cudaStream_t stream)
 {
     switch (p.unroll) {
-    case 1: return launch_enum<PDMAX, 1>(p, sink, stream);
-    case 2: return launch_enum<PDMAX, 2>(p, sink, stream);
-    case 3: return launch_enum<PDMAX, 3>(p, sink, stream);
-    case 4: return launch_enum<PDMAX, 4>(p, sink, stream);
-    case 5: return launch_enum<PDMAX, 5>(p, sink, stream);
+    case 1: return launch_enum<PDMAX, 1>(p, sink, heur, stream);
+    case 2: return launch_enum<PDMAX, 2>(p, sink, heur, stream);
+    case 3: return launch_enum<PDMAX, 3>(p, sink, heur, stream);
+    case 4: return launch_enum<PDMAX, 4>(p, sink, heur, stream);
+    case 5: return launch_enum<PDMAX, 5>(p, sink, heur, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1187,8 +1192,9 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     // a block per group: 512 threads when the batch's groups have many
     // (subset, order) pairs (n >= 9: >= 3,024), else 128
     const int prep_threads = p.total_subs >= 100u * (uint32_t)p.G ? kPrepMaxThreads : 128;
-    // the heuristic runs in the finalize launch when there is one, else here
-    const bool heur_late = d_orders && p.total_items > 0 && !p.d_done;
+    // the heuristic runs in the enumeration launch's last blocks when there
+    // is one, else here
+    const bool heur_late = d_orders && p.total_items > 0;
     PrepArgs pp = pa;
     if (heur_late) pp.orders = pp.makespans = nullptr;
     const int heur_blocks =
@@ -1207,10 +1213,12 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
         if (p.ev_before &&
             (e = cudaEventRecordWithFlags(p.ev_before, stream, rec_flags)) != cudaSuccess)
             return e;
+        PrepArgs heur = pa;
+        if (!heur_late) heur.orders = heur.makespans = nullptr;
         switch (p.pdmax) {
-        case 3: e = launch_enum_mode<3>(p, sink, stream); break;
-        case 4: e = launch_enum_mode<4>(p, sink, stream); break;
-        case 5: e = launch_enum_mode<5>(p, sink, stream); break;
+        case 3: e = launch_enum_mode<3>(p, sink, heur, stream); break;
+        case 4: e = launch_enum_mode<4>(p, sink, heur, stream); break;
+        case 5: e = launch_enum_mode<5>(p, sink, heur, stream); break;
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
@@ -1219,8 +1227,7 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
             return e;
         if (!p.d_done) {
             const int fin_blocks = (p.G * 32 + 255) / 256;
-            const int late = heur_late ? (p.G + 7) / 8 : 0;
-            finalize_kernel<<<fin_blocks + late, 256, 0, stream>>>(pa, p.d_acc, fin_blocks);
+            finalize_kernel<<<fin_blocks, 256, 0, stream>>>(pa, p.d_acc);
             e = cudaGetLastError();
         }
     }
