@@ -257,7 +257,10 @@ int tm_plan_launches(const tm_plan* plan);
  * caller with timing enabled) that every later tm_exhaustive_batch_dev call
  * on this plan records on its stream immediately before and after its
  * enumeration kernel.  NULL, NULL turns it off.  The plan does not own the
- * events; the caller keeps them alive while the hook is set. */
+ * events; the caller keeps them alive while the hook is set.  Without the
+ * hook the finalize launch is a programmatic dependent launch (it may start
+ * while the enumeration finishes, and waits for its results); with it the
+ * pass runs in plain stream order. */
 int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
 
 /* Work counts of the plan's last run, for measuring it (the exhaustive

@@ -49,6 +49,17 @@ constexpr int kEnumBlock = 128;
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Programmatic dependent launch: the finalize launch may start while the
+// enumeration finishes (launch_exhaustive sets the launch attribute when no
+// timing event sits between them).  wait blocks until the kernel before has
+// completed and its writes are visible (a no-op without the attribute);
+// launch_dependents lets the next launch begin once every block of this
+// grid has started.  (Between prep and enumeration it measured slower: the
+// enumeration's blocks, placed beside the prep blocks still running, spread
+// its uneven walk-mode-5 work worse over the SMs.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // 4-subsets of {0..11} in colexicographic order: the subsets of {0..n-1}
 // are the first C(n, 4) entries, for every n.
 struct Subsets {
@@ -993,6 +1004,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
             uint64_t split_c, uint32_t split_warps, uint32_t split_hi, uint32_t split_klo,
             uint32_t enum_blocks, PrepArgs heur)
 {
+    pdl_launch_next();   // the finalize launch may begin
     if (blockIdx.x >= enum_blocks) {
         // Blocks after the enumeration's run the heuristic, a warp per group
         // (heur.orders set): they start as enumeration blocks finish, on the
@@ -1029,24 +1041,44 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
 // heuristic, when requested, runs in the enumeration launch's last blocks.)
 __global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc)
 {
+    pdl_wait();          // the enumeration's reduction words
     const int g = (int)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (g >= a.G) return;
     const GroupInfo gi = a.info[g];
     if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, a.tbl, acc, a.stats, a.status);
 }
 
+// A launch configuration, with programmatic dependent launch if pdl.
+struct LaunchCfg {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    LaunchCfg(unsigned grid, unsigned block, cudaStream_t s, bool pdl)
+    {
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl ? attr : nullptr;
+        cfg.numAttrs = pdl ? 1 : 0;
+    }
+};
+
 // heur.orders set: the launch also runs the heuristic (enum_kernel).
 template <int PDMAX, int MODE>
-cudaError_t launch_enum(const Plan& p, const Sink& sink, const PrepArgs& heur, cudaStream_t stream)
+cudaError_t launch_enum(const Plan& p, const Sink& sink, const PrepArgs& heur, cudaStream_t stream,
+                        bool pdl)
 {
     const uint32_t blocks = (p.threads + kEnumBlock - 1) / kEnumBlock;
     const uint32_t hblocks = heur.orders ? (uint32_t)(p.G + kEnumBlock / 32 - 1) / (kEnumBlock / 32) : 0u;
     const bool dyn = p.chunks_per_thread > 1;
-    enum_kernel<PDMAX, MODE><<<blocks + hblocks, kEnumBlock, 0, stream>>>(
-        p.d_gp, p.d_info, p.d_tbl, p.d_sub, p.G, dyn ? p.chunk : p.leaves_per_thread, p.item_cost,
-        sink, dyn ? p.d_next : nullptr, dyn ? p.nchunks : 0u, dyn ? 0ull : p.split_c,
-        p.split_warps, p.split_hi, p.split_klo, blocks, heur);
-    return cudaGetLastError();
+    LaunchCfg lc(blocks + hblocks, kEnumBlock, stream, pdl);
+    return cudaLaunchKernelEx(&lc.cfg, enum_kernel<PDMAX, MODE>,
+        (const GroupPlan*)p.d_gp, (const GroupInfo*)p.d_info, (const int4*)p.d_tbl,
+        (const SuffixTab*)p.d_sub, p.G, (uint64_t)(dyn ? p.chunk : p.leaves_per_thread), p.item_cost,
+        sink, dyn ? p.d_next : (uint32_t*)nullptr, dyn ? p.nchunks : 0u,
+        (uint64_t)(dyn ? 0ull : p.split_c), p.split_warps, p.split_hi, p.split_klo, blocks, heur);
 }
 
 template <int PDMAX, int MODE>
@@ -1071,14 +1103,14 @@ cudaError_t enum_occupancy_mode(int mode, int* per_sm)
 
 template <int PDMAX>
 cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, const PrepArgs& heur,
-                             cudaStream_t stream)
+                             cudaStream_t stream, bool pdl)
 {
     switch (p.unroll) {
-    case 1: return launch_enum<PDMAX, 1>(p, sink, heur, stream);
-    case 2: return launch_enum<PDMAX, 2>(p, sink, heur, stream);
-    case 3: return launch_enum<PDMAX, 3>(p, sink, heur, stream);
-    case 4: return launch_enum<PDMAX, 4>(p, sink, heur, stream);
-    case 5: return launch_enum<PDMAX, 5>(p, sink, heur, stream);
+    case 1: return launch_enum<PDMAX, 1>(p, sink, heur, stream, pdl);
+    case 2: return launch_enum<PDMAX, 2>(p, sink, heur, stream, pdl);
+    case 3: return launch_enum<PDMAX, 3>(p, sink, heur, stream, pdl);
+    case 4: return launch_enum<PDMAX, 4>(p, sink, heur, stream, pdl);
+    case 5: return launch_enum<PDMAX, 5>(p, sink, heur, stream, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1216,9 +1248,9 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
         PrepArgs heur = pa;
         if (!heur_late) heur.orders = heur.makespans = nullptr;
         switch (p.pdmax) {
-        case 3: e = launch_enum_mode<3>(p, sink, heur, stream); break;
-        case 4: e = launch_enum_mode<4>(p, sink, heur, stream); break;
-        case 5: e = launch_enum_mode<5>(p, sink, heur, stream); break;
+        case 3: e = launch_enum_mode<3>(p, sink, heur, stream, false); break;
+        case 4: e = launch_enum_mode<4>(p, sink, heur, stream, false); break;
+        case 5: e = launch_enum_mode<5>(p, sink, heur, stream, false); break;
         default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
@@ -1227,8 +1259,10 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
             return e;
         if (!p.d_done) {
             const int fin_blocks = (p.G * 32 + 255) / 256;
-            finalize_kernel<<<fin_blocks, 256, 0, stream>>>(pa, p.d_acc);
-            e = cudaGetLastError();
+            // programmatic dependent launch where it directly follows the
+            // enumeration (a timing event between them keeps stream order)
+            LaunchCfg lc((unsigned)fin_blocks, 256, stream, !p.ev_after);
+            e = cudaLaunchKernelEx(&lc.cfg, finalize_kernel, pa, p.d_acc);
         }
     }
     return e;
