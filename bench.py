@@ -614,7 +614,7 @@ def learned_leg(args, log) -> dict:
             "clocks": clocks, "train": train_info}
 
 
-def chain_ops_per_order(T: int) -> float:
+def chain_ops_per_order(T: int, full: float = 1.0) -> float:
     """Integer operations per order of the chained search's tail, the part
     every order needs.  Four workers (the fast path): 16 recurrence steps
     for the first two positions (6 operations each: three maxima, three
@@ -624,9 +624,14 @@ def chain_ops_per_order(T: int) -> float:
     32-bit add, 64-bit add, two compares): 376 per 24 orders.  Otherwise the
     last m = min(T, 4) positions walked step by step (64 / 15 / 4 / 1 steps
     for m! = 24 / 6 / 2 / 1 orders) plus the same reduction (4 for a single
-    order).  The head positions recomputed between blocks are not counted."""
+    order).  The head positions recomputed between blocks are not counted.
+    With four workers a fraction 1 - `full` of the 24-order tails take the
+    closed form where the HtD engine's path ends all 24 (tm_chain_tail_counts):
+    every tail first costs the test (six differences, six compares, four
+    ands: 16); a closed one then takes its minimum and maximum (2 adds, 2
+    compares), 24 h + the table's sum (2) and the 64-bit sum (2): 8."""
     if T == 4:
-        return (6 * 16 + 4 + 12 * 4 + 24 * 6 + 12 * 7) / 24
+        return (16 + full * (6 * 16 + 4 + 12 * 4 + 24 * 6 + 12 * 7) + (1.0 - full) * 8) / 24
     m = min(T, 4)
     steps = {4: 64, 3: 15, 2: 4, 1: 1}[m]
     red = {4: 12 * 7, 3: 3 * 7, 2: 7, 1: 4}[m]
@@ -658,7 +663,9 @@ def chain_leg(args, log, groups: int = CHAIN_GROUPS, steps: int = 20) -> dict:
     if (d_status.cpu().numpy() != 0).any():
         raise RuntimeError("chained workload: device status errors")
     step_s = statistics.mean(ms) / 1000.0
-    ops = chain_ops_per_order(CHAIN_WORKERS)
+    tails, closed = tm.tm_chain_tail_counts()   # of the last timed step
+    full = 1.0 - closed / tails if tails else 1.0
+    ops = chain_ops_per_order(CHAIN_WORKERS, full)
     achieved = ops * n_orders / step_s / 1e12
     log(f"chain: {n_orders / step_s:.3e} orders/s")
     return {"workload": (f"{G} chained groups: {CHAIN_WORKERS} workers x {CHAIN_ROUNDS} dependent "
@@ -670,7 +677,11 @@ def chain_leg(args, log, groups: int = CHAIN_GROUPS, steps: int = 20) -> dict:
             "roofline": {"bound": "alu", "achieved": achieved, "peak": INT32_PEAK_TOPS,
                          "unit": "Tops/s (int32)", "frac": achieved / INT32_PEAK_TOPS,
                          "kernel": "chain prep + enumeration + finalize (whole call)",
-                         "ops_per_order": round(ops, 3), "traffic": None},
+                         "ops_per_order": round(ops, 3),
+                         "ops_basis": (f"{closed} of {tails} 24-order tails ({100 * (1 - full):.1f}%) "
+                                       "in the closed form of the HtD engine's path, the rest "
+                                       "order by order (see chain_ops_per_order)"),
+                         "traffic": None},
             "clocks": clocks}
 
 

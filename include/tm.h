@@ -360,6 +360,16 @@ int tm_predict_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
                                const int32_t* d_workers, int G, const int32_t* d_orders,
                                const tm_device* d_devs, int32_t* d_makespans, int32_t* d_status,
                                void* stream);
+/* Work counts of the calling host thread's last exhaustive chained search
+ * (any of the three forms above), for measuring it.  Groups of four workers
+ * and at least two rounds end every order with the last round's 24 orders of
+ * the four workers (a "tail" block); *tails counts those blocks, *closed
+ * those that took the closed form of the case where the HtD engine's path
+ * ends all 24 (decided by one vote over a warp's blocks; the others are
+ * evaluated order by order).  Reads a device counter synchronously: call it
+ * once the search has finished.  TM_OK, TM_EINVAL (a NULL argument) or
+ * TM_ECUDA; both 0 before any search. */
+int tm_chain_tail_counts(unsigned long long* tails, unsigned long long* closed);
 
 /* ---- partial-overlap variant of the model --------------------------------- */
 

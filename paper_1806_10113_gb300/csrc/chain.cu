@@ -571,6 +571,72 @@ __device__ __forceinline__ void tail4_pair(Eng s, const int4 (&lr)[4], const Pai
     }
 }
 
+// The last round's 24 orders (four workers) when the HtD engine's path ends
+// every one of them.  The recurrence is max-plus linear in the state
+// (h, k, d) entering the round and the release times c_w, so order sigma
+// ends at
+//     max(h + G_sigma, k + B_sigma, d + alpha, max_w (c_w + Dw_sigma))
+// with G, B, Dw the longest paths through the round from the HtD engine,
+// the K engine and worker w's release, and alpha the round's DtH sum, all
+// fixed by the group.  When h - d >= alpha - min G, h - k >= max (B - G) and
+// c_w - h <= min (G - Dw) for every w, each order ends at h + G_sigma: the
+// 24 makespans are h + G, their minimum h + min G at the first sigma reaching
+// it, and so on.
+struct HtdTail {
+    int32_t td, tk, tc[4];
+    int32_t gmin, gmax;
+    uint32_t imin, imax;   // lexicographic index of the first sigma reaching them
+    unsigned long long gsum;
+};
+
+__device__ __noinline__ void htd_tail_setup(const int4 (&lr)[4], HtdTail& ht)
+{
+    constexpr int64_t kNeg = -(int64_t(1) << 40);
+    int64_t gmin = INT64_MAX, gmax = INT64_MIN, tk = INT64_MIN;
+    int64_t tc[4] = {INT64_MAX, INT64_MAX, INT64_MAX, INT64_MAX};
+    unsigned long long gsum = 0;
+    uint32_t imin = 0, imax = 0, idx = 0;
+    const int64_t alpha = (int64_t)lr[0].z + lr[1].z + lr[2].z + lr[3].z;
+    for (int p0 = 0; p0 < 4; ++p0)
+        for (int p1 = 0; p1 < 4; ++p1) {
+            if (p1 == p0) continue;
+            for (int p2 = 0; p2 < 4; ++p2) {
+                if (p2 == p0 || p2 == p1) continue;
+                const int sig[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
+                // sources: 0 the HtD engine, 1 the K engine, 2 + w worker w's release
+                int64_t h[6], k[6], d[6];
+                for (int q = 0; q < 6; ++q) {
+                    h[q] = q == 0 ? 0 : kNeg;
+                    k[q] = q == 1 ? 0 : kNeg;
+                    d[q] = kNeg;
+                }
+                for (int i = 0; i < 4; ++i) {
+                    const int w = sig[i];
+                    for (int q = 0; q < 6; ++q) {
+                        h[q] = max(h[q], q == 2 + w ? (int64_t)0 : kNeg) + lr[w].x;
+                        k[q] = max(k[q], h[q]) + lr[w].y;
+                        d[q] = max(d[q], k[q]) + lr[w].z;
+                    }
+                }
+                const int64_t g = d[0];
+                gsum += (unsigned long long)g;
+                if (g < gmin) { gmin = g; imin = idx; }
+                if (g > gmax) { gmax = g; imax = idx; }
+                tk = max(tk, d[1] - g);
+                for (int w = 0; w < 4; ++w) tc[w] = min(tc[w], g - d[2 + w]);
+                ++idx;
+            }
+        }
+    ht.td = (int32_t)(alpha - gmin);
+    ht.tk = (int32_t)tk;
+    for (int w = 0; w < 4; ++w) ht.tc[w] = (int32_t)tc[w];
+    ht.gmin = (int32_t)gmin;
+    ht.gmax = (int32_t)gmax;
+    ht.imin = imin;
+    ht.imax = imax;
+    ht.gsum = gsum;
+}
+
 // The T! orders of the last round's workers 0 .. T-1 from state s, in
 // lexicographic order: ranks rank, rank + 1, ...  (T = 4 takes tail4_pair.)
 template <int T>
@@ -594,13 +660,17 @@ __global__ void __launch_bounds__(kChainBlock)
 chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                    const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
                    unsigned long long* __restrict__ acc, unsigned long long per_thread,
-                   uint32_t one)
+                   uint32_t one, unsigned long long* __restrict__ counts)
 {
     constexpr int F = T == 2 ? 2 : T == 3 ? 6 : 24;
+    uint32_t ntail = 0, nclosed = 0;   // four workers: tails walked, closed forms taken
     const unsigned long long total = unit_base[G];
+    // a warp takes 32 per_thread consecutive units, lane l every 32nd from
+    // the l-th, so that its lanes walk neighbouring units (one group) at once
     const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long u = t * per_thread;
-    const unsigned long long u_end = min(total, u + per_thread);
+    const unsigned long long w0 = (t >> 5) * 32ull * per_thread;
+    unsigned long long u = w0 + (t & 31);
+    const unsigned long long u_end = min(total, w0 + 32ull * per_thread);
     if (u >= u_end) return;
     int g = 0;
     {
@@ -617,7 +687,7 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
         const ChainInfo ci = info[g];
         const unsigned long long g_end = min(u_end, (unsigned long long)unit_base[g + 1]);
         if (ci.status != 0 || ci.T != T || ci.R < 2) {   // rejected by the prep kernel
-            u = g_end;
+            u += (g_end - u + 31) / 32 * 32;   // the lane's next unit past the group
             continue;
         }
         const int R = ci.R;
@@ -634,8 +704,12 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
             sh_last += l.htd;
         }
         Pair4 pq;
-        if constexpr (T == 4) pair4_setup(reinterpret_cast<const int4 (&)[4]>(lrow), pq);
-        for (; u < g_end; ++u) {
+        HtdTail ht;
+        if constexpr (T == 4) {
+            pair4_setup(reinterpret_cast<const int4 (&)[4]>(lrow), pq);
+            htd_tail_setup(reinterpret_cast<const int4 (&)[4]>(lrow), ht);
+        }
+        for (; u < g_end; u += 32) {
             const uint32_t o = (uint32_t)(u - unit_base[g]);
             // replay rounds 0 .. R-3 of prefix o (digits base T!, round 0 first)
             Eng s{0, 0, 0};
@@ -694,13 +768,41 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                                       pick<T>(dend, (int)((iw >> (4 * w)) & 0xF)));
                 Eng s1 = st[T - 1];
                 if (ci.dma == 1) { s1.h = s1.d; s1.d += sh_last; }
-                if constexpr (T == 4)
-                    tail4_pair(s1, reinterpret_cast<const int4 (&)[4]>(lr), pq, a, rank, one);
-                else tail_static<T>(s1, lr, a, rank);
+                if constexpr (T == 4) {
+                    // the closed form when the HtD engine's path ends every
+                    // order on every lane of the warp (one path per warp)
+                    ++ntail;
+                    const int32_t hh = s1.h;
+                    bool hd = hh - s1.d >= ht.td && hh - s1.k >= ht.tk;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) hd = hd && lr[w].w - hh <= ht.tc[w];
+                    if (__all_sync(__activemask(), hd)) {
+                        ++nclosed;
+                        const int32_t mn = hh + ht.gmin, mx = hh + ht.gmax;
+                        if (mn < a.best) { a.best = mn; a.brank = rank + ht.imin; }
+                        if (mx > a.worst) { a.worst = mx; a.wrank = rank + ht.imax; }
+                        a.sum += 24ull * (uint32_t)hh + ht.gsum;
+                    } else {
+                        tail4_pair(s1, reinterpret_cast<const int4 (&)[4]>(lr), pq, a, rank, one);
+                    }
+                } else {
+                    tail_static<T>(s1, lr, a, rank);
+                }
                 rank += F;
             }
         }
         flush(a, acc, g);
+    }
+    if constexpr (T == 4) {
+        if (counts) {   // one pair of atomics per warp
+            const unsigned live = __activemask();
+            const uint32_t t32 = __reduce_add_sync(live, ntail);
+            const uint32_t c32 = __reduce_add_sync(live, nclosed);
+            if ((int)(threadIdx.x & 31) == __ffs(live) - 1) {
+                atomicAdd(&counts[0], (unsigned long long)t32);
+                atomicAdd(&counts[1], (unsigned long long)c32);
+            }
+        }
     }
 }
 
@@ -811,6 +913,7 @@ struct ChainScratch {
     size_t cap = 0;
     int device = -1;
     std::vector<unsigned long long> h_base;   // generic blocks, then fast-path units per T
+    unsigned long long* d_counts = nullptr;   // the last search's tails walked, closed forms
 };
 
 // Groups the fast path takes: 2 <= T <= 4 workers and at least two rounds.
@@ -819,7 +922,7 @@ inline bool chain_fast(int n, int T) { return T >= 2 && T <= 4 && n % T == 0 && 
 template <int T>
 cudaError_t launch_small(const unsigned long long* d_base, const unsigned long long* h_base, int G,
                          const ChainInfo* d_info, const tm_task* d_tasks, unsigned long long* d_acc,
-                         int dev, cudaStream_t s)
+                         int dev, cudaStream_t s, unsigned long long* d_counts)
 {
     const unsigned long long total = h_base[G];
     if (total == 0) return cudaSuccess;
@@ -833,7 +936,7 @@ cudaError_t launch_small(const unsigned long long* d_base, const unsigned long l
     const unsigned long long per_thread = (total + threads - 1) / threads;
     const unsigned long long used = (total + per_thread - 1) / per_thread;
     chain_small_kernel<T><<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
-        d_base, G, d_info, d_tasks, d_acc, per_thread, 1u);
+        d_base, G, d_info, d_tasks, d_acc, per_thread, 1u, d_counts);
     return cudaGetLastError();
 }
 thread_local ChainScratch t_chain;
@@ -854,7 +957,7 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     const size_t b_base = 4 * al((size_t)(G + 1) * 8), b_info = al((size_t)G * sizeof(ChainInfo)),
                  b_acc = al((size_t)G * 32);
     const size_t base_stride = al((size_t)(G + 1) * 8) / 8;
-    const size_t need = b_base + b_info + b_acc;
+    const size_t need = b_base + b_info + b_acc + al(16);   // + the tail counters
     if (sc.device != dev || sc.cap < need) {
         if (sc.p && sc.device == dev) {
             cudaDeviceSynchronize();   // earlier calls may still use it
@@ -870,6 +973,10 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     unsigned long long* d_base = reinterpret_cast<unsigned long long*>(p);
     ChainInfo* d_info = reinterpret_cast<ChainInfo*>(p + b_base);
     unsigned long long* d_acc = reinterpret_cast<unsigned long long*>(p + b_base + b_info);
+    unsigned long long* d_counts =
+        reinterpret_cast<unsigned long long*>(p + b_base + b_info + b_acc);
+    sc.d_counts = d_counts;
+    if (cudaMemsetAsync(d_counts, 0, 16, s) != cudaSuccess) return TM_ECUDA;
     // blocks of m! orders per group for the generic kernel (0 for a shape the
     // prep kernel rejects, and for the fast path's groups); units of (T!)^2
     // orders per fast-path group, one table per T
@@ -909,16 +1016,27 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
         chain_enum_kernel<<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
             d_base, G, d_info, d_tasks, d_acc, per_thread);
     }
-    if (launch_small<2>(d_base + base_stride, hb[1], G, d_info, d_tasks, d_acc, dev, s) !=
+    if (launch_small<2>(d_base + base_stride, hb[1], G, d_info, d_tasks, d_acc, dev, s, nullptr) !=
             cudaSuccess ||
-        launch_small<3>(d_base + 2 * base_stride, hb[2], G, d_info, d_tasks, d_acc, dev, s) !=
-            cudaSuccess ||
-        launch_small<4>(d_base + 3 * base_stride, hb[3], G, d_info, d_tasks, d_acc, dev, s) !=
-            cudaSuccess)
+        launch_small<3>(d_base + 2 * base_stride, hb[2], G, d_info, d_tasks, d_acc, dev, s,
+                        nullptr) != cudaSuccess ||
+        launch_small<4>(d_base + 3 * base_stride, hb[3], G, d_info, d_tasks, d_acc, dev, s,
+                        d_counts) != cudaSuccess)
         return TM_ECUDA;
     chain_finalize_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_info, d_tasks, G, d_acc, d_stats,
                                                          d_status);
     return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int chain_tail_counts(unsigned long long* tails, unsigned long long* closed)
+{
+    unsigned long long h[2] = {0ull, 0ull};
+    if (t_chain.d_counts &&
+        cudaMemcpy(h, t_chain.d_counts, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TM_ECUDA;
+    *tails = h[0];
+    *closed = h[1];
+    return TM_OK;
 }
 
 cudaError_t launch_chain_predict(const tm_task* d_tasks, const int32_t* d_offsets,
@@ -977,6 +1095,12 @@ thread_local ChainStage t_stage;
 }  // namespace
 
 extern "C" {
+
+int tm_chain_tail_counts(unsigned long long* tails, unsigned long long* closed)
+{
+    if (!tails || !closed) return TM_EINVAL;
+    return chain_tail_counts(tails, closed);
+}
 
 int tm_exhaustive_chain_batch_dev(const tm_task* d_tasks, const int32_t* d_offsets,
                                   const int32_t* h_offsets, const int32_t* d_workers,

@@ -103,6 +103,7 @@ _SIGS = {
     "tm_exhaustive_chain": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp],
     "tm_exhaustive_chain_batch": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp],
     "tm_exhaustive_chain_batch_dev": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tm_chain_tail_counts": [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)],
     "tm_predict_chain_batch_dev": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "tm_server_create": [_vp, _vp, ctypes.POINTER(_vp)],
     "tm_server_submit": [_vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_uint64)],
@@ -733,6 +734,15 @@ def tm_exhaustive_chain_batch_dev(d_tasks, d_offsets, offsets, d_workers, worker
                                                _dptr(d_workers), _p(w), G, _dptr(d_devs),
                                                _dptr(d_stats), _dptr(d_status), _stream(stream)),
            "tm_exhaustive_chain_batch_dev")
+
+
+def tm_chain_tail_counts():
+    """(tail blocks walked, tail blocks in closed form) of this host thread's
+    last exhaustive chained search; call it once the search has finished."""
+    tails, closed = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    _check(lib().tm_chain_tail_counts(ctypes.byref(tails), ctypes.byref(closed)),
+           "tm_chain_tail_counts")
+    return int(tails.value), int(closed.value)
 
 
 def tm_predict_chain_batch_dev(d_tasks, d_offsets, d_workers, G: int, d_orders, d_devs,

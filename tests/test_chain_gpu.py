@@ -177,6 +177,55 @@ def test_chain_workload_groups(tm):
         assert_stats_equal(got[g], ref[g], g)
 
 
+def test_chain_closed_form_counts_and_parity(tm):
+    """Four-worker tails in the closed form of the HtD engine's path: none
+    where kernels dominate under two DMA engines (the K engine runs ahead of
+    the HtD engine; with one engine the round starts after the last DtH, so
+    the HtD engine's path can end every order there too, and only parity is
+    checked); all where only the last round's HtDs are long and every
+    earlier task ends with its HtD (K = D = 0, so no release time and no
+    engine gets ahead of the HtD engine), under both models; some on the
+    mixed workload.  Every case equals the oracle's enumeration, and
+    tm_chain_tail_counts counts 24^(R-1) tails per group."""
+    rng = random.Random(31)
+
+    def kernels(r, R):
+        return [rng.randint(1, 9), rng.randint(10**6, 2 * 10**6), rng.randint(1, 9)]
+
+    def htd_last(r, R):
+        if r < R - 1:
+            return [rng.randint(1, 9), 0, 0]
+        return [rng.randint(10**6, 2 * 10**6), rng.randint(0, 9), 0]
+
+    for name, mk, dma in (("kernels", kernels, [2, 2, 2, 2]), ("kernels1", kernels, [1, 1, 1, 1]),
+                          ("htd_last", htd_last, [2, 1, 2, 1])):
+        for R in (2, 3, 4):
+            groups = [[mk(i // 4, R) for i in range(4 * R)] for _ in range(4)]
+            b = inputs.make_batch(groups, dma)
+            w = np.full(b.G, 4, dtype=np.int32)
+            got = tm.stats_to_dicts(tm.tm_exhaustive_chain_batch(b.tasks, b.offsets, w, b.dma),
+                                    b.sizes())
+            tails, closed = tm.tm_chain_tail_counts()
+            assert tails == b.G * 24 ** (R - 1), (name, R)
+            if name == "kernels":
+                assert closed == 0, (R, closed)
+            elif name == "htd_last":
+                assert closed == tails, (R, closed, tails)
+            ref = oracle.exhaustive_chain_batch(b.tasks, b.offsets, w, b.dma)
+            for g in range(b.G):
+                assert_stats_equal(got[g], ref[g], (name, R, g))
+    # the benchmark's shape (4 x 4: 576 units of 576 orders per group, so a
+    # warp's lanes walk one group at a time): the one-DMA groups' tails close
+    b = inputs.chained_groups(groups=24, workers=4, rounds=4, seed=9)
+    w = b.meta["workers"]
+    got = tm.stats_to_dicts(tm.tm_exhaustive_chain_batch(b.tasks, b.offsets, w, b.dma), b.sizes())
+    tails, closed = tm.tm_chain_tail_counts()
+    assert tails == b.G * 24 ** 3 and 0 < closed < tails
+    ref = oracle.exhaustive_chain_batch(b.tasks, b.offsets, w, b.dma)
+    for g in range(b.G):
+        assert_stats_equal(got[g], ref[g], g)
+
+
 def test_chain_dev_reports_bad_groups(tm):
     import torch
     b, workers = chain_batch(16, [(3, 2), (4, 2), (2, 3)], hi=1000)
