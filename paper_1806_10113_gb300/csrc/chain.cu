@@ -138,11 +138,78 @@ __device__ __forceinline__ uint32_t inverse_nib(uint32_t w, int T)
     return inv;
 }
 
+// The last round's 24 orders (four workers) when the HtD engine's path ends
+// every one of them.  The recurrence is max-plus linear in the state
+// (h, k, d) entering the round and the release times c_w, so order sigma
+// ends at
+//     max(h + G_sigma, k + B_sigma, d + alpha, max_w (c_w + Dw_sigma))
+// with G, B, Dw the longest paths through the round from the HtD engine,
+// the K engine and worker w's release, and alpha the round's DtH sum, all
+// fixed by the group.  When h - d >= alpha - min G, h - k >= max (B - G) and
+// c_w - h <= min (G - Dw) for every w, each order ends at h + G_sigma: the
+// 24 makespans are h + G, their minimum h + min G at the first sigma reaching
+// it, and so on.
+struct HtdTail {
+    int32_t td, tk, tc[4];
+    int32_t gmin, gmax;
+    uint32_t imin, imax;   // lexicographic index of the first sigma reaching them
+    unsigned long long gsum;
+};
+
+__device__ __noinline__ void htd_tail_setup(const int4 (&lr)[4], HtdTail& ht)
+{
+    constexpr int64_t kNeg = -(int64_t(1) << 40);
+    int64_t gmin = INT64_MAX, gmax = INT64_MIN, tk = INT64_MIN;
+    int64_t tc[4] = {INT64_MAX, INT64_MAX, INT64_MAX, INT64_MAX};
+    unsigned long long gsum = 0;
+    uint32_t imin = 0, imax = 0, idx = 0;
+    const int64_t alpha = (int64_t)lr[0].z + lr[1].z + lr[2].z + lr[3].z;
+    for (int p0 = 0; p0 < 4; ++p0)
+        for (int p1 = 0; p1 < 4; ++p1) {
+            if (p1 == p0) continue;
+            for (int p2 = 0; p2 < 4; ++p2) {
+                if (p2 == p0 || p2 == p1) continue;
+                const int sig[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
+                // sources: 0 the HtD engine, 1 the K engine, 2 + w worker w's release
+                int64_t h[6], k[6], d[6];
+                for (int q = 0; q < 6; ++q) {
+                    h[q] = q == 0 ? 0 : kNeg;
+                    k[q] = q == 1 ? 0 : kNeg;
+                    d[q] = kNeg;
+                }
+                for (int i = 0; i < 4; ++i) {
+                    const int w = sig[i];
+                    for (int q = 0; q < 6; ++q) {
+                        h[q] = max(h[q], q == 2 + w ? (int64_t)0 : kNeg) + lr[w].x;
+                        k[q] = max(k[q], h[q]) + lr[w].y;
+                        d[q] = max(d[q], k[q]) + lr[w].z;
+                    }
+                }
+                const int64_t g = d[0];
+                gsum += (unsigned long long)g;
+                if (g < gmin) { gmin = g; imin = idx; }
+                if (g > gmax) { gmax = g; imax = idx; }
+                tk = max(tk, d[1] - g);
+                for (int w = 0; w < 4; ++w) tc[w] = min(tc[w], g - d[2 + w]);
+                ++idx;
+            }
+        }
+    ht.td = (int32_t)(alpha - gmin);
+    ht.tk = (int32_t)tk;
+    for (int w = 0; w < 4; ++w) ht.tc[w] = (int32_t)tc[w];
+    ht.gmin = (int32_t)gmin;
+    ht.gmax = (int32_t)gmax;
+    ht.imin = imin;
+    ht.imax = imax;
+    ht.gsum = gsum;
+}
+
 __global__ void chain_prep_kernel(const tm_task* __restrict__ tasks,
                                   const int32_t* __restrict__ offsets,
                                   const int32_t* __restrict__ workers, int G,
                                   const tm_device* __restrict__ devs, ChainInfo* __restrict__ info,
-                                  unsigned long long* __restrict__ acc, int32_t* __restrict__ status)
+                                  unsigned long long* __restrict__ acc, int32_t* __restrict__ status,
+                                  HtdTail* __restrict__ tails)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
@@ -161,6 +228,16 @@ __global__ void chain_prep_kernel(const tm_task* __restrict__ tasks,
     acc[4 * (size_t)g + 1] = 0ull;
     acc[4 * (size_t)g + 2] = 0ull;
     if (status && rc != 0) status[g] = rc;
+    if (tails && rc == 0 && T == 4 && ci.R >= 2) {   // the fast path's closed-form table
+        int4 lr[4];
+        for (int w = 0; w < 4; ++w) {
+            const tm_task l = tasks[off + (ci.R - 1) * 4 + w];
+            lr[w] = make_int4(l.htd, l.k, l.dth, 0);
+        }
+        HtdTail ht;
+        htd_tail_setup(lr, ht);
+        tails[g] = ht;
+    }
 }
 
 // One thread's view of one group: the current order (worker of every
@@ -298,6 +375,36 @@ __device__ void flush(ChainAcc& a, unsigned long long* __restrict__ acc, int g)
     atomicMax(&acc[4 * (size_t)g + 1],
               ((unsigned long long)(uint32_t)a.worst << 32) | (0xFFFFFFFFu - a.wrank));
     atomicAdd(&acc[4 * (size_t)g + 2], a.sum);
+    a = ChainAcc{INT32_MAX, -1, 0u, 0u, 0ull};
+}
+
+// flush() by a whole warp whose lanes all hold group g: one set of atomics
+// for the warp (else each lane's own).
+__device__ void flush_warp(ChainAcc& a, unsigned long long* __restrict__ acc, int g)
+{
+    const unsigned live = __activemask();
+    if (live != 0xFFFFFFFFu || !__all_sync(live, g == __shfl_sync(live, g, 0))) {
+        flush(a, acc, g);
+        return;
+    }
+    const bool any = a.best != INT32_MAX;
+    unsigned long long bk = any ? (((unsigned long long)(uint32_t)a.best << 32) | a.brank) : ~0ull;
+    unsigned long long wk =
+        any ? (((unsigned long long)(uint32_t)a.worst << 32) | (0xFFFFFFFFu - a.wrank)) : 0ull;
+    unsigned long long sum = a.sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b2 = __shfl_xor_sync(live, bk, o);
+        const unsigned long long w2 = __shfl_xor_sync(live, wk, o);
+        bk = b2 < bk ? b2 : bk;
+        wk = w2 > wk ? w2 : wk;
+        sum += __shfl_xor_sync(live, sum, o);
+    }
+    if ((threadIdx.x & 31) == 0 && bk != ~0ull) {
+        atomicMin(&acc[4 * (size_t)g + 0], bk);
+        atomicMax(&acc[4 * (size_t)g + 1], wk);
+        atomicAdd(&acc[4 * (size_t)g + 2], sum);
+    }
     a = ChainAcc{INT32_MAX, -1, 0u, 0u, 0ull};
 }
 
@@ -571,71 +678,6 @@ __device__ __forceinline__ void tail4_pair(Eng s, const int4 (&lr)[4], const Pai
     }
 }
 
-// The last round's 24 orders (four workers) when the HtD engine's path ends
-// every one of them.  The recurrence is max-plus linear in the state
-// (h, k, d) entering the round and the release times c_w, so order sigma
-// ends at
-//     max(h + G_sigma, k + B_sigma, d + alpha, max_w (c_w + Dw_sigma))
-// with G, B, Dw the longest paths through the round from the HtD engine,
-// the K engine and worker w's release, and alpha the round's DtH sum, all
-// fixed by the group.  When h - d >= alpha - min G, h - k >= max (B - G) and
-// c_w - h <= min (G - Dw) for every w, each order ends at h + G_sigma: the
-// 24 makespans are h + G, their minimum h + min G at the first sigma reaching
-// it, and so on.
-struct HtdTail {
-    int32_t td, tk, tc[4];
-    int32_t gmin, gmax;
-    uint32_t imin, imax;   // lexicographic index of the first sigma reaching them
-    unsigned long long gsum;
-};
-
-__device__ __noinline__ void htd_tail_setup(const int4 (&lr)[4], HtdTail& ht)
-{
-    constexpr int64_t kNeg = -(int64_t(1) << 40);
-    int64_t gmin = INT64_MAX, gmax = INT64_MIN, tk = INT64_MIN;
-    int64_t tc[4] = {INT64_MAX, INT64_MAX, INT64_MAX, INT64_MAX};
-    unsigned long long gsum = 0;
-    uint32_t imin = 0, imax = 0, idx = 0;
-    const int64_t alpha = (int64_t)lr[0].z + lr[1].z + lr[2].z + lr[3].z;
-    for (int p0 = 0; p0 < 4; ++p0)
-        for (int p1 = 0; p1 < 4; ++p1) {
-            if (p1 == p0) continue;
-            for (int p2 = 0; p2 < 4; ++p2) {
-                if (p2 == p0 || p2 == p1) continue;
-                const int sig[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
-                // sources: 0 the HtD engine, 1 the K engine, 2 + w worker w's release
-                int64_t h[6], k[6], d[6];
-                for (int q = 0; q < 6; ++q) {
-                    h[q] = q == 0 ? 0 : kNeg;
-                    k[q] = q == 1 ? 0 : kNeg;
-                    d[q] = kNeg;
-                }
-                for (int i = 0; i < 4; ++i) {
-                    const int w = sig[i];
-                    for (int q = 0; q < 6; ++q) {
-                        h[q] = max(h[q], q == 2 + w ? (int64_t)0 : kNeg) + lr[w].x;
-                        k[q] = max(k[q], h[q]) + lr[w].y;
-                        d[q] = max(d[q], k[q]) + lr[w].z;
-                    }
-                }
-                const int64_t g = d[0];
-                gsum += (unsigned long long)g;
-                if (g < gmin) { gmin = g; imin = idx; }
-                if (g > gmax) { gmax = g; imax = idx; }
-                tk = max(tk, d[1] - g);
-                for (int w = 0; w < 4; ++w) tc[w] = min(tc[w], g - d[2 + w]);
-                ++idx;
-            }
-        }
-    ht.td = (int32_t)(alpha - gmin);
-    ht.tk = (int32_t)tk;
-    for (int w = 0; w < 4; ++w) ht.tc[w] = (int32_t)tc[w];
-    ht.gmin = (int32_t)gmin;
-    ht.gmax = (int32_t)gmax;
-    ht.imin = imin;
-    ht.imax = imax;
-    ht.gsum = gsum;
-}
 
 // The T! orders of the last round's workers 0 .. T-1 from state s, in
 // lexicographic order: ranks rank, rank + 1, ...  (T = 4 takes tail4_pair.)
@@ -659,21 +701,28 @@ template <int T>
 __global__ void __launch_bounds__(kChainBlock)
 chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                    const ChainInfo* __restrict__ info, const tm_task* __restrict__ tasks,
-                   unsigned long long* __restrict__ acc, unsigned long long per_thread,
-                   uint32_t one, unsigned long long* __restrict__ counts)
+                   unsigned long long* __restrict__ acc, unsigned long long per_lane,
+                   uint32_t one, unsigned long long* __restrict__ counts,
+                   const HtdTail* __restrict__ tails, unsigned long long* __restrict__ next)
 {
     constexpr int F = T == 2 ? 2 : T == 3 ? 6 : 24;
     uint32_t ntail = 0, nclosed = 0;   // four workers: tails walked, closed forms taken
     const unsigned long long total = unit_base[G];
-    // a warp takes 32 per_thread consecutive units, lane l every 32nd from
-    // the l-th, so that its lanes walk neighbouring units (one group) at once
-    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long w0 = (t >> 5) * 32ull * per_thread;
-    unsigned long long u = w0 + (t & 31);
-    const unsigned long long u_end = min(total, w0 + 32ull * per_thread);
-    if (u >= u_end) return;
+    const int lane = threadIdx.x & 31;
+    ChainAcc a{INT32_MAX, -1, 0u, 0u, 0ull};
+    // Warps take batches of 32 per_lane consecutive units from *next in
+    // turn (units cost unevenly: closed-form tails are cheap), lane l every
+    // 32nd from the l-th, so that a warp's lanes walk neighbouring units
+    // (one group) at once.
+    for (;;) {
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(next, 32ull * per_lane);
+    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+    if (b0 >= total) break;
+    unsigned long long u = b0 + (unsigned long long)lane;
+    const unsigned long long u_end = min(total, b0 + 32ull * per_lane);
     int g = 0;
-    {
+    if (u < u_end) {
         int lo = 0, hi = G;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -681,7 +730,6 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
         }
         g = lo;
     }
-    ChainAcc a{INT32_MAX, -1, 0u, 0u, 0ull};
     while (u < u_end) {
         while (u >= unit_base[g + 1]) ++g;
         const ChainInfo ci = info[g];
@@ -707,7 +755,7 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
         HtdTail ht;
         if constexpr (T == 4) {
             pair4_setup(reinterpret_cast<const int4 (&)[4]>(lrow), pq);
-            htd_tail_setup(reinterpret_cast<const int4 (&)[4]>(lrow), ht);
+            ht = tails[g];   // tabulated by the prep kernel
         }
         for (; u < g_end; u += 32) {
             const uint32_t o = (uint32_t)(u - unit_base[g]);
@@ -791,7 +839,9 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
                 rank += F;
             }
         }
-        flush(a, acc, g);
+        flush_warp(a, acc, g);
+    }
+    __syncwarp();
     }
     if constexpr (T == 4) {
         if (counts) {   // one pair of atomics per warp
@@ -922,7 +972,8 @@ inline bool chain_fast(int n, int T) { return T >= 2 && T <= 4 && n % T == 0 && 
 template <int T>
 cudaError_t launch_small(const unsigned long long* d_base, const unsigned long long* h_base, int G,
                          const ChainInfo* d_info, const tm_task* d_tasks, unsigned long long* d_acc,
-                         int dev, cudaStream_t s, unsigned long long* d_counts)
+                         int dev, cudaStream_t s, unsigned long long* d_counts,
+                         const HtdTail* d_tails, unsigned long long* d_next)
 {
     const unsigned long long total = h_base[G];
     if (total == 0) return cudaSuccess;
@@ -932,11 +983,15 @@ cudaError_t launch_small(const unsigned long long* d_base, const unsigned long l
                                                       0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const unsigned long long resident = (unsigned long long)std::max(sms, 1) * per_sm * kChainBlock;
-    const unsigned long long threads = std::min(total, resident);
-    const unsigned long long per_thread = (total + threads - 1) / threads;
-    const unsigned long long used = (total + per_thread - 1) / per_thread;
-    chain_small_kernel<T><<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
-        d_base, G, d_info, d_tasks, d_acc, per_thread, 1u, d_counts);
+    // batches of 32 x per_lane units, at least four per warp where the
+    // batch allows, at most 4 units a lane
+    const unsigned long long per_lane = std::max<unsigned long long>(
+        1ull, std::min<unsigned long long>(4ull, total / (4ull * resident)));
+    const unsigned long long warps =
+        std::min((resident + 31) / 32, (total + 32 * per_lane - 1) / (32 * per_lane));
+    const unsigned blocks = (unsigned)((warps * 32 + kChainBlock - 1) / kChainBlock);
+    chain_small_kernel<T><<<blocks, kChainBlock, 0, s>>>(d_base, G, d_info, d_tasks, d_acc,
+                                                        per_lane, 1u, d_counts, d_tails, d_next);
     return cudaGetLastError();
 }
 thread_local ChainScratch t_chain;
@@ -957,7 +1012,9 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     const size_t b_base = 4 * al((size_t)(G + 1) * 8), b_info = al((size_t)G * sizeof(ChainInfo)),
                  b_acc = al((size_t)G * 32);
     const size_t base_stride = al((size_t)(G + 1) * 8) / 8;
-    const size_t need = b_base + b_info + b_acc + al(16);   // + the tail counters
+    const size_t b_tails = al((size_t)G * sizeof(HtdTail));
+    // + the tail counters and the three fast-path batch counters
+    const size_t need = b_base + b_info + b_acc + b_tails + al(40);
     if (sc.device != dev || sc.cap < need) {
         if (sc.p && sc.device == dev) {
             cudaDeviceSynchronize();   // earlier calls may still use it
@@ -973,10 +1030,11 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
     unsigned long long* d_base = reinterpret_cast<unsigned long long*>(p);
     ChainInfo* d_info = reinterpret_cast<ChainInfo*>(p + b_base);
     unsigned long long* d_acc = reinterpret_cast<unsigned long long*>(p + b_base + b_info);
+    HtdTail* d_tails = reinterpret_cast<HtdTail*>(p + b_base + b_info + b_acc);
     unsigned long long* d_counts =
-        reinterpret_cast<unsigned long long*>(p + b_base + b_info + b_acc);
+        reinterpret_cast<unsigned long long*>(p + b_base + b_info + b_acc + b_tails);
     sc.d_counts = d_counts;
-    if (cudaMemsetAsync(d_counts, 0, 16, s) != cudaSuccess) return TM_ECUDA;
+    if (cudaMemsetAsync(d_counts, 0, 40, s) != cudaSuccess) return TM_ECUDA;
     // blocks of m! orders per group for the generic kernel (0 for a shape the
     // prep kernel rejects, and for the fast path's groups); units of (T!)^2
     // orders per fast-path group, one table per T
@@ -1001,7 +1059,7 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
         cudaSuccess)
         return TM_ECUDA;
     chain_prep_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_tasks, d_offsets, d_workers, G, d_devs,
-                                                     d_info, d_acc, d_status);
+                                                     d_info, d_acc, d_status, d_tails);
     const unsigned long long total = hb[0][G];
     if (total > 0) {
         int sms = 0, per_sm = 0;
@@ -1016,12 +1074,12 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
         chain_enum_kernel<<<(unsigned)((used + kChainBlock - 1) / kChainBlock), kChainBlock, 0, s>>>(
             d_base, G, d_info, d_tasks, d_acc, per_thread);
     }
-    if (launch_small<2>(d_base + base_stride, hb[1], G, d_info, d_tasks, d_acc, dev, s, nullptr) !=
-            cudaSuccess ||
+    if (launch_small<2>(d_base + base_stride, hb[1], G, d_info, d_tasks, d_acc, dev, s, nullptr,
+                        d_tails, d_counts + 2) != cudaSuccess ||
         launch_small<3>(d_base + 2 * base_stride, hb[2], G, d_info, d_tasks, d_acc, dev, s,
-                        nullptr) != cudaSuccess ||
+                        nullptr, d_tails, d_counts + 3) != cudaSuccess ||
         launch_small<4>(d_base + 3 * base_stride, hb[3], G, d_info, d_tasks, d_acc, dev, s,
-                        d_counts) != cudaSuccess)
+                        d_counts, d_tails, d_counts + 4) != cudaSuccess)
         return TM_ECUDA;
     chain_finalize_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_info, d_tasks, G, d_acc, d_stats,
                                                          d_status);
