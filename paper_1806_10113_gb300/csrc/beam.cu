@@ -296,7 +296,7 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
 // the low words among the lanes that hold the top high word by a second --
 // and the lane that held it advances.  The keys are distinct, so the B kept
 // beams, and their order, are those of the block kernel.
-constexpr int kWarpSelectMaxB = 16;
+constexpr int kWarpSelectMaxB = 16;   // = kBeamWarpSelectMaxB (learn_internal.h)
 constexpr int kWarpSelectKeys = kWarpSelectMaxB * TM_MAX_TASKS / 32;
 static_assert(kWarpSelectKeys == 8, "the sorting network below is for eight keys");
 

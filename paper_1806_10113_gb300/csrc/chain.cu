@@ -36,6 +36,7 @@
 // R - 2's permutations read from a table.
 //
 //   chain_prep_kernel      per group: checks, reduction words
+//   chain_tail_kernel      per group of four workers: the closed-form table
 //   chain_enum_kernel      every order of every other group
 //   chain_small_kernel<T>  every order of the groups of T = 2, 3, 4 workers
 //   chain_finalize_kernel  reduction words -> tm_stats (orders unranked)
@@ -156,60 +157,12 @@ struct HtdTail {
     unsigned long long gsum;
 };
 
-__device__ __noinline__ void htd_tail_setup(const int4 (&lr)[4], HtdTail& ht)
-{
-    constexpr int64_t kNeg = -(int64_t(1) << 40);
-    int64_t gmin = INT64_MAX, gmax = INT64_MIN, tk = INT64_MIN;
-    int64_t tc[4] = {INT64_MAX, INT64_MAX, INT64_MAX, INT64_MAX};
-    unsigned long long gsum = 0;
-    uint32_t imin = 0, imax = 0, idx = 0;
-    const int64_t alpha = (int64_t)lr[0].z + lr[1].z + lr[2].z + lr[3].z;
-    for (int p0 = 0; p0 < 4; ++p0)
-        for (int p1 = 0; p1 < 4; ++p1) {
-            if (p1 == p0) continue;
-            for (int p2 = 0; p2 < 4; ++p2) {
-                if (p2 == p0 || p2 == p1) continue;
-                const int sig[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
-                // sources: 0 the HtD engine, 1 the K engine, 2 + w worker w's release
-                int64_t h[6], k[6], d[6];
-                for (int q = 0; q < 6; ++q) {
-                    h[q] = q == 0 ? 0 : kNeg;
-                    k[q] = q == 1 ? 0 : kNeg;
-                    d[q] = kNeg;
-                }
-                for (int i = 0; i < 4; ++i) {
-                    const int w = sig[i];
-                    for (int q = 0; q < 6; ++q) {
-                        h[q] = max(h[q], q == 2 + w ? (int64_t)0 : kNeg) + lr[w].x;
-                        k[q] = max(k[q], h[q]) + lr[w].y;
-                        d[q] = max(d[q], k[q]) + lr[w].z;
-                    }
-                }
-                const int64_t g = d[0];
-                gsum += (unsigned long long)g;
-                if (g < gmin) { gmin = g; imin = idx; }
-                if (g > gmax) { gmax = g; imax = idx; }
-                tk = max(tk, d[1] - g);
-                for (int w = 0; w < 4; ++w) tc[w] = min(tc[w], g - d[2 + w]);
-                ++idx;
-            }
-        }
-    ht.td = (int32_t)(alpha - gmin);
-    ht.tk = (int32_t)tk;
-    for (int w = 0; w < 4; ++w) ht.tc[w] = (int32_t)tc[w];
-    ht.gmin = (int32_t)gmin;
-    ht.gmax = (int32_t)gmax;
-    ht.imin = imin;
-    ht.imax = imax;
-    ht.gsum = gsum;
-}
 
 __global__ void chain_prep_kernel(const tm_task* __restrict__ tasks,
                                   const int32_t* __restrict__ offsets,
                                   const int32_t* __restrict__ workers, int G,
                                   const tm_device* __restrict__ devs, ChainInfo* __restrict__ info,
-                                  unsigned long long* __restrict__ acc, int32_t* __restrict__ status,
-                                  HtdTail* __restrict__ tails)
+                                  unsigned long long* __restrict__ acc, int32_t* __restrict__ status)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
@@ -228,16 +181,6 @@ __global__ void chain_prep_kernel(const tm_task* __restrict__ tasks,
     acc[4 * (size_t)g + 1] = 0ull;
     acc[4 * (size_t)g + 2] = 0ull;
     if (status && rc != 0) status[g] = rc;
-    if (tails && rc == 0 && T == 4 && ci.R >= 2) {   // the fast path's closed-form table
-        int4 lr[4];
-        for (int w = 0; w < 4; ++w) {
-            const tm_task l = tasks[off + (ci.R - 1) * 4 + w];
-            lr[w] = make_int4(l.htd, l.k, l.dth, 0);
-        }
-        HtdTail ht;
-        htd_tail_setup(lr, ht);
-        tails[g] = ht;
-    }
 }
 
 // One thread's view of one group: the current order (worker of every
@@ -697,6 +640,75 @@ __device__ __forceinline__ void tail_static(Eng s, const int4 (&lr)[T], ChainAcc
     }
 }
 
+// The closed-form table (HtdTail) of every group of four workers and at
+// least two rounds, a warp per group: lane q < 24 takes the q-th order of
+// the last round (lexicographic), follows the paths from the HtD engine, the
+// K engine and each worker's release through it (64-bit, with unreached
+// sources far below any time), and the warp reduces: G's minimum and
+// maximum with their first order, its sum, max (B - G) and min (G - Dw).
+__global__ void chain_tail_kernel(const ChainInfo* __restrict__ info,
+                                  const tm_task* __restrict__ tasks, int G,
+                                  HtdTail* __restrict__ tails)
+{
+    const int g = (int)(((unsigned)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;   // whole warps
+    const ChainInfo ci = info[g];
+    if (ci.status != 0 || ci.T != 4 || ci.R < 2) return;
+    constexpr long long kNeg = -(1ll << 40);
+    const bool live = lane < 24;
+    long long G_ = 0, tk = LLONG_MIN, tc[4] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MAX};
+    if (live) {
+        const uint32_t pw = c_small.perm[2][lane];
+        long long h[6], k[6], d[6];
+        for (int q = 0; q < 6; ++q) {
+            h[q] = q == 0 ? 0 : kNeg;
+            k[q] = q == 1 ? 0 : kNeg;
+            d[q] = kNeg;
+        }
+        for (int i = 0; i < 4; ++i) {
+            const int w = (int)((pw >> (4 * i)) & 0xF);
+            const tm_task t = tasks[ci.off + (ci.R - 1) * 4 + w];
+            for (int q = 0; q < 6; ++q) {
+                h[q] = max(h[q], q == 2 + w ? 0ll : kNeg) + t.htd;
+                k[q] = max(k[q], h[q]) + t.k;
+                d[q] = max(d[q], k[q]) + t.dth;
+            }
+        }
+        G_ = d[0];
+        tk = d[1] - G_;
+        for (int w = 0; w < 4; ++w) tc[w] = G_ - d[2 + w];
+    }
+    // G < 2^31 and the order index < 32: (G, index) packed keeps the first order on ties
+    unsigned long long kmin = live ? ((unsigned long long)G_ << 5) | (unsigned)lane : ~0ull;
+    unsigned long long kmax = live ? ((unsigned long long)G_ << 5) | (31u - (unsigned)lane) : 0ull;
+    unsigned long long sum = live ? (unsigned long long)G_ : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, kmin, o);
+        const unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        tk = max(tk, __shfl_xor_sync(0xFFFFFFFFu, tk, o));
+        for (int w = 0; w < 4; ++w) tc[w] = min(tc[w], __shfl_xor_sync(0xFFFFFFFFu, tc[w], o));
+    }
+    if (lane == 0) {
+        long long alpha = 0;
+        for (int w = 0; w < 4; ++w) alpha += tasks[ci.off + (ci.R - 1) * 4 + w].dth;
+        HtdTail ht;
+        ht.gmin = (int32_t)(kmin >> 5);
+        ht.imin = (uint32_t)(kmin & 31u);
+        ht.gmax = (int32_t)(kmax >> 5);
+        ht.imax = 31u - (uint32_t)(kmax & 31u);
+        ht.gsum = sum;
+        ht.td = (int32_t)(alpha - (long long)ht.gmin);
+        ht.tk = (int32_t)tk;
+        for (int w = 0; w < 4; ++w) ht.tc[w] = (int32_t)tc[w];
+        tails[g] = ht;
+    }
+}
+
 template <int T>
 __global__ void __launch_bounds__(kChainBlock)
 chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
@@ -755,7 +767,7 @@ chain_small_kernel(const unsigned long long* __restrict__ unit_base, int G,
         HtdTail ht;
         if constexpr (T == 4) {
             pair4_setup(reinterpret_cast<const int4 (&)[4]>(lrow), pq);
-            ht = tails[g];   // tabulated by the prep kernel
+            ht = tails[g];   // tabulated by chain_tail_kernel
         }
         for (; u < g_end; u += 32) {
             const uint32_t o = (uint32_t)(u - unit_base[g]);
@@ -1059,7 +1071,9 @@ int chain_exhaustive(const tm_task* d_tasks, const int32_t* d_offsets, const int
         cudaSuccess)
         return TM_ECUDA;
     chain_prep_kernel<<<(G + 127) / 128, 128, 0, s>>>(d_tasks, d_offsets, d_workers, G, d_devs,
-                                                     d_info, d_acc, d_status, d_tails);
+                                                     d_info, d_acc, d_status);
+    if (hb[3][G] > 0)   // groups on the four-worker fast path: their closed-form tables
+        chain_tail_kernel<<<(G + 3) / 4, 128, 0, s>>>(d_info, d_tasks, G, d_tails);
     const unsigned long long total = hb[0][G];
     if (total > 0) {
         int sms = 0, per_sm = 0;
