@@ -298,6 +298,10 @@ beam_select_kernel(const int32_t* __restrict__ offsets, const tm_task* __restric
 // beams, and their order, are those of the block kernel.
 constexpr int kWarpSelectMaxB = 16;   // = kBeamWarpSelectMaxB (learn_internal.h)
 constexpr int kWarpSelectKeys = kWarpSelectMaxB * TM_MAX_TASKS / 32;
+constexpr int kWarpSelectBlock = 256;   // 8 groups per block
+// Batches of at most this many groups keep the block selection (a block of
+// 1024 threads per group writes the next rows; the serving loop's batches).
+constexpr int kBlockSelectMaxGroups = 8;
 static_assert(kWarpSelectKeys == 8, "the sorting network below is for eight keys");
 
 __device__ __forceinline__ void cx_desc(unsigned long long& a, unsigned long long& b)
@@ -307,10 +311,13 @@ __device__ __forceinline__ void cx_desc(unsigned long long& a, unsigned long lon
     b = lo;
 }
 
-__global__ void __launch_bounds__(256)
+template <bool WRITE_NEXT>
+__global__ void __launch_bounds__(kWarpSelectBlock)
 beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __restrict__ tasks,
                         const float* __restrict__ logits, const BeamState* __restrict__ cur,
-                        BeamState* __restrict__ nxt, int G, int B, int R, int GS, int pos)
+                        BeamState* __restrict__ nxt, int G, int B, int R, int GS, int pos,
+                        const tm_device* __restrict__ devs, const float* __restrict__ scale,
+                        __nv_bfloat16* __restrict__ X)
 {
     const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -387,15 +394,13 @@ beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __re
         c = i - pb * R;
     }
     const float plse = __shfl_sync(kFull, lse, pb);
-    if (lane >= B) return;
     BeamState s;
-    if (mine == 0ull) {
-        s.alive = 0;
-        s.h = s.k = s.d = 0;
-        s.used = 0;
-        s.order = 0;
-        s.logp = 0.0f;
-    } else {
+    s.alive = 0;
+    s.h = s.k = s.d = 0;
+    s.used = 0;
+    s.order = 0;
+    s.logp = 0.0f;
+    if (lane < B && mine != 0ull) {
         const BeamState p = cg[pb];
         const int j = slot_task(p.used, n, c);
         const tm_task t = tasks[off + j];
@@ -406,7 +411,26 @@ beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __re
         s.logp = p.logp + (lg0[(size_t)pb * R + c] - plse);
         s.alive = 1;
     }
-    ng[lane] = s;
+    if (lane < B) ng[lane] = s;
+    if constexpr (WRITE_NEXT) {
+        // the candidate rows of position pos + 1 (R - 1 per beam) from the
+        // new beams, spread over the warp's lanes
+        __shared__ BeamState s_new[kWarpSelectBlock / 32][kWarpSelectMaxB];
+        const int wi = threadIdx.x >> 5;
+        if (lane < B) s_new[wi][lane] = s;
+        __syncwarp();
+        const int R1 = R - 1, left = n - pos - 1;
+        if (R1 > 0 && left > 0) {
+            const int dma = devs[g].dma_engines;
+            const float sc = scale[g];
+            for (int r = lane; r < B * R1; r += 32) {
+                const int b = r / R1, slot = r - b * R1;
+                if (slot < left && s_new[wi][b].alive)
+                    write_row(X, ((int64_t)g * B + b) * R1 + slot, tasks + off, n, s_new[wi][b],
+                              dma, sc, slot);
+            }
+        }
+    }
 }
 
 // Best finished beam vs the heuristic's order, which is already in `orders`
@@ -689,15 +713,22 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
     // the logits of position 0 are beam 0's alone (beam_init_kernel)
     const int GS = pos == 0 ? R : B * R;
     // X == nullptr: the caller writes the next position's rows itself.
-    // Large batches: 512 threads per group (more blocks per SM); small ones:
-    // 1024 (more threads for the log-softmax and the next position's rows).
+    // Widths up to 16 on more than kBlockSelectMaxGroups groups: a warp per
+    // group.  Otherwise a block per group: 512 threads for large batches
+    // (more blocks per SM), 1024 for small ones (more threads for the
+    // log-softmax and the next position's rows).
     const BeamState* c = static_cast<const BeamState*>(cur);
     BeamState* nx = static_cast<BeamState*>(nxt);
     __nv_bfloat16* x = reinterpret_cast<__nv_bfloat16*>(X);
-    if (!X && B <= kWarpSelectMaxB) {
+    if (B <= kWarpSelectMaxB && G > kBlockSelectMaxGroups) {
         const int64_t threads = (int64_t)G * 32;
-        beam_select_warp_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            offsets, tasks, logits, c, nx, G, B, R, GS, pos);
+        const unsigned blocks = (unsigned)((threads + kWarpSelectBlock - 1) / kWarpSelectBlock);
+        if (X)
+            beam_select_warp_kernel<true><<<blocks, kWarpSelectBlock, 0, s>>>(
+                offsets, tasks, logits, c, nx, G, B, R, GS, pos, devs, scale, x);
+        else
+            beam_select_warp_kernel<false><<<blocks, kWarpSelectBlock, 0, s>>>(
+                offsets, tasks, logits, c, nx, G, B, R, GS, pos, devs, scale, nullptr);
     } else if (G > 1024) {
         if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, x);
         else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, nullptr);

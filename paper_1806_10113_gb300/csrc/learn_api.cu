@@ -101,8 +101,7 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
                       sc.bx.as<bf16_raw>(), s);
         // small batches: the selection writes the next rows (two launches per
         // position); large ones: a separate row kernel spreads them over the GPU
-        const bool fused = (int64_t)gc * B * nm <= kBeamFusedRows &&
-                           (B > kBeamWarpSelectMaxB || gc <= kBeamFusedGroupsNarrow);
+        const bool fused = B <= kBeamWarpSelectMaxB || (int64_t)gc * B * nm <= kBeamFusedRows;
         for (int pos = 0; pos < nm && e == cudaSuccess; ++pos) {
             const int R = nm - pos;
             // position 0: beam 0's rows alone (the other beams start dead)

@@ -47,11 +47,9 @@ constexpr int64_t kBeamRowsPerChunk = int64_t(1) << 22;
 // Batches with at most this many first-position rows let the selection
 // kernel write the next position's rows (fewer launches); larger ones use a
 // separate row kernel (more parallel).  At widths up to kBeamWarpSelectMaxB
-// the separate row kernel goes with the one-warp-per-group selection, which
-// is faster from kBeamFusedGroupsNarrow groups on, whatever the row count.
+// a warp per group selects and writes the next rows, at any batch size.
 constexpr int64_t kBeamFusedRows = int64_t(1) << 19;
 constexpr int kBeamWarpSelectMaxB = 16;
-constexpr int kBeamFusedGroupsNarrow = 256;
 
 // Beam search of G groups (see tm_beam_batch_dev).  d_offsets / h_offsets
 // hold G + 1 task offsets (h_offsets need not start at 0; only differences

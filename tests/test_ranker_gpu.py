@@ -327,25 +327,24 @@ def test_beam_large_batch_equals_small_batches():
     assert np.array_equal(big[3][:25], small[3]) and (big[2] == 0).all()
 
 
-@pytest.mark.parametrize("width", [16, 7, 1])
+@pytest.mark.parametrize("width", [16, 7, 4, 1])
 def test_beam_warp_selection_equals_block_selection(width):
-    # Ragged groups of 1..16 tasks, enough of them that the first position
-    # has more than 2^19 rows (the separate row kernel and, for widths up to
-    # 16, the one-warp-per-group selection); 40 of them alone take the fused
-    # block selection.  The kept beams, so the orders, makespans and winners,
-    # must agree exactly.
+    # 600 ragged groups of 1..16 tasks take the one-warp-per-group selection
+    # (widths up to 16, more than 8 groups), which also writes the next
+    # position's rows; 8 of them alone take the block selection.  The kept
+    # beams, so the orders, makespans and winners, must agree exactly.
     rng = np.random.default_rng(21)
-    sizes = rng.integers(1, 17, (1 << 19) // (16 * width) + 200)
+    sizes = rng.integers(1, 17, 600)
     sizes[0] = 16
     b = inputs.random_groups(22, sizes, hi=3_000_000)
     r = tm.Ranker(seed=8)
     big = run_beam(b, r, width)
-    sub = inputs.make_batch([b.group(g) for g in range(40)], b.dma[:40])
+    sub = inputs.make_batch([b.group(g) for g in range(8)], b.dma[:8])
     small = run_beam(sub, r, width)
     T = int(sub.offsets[-1])
     assert (big[2] == 0).all() and (small[2] == 0).all()
-    assert np.array_equal(big[0][:T], small[0]) and np.array_equal(big[1][:40], small[1])
-    assert np.array_equal(big[3][:40], small[3])
+    assert np.array_equal(big[0][:T], small[0]) and np.array_equal(big[1][:8], small[1])
+    assert np.array_equal(big[3][:8], small[3])
 
 
 def test_beam_is_exhaustive_when_wide_enough():
