@@ -319,6 +319,10 @@ beam_select_warp_kernel(const int32_t* __restrict__ offsets, const tm_task* __re
                         const tm_device* __restrict__ devs, const float* __restrict__ scale,
                         __nv_bfloat16* __restrict__ X)
 {
+    // as a programmatic dependent launch it may start while the scores'
+    // kernel finishes: wait for it (a no-op otherwise)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= G) return;   // whole warps
@@ -708,7 +712,7 @@ cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm
 
 cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
                         const float* scale, const float* logits, const void* cur, void* nxt, int G,
-                        int B, int R, int pos, bf16_raw* X, cudaStream_t s)
+                        int B, int R, int pos, bf16_raw* X, cudaStream_t s, bool pdl)
 {
     // the logits of position 0 are beam 0's alone (beam_init_kernel)
     const int GS = pos == 0 ? R : B * R;
@@ -723,12 +727,21 @@ cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_d
     if (B <= kWarpSelectMaxB && G > kBlockSelectMaxGroups) {
         const int64_t threads = (int64_t)G * 32;
         const unsigned blocks = (unsigned)((threads + kWarpSelectBlock - 1) / kWarpSelectBlock);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kWarpSelectBlock);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl ? attr : nullptr;
+        cfg.numAttrs = pdl ? 1 : 0;
         if (X)
-            beam_select_warp_kernel<true><<<blocks, kWarpSelectBlock, 0, s>>>(
-                offsets, tasks, logits, c, nx, G, B, R, GS, pos, devs, scale, x);
-        else
-            beam_select_warp_kernel<false><<<blocks, kWarpSelectBlock, 0, s>>>(
-                offsets, tasks, logits, c, nx, G, B, R, GS, pos, devs, scale, nullptr);
+            return cudaLaunchKernelEx(&cfg, beam_select_warp_kernel<true>, offsets, tasks, logits, c,
+                                      nx, G, B, R, GS, pos, devs, scale, x);
+        return cudaLaunchKernelEx(&cfg, beam_select_warp_kernel<false>, offsets, tasks, logits, c,
+                                  nx, G, B, R, GS, pos, devs, scale, (__nv_bfloat16*)nullptr);
     } else if (G > 1024) {
         if (X) beam_select_kernel<true, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, x);
         else beam_select_kernel<false, 512><<<G, 512, 0, s>>>(offsets, tasks, devs, scale, logits, c, nx, B, R, GS, pos, nullptr);

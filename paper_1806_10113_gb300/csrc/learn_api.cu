@@ -19,7 +19,7 @@ cudaError_t beam_features(const int32_t* offsets, const tm_task* tasks, const tm
                           bf16_raw* X, cudaStream_t s);
 cudaError_t beam_select(const int32_t* offsets, const tm_task* tasks, const tm_device* devs,
                         const float* scale, const float* logits, const void* cur, void* nxt, int G,
-                        int B, int R, int pos, bf16_raw* X, cudaStream_t s);
+                        int B, int R, int pos, bf16_raw* X, cudaStream_t s, bool pdl);
 cudaError_t beam_finish(const int32_t* offsets, const int32_t* status, const void* st, int G,
                         int B, const int32_t* heur_ms, int32_t* orders, int32_t* ms,
                         int32_t* beam_won, cudaStream_t s);
@@ -110,11 +110,14 @@ int beam_batch(const tm_ranker* r, BeamScratch& sc, const tm_task* d_tasks,
                 e = beam_features(off, d_tasks, d_devs + g0, sc.scale.as<float>(), cur, gc, B, R,
                                   pos, sc.bx.as<bf16_raw>(), s);
             if (e == cudaSuccess)
+                // programmatic dependent launches: each position's scores
+                // and selection may start while the kernel before finishes
                 e = ranker_forward_tc(sc.bx.as<bf16_raw>(), rows, r->Wimg, sc.blog.as<float>(),
-                                      r->d_err, forward_blocks(r, rows), s);
+                                      r->d_err, forward_blocks(r, rows), s, nullptr, true);
             if (e == cudaSuccess)
                 e = beam_select(off, d_tasks, d_devs + g0, sc.scale.as<float>(), sc.blog.as<float>(),
-                                cur, nxt, gc, B, R, pos, fused ? sc.bx.as<bf16_raw>() : nullptr, s);
+                                cur, nxt, gc, B, R, pos, fused ? sc.bx.as<bf16_raw>() : nullptr, s,
+                                true);
             std::swap(cur, nxt);
         }
         if (e == cudaSuccess && K == 0)

@@ -66,8 +66,10 @@ size_t ranker_image_bytes();
 cudaError_t ranker_image(const float* P, const bf16_raw* Wb, unsigned char* img, cudaStream_t s);
 cudaError_t ranker_tc_configure();
 // keep (may be null): also the hidden layers' bfloat16 activations, [3][M][128].
+// pdl: launched as a programmatic dependent launch (its prologue, which
+// reads only the weight image, overlaps the end of the kernel before).
 cudaError_t ranker_forward_tc(const bf16_raw* X, int64_t M, const unsigned char* img,
                               float* logits, int* err, int blocks, cudaStream_t s,
-                              bf16_raw* keep = nullptr);
+                              bf16_raw* keep = nullptr, bool pdl = false);
 
 }  // namespace tmgpu

@@ -360,6 +360,10 @@ forward_tc_kernel(const bf16* __restrict__ X, int64_t M, const unsigned char* __
         }
     };
     uint4 v[4];
+    // launched as a programmatic dependent launch (the beam search), the
+    // prologue above overlaps the kernel before; its rows are read only now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     load_row(tile, v);
     for (; ok && tile < tiles; tile += step) {
         const int64_t r0 = tile * kTile;
@@ -474,18 +478,27 @@ cudaError_t ranker_tc_configure()
 }
 
 cudaError_t ranker_forward_tc(const bf16_raw* X, int64_t M, const unsigned char* img,
-                              float* logits, int* err, int blocks, cudaStream_t s, bf16_raw* keep)
+                              float* logits, int* err, int blocks, cudaStream_t s, bf16_raw* keep,
+                              bool pdl)
 {
     if (M <= 0) return cudaSuccess;
     const int64_t groups = (M + (int64_t)kTile * kGroups - 1) / ((int64_t)kTile * kGroups);
     const int grid = (int)(groups < blocks ? groups : blocks);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
     if (keep)
-        forward_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(
-            reinterpret_cast<const bf16*>(X), M, img, logits, err, reinterpret_cast<bf16*>(keep));
-    else
-        forward_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(
-            reinterpret_cast<const bf16*>(X), M, img, logits, err, nullptr);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, forward_tc_kernel<true>, reinterpret_cast<const bf16*>(X),
+                                  M, img, logits, err, reinterpret_cast<bf16*>(keep));
+    return cudaLaunchKernelEx(&cfg, forward_tc_kernel<false>, reinterpret_cast<const bf16*>(X), M,
+                              img, logits, err, (bf16*)nullptr);
 }
 
 }  // namespace tmgpu
