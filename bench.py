@@ -103,7 +103,7 @@ def method_ops_per_order(n: int) -> float:
 
 
 def dominance_ops_per_order(n: int, full: float) -> float:
-    """Integer operations per order of walk mode 5 (tm_tuning.unroll 5), where
+    """Integer operations per order of walk modes 5 to 7 (tm_tuning.unroll), where
     a fraction `full` of the prefixes had their 24 orders evaluated one by one
     (tm_plan_walk_counts) and the others took the closed forms.
 
@@ -140,7 +140,7 @@ def workload(rank: int = 0, name: str = "dkdt64x10"):
 
 def ops_per_order(b, full=None) -> float:
     """method_ops_per_order weighted by each group's orders (groups n >= 4);
-    with `full` (walk mode 5: the fraction of prefixes evaluated order by
+    with `full` (walk modes 5 to 7: the fraction of prefixes evaluated order by
     order, over the whole batch), dominance_ops_per_order instead."""
     f = (lambda n: method_ops_per_order(n)) if full is None else \
         (lambda n: dominance_ops_per_order(n, full))
@@ -150,12 +150,13 @@ def ops_per_order(b, full=None) -> float:
 
 def walk_basis(plan, tuning) -> tuple:
     """(fraction of prefixes evaluated order by order in the plan's last run,
-    or None outside walk mode 5; a one-line statement of the count's basis)."""
-    if int(tuning.get("unroll", 0)) != 5:
+    or None outside walk modes 5 to 7; a one-line statement of the count's basis)."""
+    mode = int(tuning.get("unroll", 0))
+    if mode < 5:
         return None, "max-plus suffix decomposition (see method_ops_per_order)"
     pre, full = plan.walk_counts()
     f = full / pre if pre else 1.0
-    return f, (f"walk mode 5: {full} of {pre} prefixes ({100 * f:.1f}%) evaluated order by "
+    return f, (f"walk mode {mode}: {full} of {pre} prefixes ({100 * f:.1f}%) evaluated order by "
                "order, the rest by closed forms (see dominance_ops_per_order)")
 
 

@@ -199,7 +199,7 @@ bool tuning_invalid(const tm_tuning& t)
     return (t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
            t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 ||
            t.item_cost > (1 << 20) || t.chunks_per_thread < 0 || t.chunks_per_thread > 64 ||
-           (t.fuse_finalize == 1 && t.chunks_per_thread > 1) || t.unroll < 0 || t.unroll > 5;
+           (t.fuse_finalize == 1 && t.chunks_per_thread > 1) || t.unroll < 0 || t.unroll > 7;
 }
 
 void free_plan(Plan& p)
@@ -426,7 +426,7 @@ int tm_plan_walk_counts(const tm_plan* plan, unsigned long long* prefixes,
     if (!plan || !prefixes || !full) return TM_EINVAL;
     *prefixes = plan->p.total_prefixes;
     *full = plan->p.total_prefixes;
-    if (plan->p.unroll != 5 || !plan->p.d_full || plan->p.total_items == 0) return TM_OK;
+    if (plan->p.unroll < 5 || !plan->p.d_full || plan->p.total_items == 0) return TM_OK;
     unsigned long long v = 0;
     if (cudaMemcpy(&v, plan->p.d_full, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
         return TM_ECUDA;

@@ -538,6 +538,9 @@ struct Sfx {
     int32_t bmin, cmin, tmin, tmax;   // tmin / tmax: min / max over sigma of gamma - beta
     uint32_t bsum, csum;              // sums of beta and gamma mod 2^32
     uint32_t one;   // 1, read from a kernel parameter (see leaves)
+    // Walk modes 6, 7: b and c live in shared memory instead, six int4 rows of
+    // b then six of c, row r of this thread at sq[r * kEnumBlock].
+    const int4* sq;
 };
 
 // Lexicographic rank of the first order that starts with the P tasks in
@@ -579,11 +582,20 @@ __device__ __forceinline__ int first_completion(int32_t k, int32_t d, int32_t v,
 // addition k + beta as a multiply-add by S.one, so that it too issues on the
 // FMA pipe beside the ALU pipe's maxima and minima; 4 as 3, compiled for four
 // resident blocks per SM (at most 128 registers) instead of three; 5 as 3,
-// with the dominance test (dominated()) before each prefix's 24 orders.
+// with the dominance test (dominated()) before each prefix's 24 orders; 6
+// as 5, with S's beta and gamma in shared memory instead of 48 registers,
+// the six prefixes of the straight-line level evaluated quad by quad of S's
+// orders (leaves6), compiled for four resident blocks per SM; 7 as 6, with
+// the six prefixes' vote and closed forms in one pass.
 __host__ __device__ constexpr bool mode_straight(int mode) { return mode != 2; }
 __host__ __device__ constexpr bool mode_fma_add(int mode) { return mode >= 3; }
-__host__ __device__ constexpr int mode_min_blocks(int mode) { return mode == 4 ? 4 : TM_ENUM_MIN_BLOCKS; }
-__host__ __device__ constexpr bool mode_dominance(int mode) { return mode == 5; }
+__host__ __device__ constexpr int mode_min_blocks(int mode)
+{
+    return (mode == 4 || mode >= 6) ? 4 : TM_ENUM_MIN_BLOCKS;
+}
+__host__ __device__ constexpr bool mode_dominance(int mode) { return mode >= 5; }
+__host__ __device__ constexpr bool mode_smem_sfx(int mode) { return mode >= 6; }
+__host__ __device__ constexpr bool mode_one_pass(int mode) { return mode == 7; }
 
 // One engine's path ends all 24 orders of S after a prefix with engine
 // times (k, d) in three cases, each with a closed form for the minimum, the
@@ -646,7 +658,17 @@ __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& 
     }
     const int32_t c0 = d + S.alpha;
     int32_t m[24];
-    if constexpr (mode_fma_add(MODE)) {
+    if constexpr (mode_smem_sfx(MODE)) {
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const int4 bq = S.sq[r * kEnumBlock], cq = S.sq[(6 + r) * kEnumBlock];
+            const uint32_t ku = (uint32_t)k;
+            m[4 * r] = max3i(c0, cq.x, (int32_t)(ku * S.one + (uint32_t)bq.x));
+            m[4 * r + 1] = max3i(c0, cq.y, (int32_t)(ku * S.one + (uint32_t)bq.y));
+            m[4 * r + 2] = max3i(c0, cq.z, (int32_t)(ku * S.one + (uint32_t)bq.z));
+            m[4 * r + 3] = max3i(c0, cq.w, (int32_t)(ku * S.one + (uint32_t)bq.w));
+        }
+    } else if constexpr (mode_fma_add(MODE)) {
 #pragma unroll
         for (int j = 0; j < 24; ++j)
             m[j] = max3i(c0, S.c[j], (int32_t)((uint32_t)k * S.one + (uint32_t)S.b[j]));
@@ -691,6 +713,55 @@ __device__ __forceinline__ void last_two(Eng st, int4 x, int4 y, const Sfx& S, A
     leaves<SUM32, MODE>(syx.k, syx.d, S, a);
 }
 
+// Walk modes 6, 7: the 24 orders of S after each of six prefixes (in walk
+// order), quad by quad of S's orders, so that each int4 of beta and gamma is
+// read from shared memory once for the six.  Each prefix keeps its own
+// minimum and (SUM32) its own 32-bit sum, which fits as in leaves.
+template <bool SUM32>
+__device__ __forceinline__ void leaves6(const Eng (&e)[6], const Sfx& S, Acc& a)
+{
+    int32_t c0[6], mn[6];
+    uint32_t sm[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        c0[i] = e[i].d + S.alpha;
+        mn[i] = INT32_MAX;
+        sm[i] = 0u;
+    }
+    unsigned long long wide = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const int4 bq = S.sq[r * kEnumBlock], cq = S.sq[(6 + r) * kEnumBlock];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const uint32_t ku = (uint32_t)e[i].k;
+            const int32_t m0 = max3i(c0[i], cq.x, (int32_t)(ku * S.one + (uint32_t)bq.x));
+            const int32_t m1 = max3i(c0[i], cq.y, (int32_t)(ku * S.one + (uint32_t)bq.y));
+            const int32_t m2 = max3i(c0[i], cq.z, (int32_t)(ku * S.one + (uint32_t)bq.z));
+            const int32_t m3 = max3i(c0[i], cq.w, (int32_t)(ku * S.one + (uint32_t)bq.w));
+            mn[i] = min3i(min3i(mn[i], m0, m1), m2, m3);
+            if (SUM32) {
+                // two terms as multiply-adds (FMA pipe), two as one 3-input add
+                sm[i] = (uint32_t)m0 * S.one + sm[i];
+                sm[i] = (uint32_t)m1 * S.one + sm[i];
+                sm[i] = sm[i] + (uint32_t)m2 + (uint32_t)m3;
+            } else {
+                // two makespans fit in 32 bits unsigned
+                wide += (uint32_t)m0 + (uint32_t)m1;
+                wide += (uint32_t)m2 + (uint32_t)m3;
+            }
+        }
+    }
+    if (SUM32) {
+        a.sum += ((unsigned long long)sm[0] + sm[1]) + ((unsigned long long)sm[2] + sm[3]) +
+                 ((unsigned long long)sm[4] + sm[5]);
+    } else {
+        a.sum += wide;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) note_prefix(mn[i], max3i(c0[i], e[i].k + S.bmax, S.cmax), a);
+}
+
 // Depth-first walk over the D remaining prefix tasks (ascending in `rem`):
 // their orders in lexicographic order, so `walked` counts prefixes in rank
 // order.  Straight-line modes: the level with three tasks left runs as straight-line code
@@ -709,6 +780,64 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
         leaves<SUM32, MODE>(s1.k, s1.d, S, a);
     } else if constexpr (D == 2) {
         last_two<SUM32, MODE>(st, tbl[nib_get(rem, 0)], tbl[nib_get(rem, 1)], S, a);
+    } else if constexpr (D == 3 && mode_one_pass(MODE) && SUM32) {
+        // walk mode 7: as the block below, with the vote and the closed
+        // forms in one pass (beta and gamma are not in registers here);
+        // groups whose sums need 64 bits, where only the DtH engine's case
+        // applies and the vote fails more often, take the block below.
+        // Under any of the three cases the minimum of the 24 makespans is
+        // max(c0, k + bmin, cmin): the dominating term's minimum, which
+        // bounds the other two terms' minima; the maximum max(c0, k + bmax,
+        // cmax) holds always.
+        const int4 t0 = tbl[nib_get(rem, 0)], t1 = tbl[nib_get(rem, 1)], t2 = tbl[nib_get(rem, 2)];
+        const Eng s0 = step(st, t0.x, t0.y, t0.z), s1 = step(st, t1.x, t1.y, t1.z),
+                  s2 = step(st, t2.x, t2.y, t2.z);
+        Eng e[6];
+        e[0] = step(step(s0, t1.x, t1.y, t1.z), t2.x, t2.y, t2.z);
+        e[1] = step(step(s0, t2.x, t2.y, t2.z), t1.x, t1.y, t1.z);
+        e[2] = step(step(s1, t0.x, t0.y, t0.z), t2.x, t2.y, t2.z);
+        e[3] = step(step(s1, t2.x, t2.y, t2.z), t0.x, t0.y, t0.z);
+        e[4] = step(step(s2, t0.x, t0.y, t0.z), t1.x, t1.y, t1.z);
+        e[5] = step(step(s2, t1.x, t1.y, t1.z), t0.x, t0.y, t0.z);
+        int32_t mn[6], mx[6];
+        unsigned long long sum = 0;
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const int32_t c0 = e[i].d + S.alpha, kmin = e[i].k + S.bmin;
+            mx[i] = max3i(c0, e[i].k + S.bmax, S.cmax);
+            mn[i] = max3i(c0, kmin, S.cmin);
+            const bool all_d = c0 >= mx[i];
+            const bool all_k = e[i].k >= S.tmax && c0 <= kmin;
+            const bool all_c = e[i].k <= S.tmin && c0 <= S.cmin;
+            ok = ok && (all_d || all_k || all_c);
+            sum += all_d ? 24u * (uint32_t)c0 : all_k ? 24u * (uint32_t)e[i].k + S.bsum : S.csum;
+        }
+        if (__all_sync(__activemask(), ok)) {
+            a.sum += sum;
+            const int32_t pmin = min(min3i(mn[0], mn[1], mn[2]), min3i(mn[3], mn[4], mn[5]));
+            const int32_t pmax = max(max3i(mx[0], mx[1], mx[2]), max3i(mx[3], mx[4], mx[5]));
+            if (pmin < a.imin) {
+                int at = 5;
+#pragma unroll
+                for (int i = 4; i >= 0; --i)
+                    if (mn[i] == pmin) at = i;
+                a.imin = pmin;
+                a.imin_at = a.walked + (uint32_t)at;
+            }
+            if (pmax > a.imax) {
+                int at = 5;
+#pragma unroll
+                for (int i = 4; i >= 0; --i)
+                    if (mx[i] == pmax) at = i;
+                a.imax = pmax;
+                a.imax_at = a.walked + (uint32_t)at;
+            }
+            a.walked += 6;
+        } else {
+            a.full += 6;
+            leaves6<SUM32>(e, S, a);
+        }
     } else if constexpr (D == 3 && mode_dominance(MODE)) {
         // as below, with one dominance vote for all six prefixes: either all
         // six take the closed form on every lane, or all six the full leaves
@@ -756,8 +885,12 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
             a.walked += 6;
         } else {
             a.full += 6;
+            if constexpr (mode_smem_sfx(MODE)) {
+                leaves6<SUM32>(e, S, a);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) leaves<SUM32, MODE, false>(e[i].k, e[i].d, S, a);
+                for (int i = 0; i < 6; ++i) leaves<SUM32, MODE, false>(e[i].k, e[i].d, S, a);
+            }
         }
     } else if constexpr (D == 3 && mode_straight(MODE)) {
         // the three tasks' rows loaded once; their six orders in
@@ -871,7 +1004,8 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
                                            const GroupInfo* __restrict__ info,
                                            const int4* __restrict__ tbl,
                                            const SuffixTab* __restrict__ sub, int G, uint64_t x0,
-                                           uint64_t x1, uint32_t item_cost, const Sink& sink)
+                                           uint64_t x1, uint32_t item_cost, const Sink& sink,
+                                           int4* sq)
 {
     const uint64_t total = gp[G].cost_base;
     if (x0 >= total) return;
@@ -884,6 +1018,7 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
     a.full = 0;
     Sfx S;
     S.one = sink.one;
+    S.sq = sq;
     GroupInfo gi;
     const int4* gt = tbl;
     uint32_t gbase = 0, gend = 0, heads = 1, cur = kFull;
@@ -926,6 +1061,10 @@ __device__ __forceinline__ void enum_range(const GroupPlan* __restrict__ gp,
                 S.b[4 * q] = b.x; S.b[4 * q + 1] = b.y; S.b[4 * q + 2] = b.z; S.b[4 * q + 3] = b.w;
                 int4 c = __ldg(v + 6 + q);
                 S.c[4 * q] = c.x; S.c[4 * q + 1] = c.y; S.c[4 * q + 2] = c.z; S.c[4 * q + 3] = c.w;
+                if constexpr (mode_smem_sfx(MODE)) {   // this thread's column only
+                    sq[q * kEnumBlock] = b;
+                    sq[(6 + q) * kEnumBlock] = c;
+                }
             }
             int4 tail = __ldg(v + 12);
             S.alpha = tail.x;
@@ -1013,11 +1152,14 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
                        threadIdx.x & 31);
         return;
     }
+    // walk modes 6, 7: each thread's suffix constants, a column of 12 int4
+    __shared__ int4 s_sfx[mode_smem_sfx(MODE) ? 12 * kEnumBlock : 1];
+    int4* const sq = mode_smem_sfx(MODE) ? s_sfx + threadIdx.x : s_sfx;
     if (!next) {   // static split: one range per thread
         const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         uint64_t x0, x1;
         static_range(t, per_thread, split_c, split_warps, split_hi, split_klo, &x0, &x1);
-        enum_range<PDMAX, MODE>(gp, info, tbl, sub, G, x0, x1, item_cost, sink);
+        enum_range<PDMAX, MODE>(gp, info, tbl, sub, G, x0, x1, item_cost, sink, sq);
         return;
     }
     // dynamic: each warp takes 32 consecutive chunks at a time, one per lane
@@ -1029,7 +1171,7 @@ enum_kernel(const GroupPlan* __restrict__ gp, const GroupInfo* __restrict__ info
         if (c0 >= nchunks) break;
         const uint64_t c = (uint64_t)c0 + lane;
         enum_range<PDMAX, MODE>(gp, info, tbl, sub, G, c * per_thread, (c + 1) * per_thread, item_cost,
-                          sink);
+                                sink, sq);
         __syncwarp();
     }
 }
@@ -1097,6 +1239,8 @@ cudaError_t enum_occupancy_mode(int mode, int* per_sm)
     case 3: return enum_occupancy<PDMAX, 3>(per_sm);
     case 4: return enum_occupancy<PDMAX, 4>(per_sm);
     case 5: return enum_occupancy<PDMAX, 5>(per_sm);
+    case 6: return enum_occupancy<PDMAX, 6>(per_sm);
+    case 7: return enum_occupancy<PDMAX, 7>(per_sm);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1111,6 +1255,8 @@ cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, const PrepArgs& he
     case 3: return launch_enum<PDMAX, 3>(p, sink, heur, stream, pdl);
     case 4: return launch_enum<PDMAX, 4>(p, sink, heur, stream, pdl);
     case 5: return launch_enum<PDMAX, 5>(p, sink, heur, stream, pdl);
+    case 6: return launch_enum<PDMAX, 6>(p, sink, heur, stream, pdl);
+    case 7: return launch_enum<PDMAX, 7>(p, sink, heur, stream, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1124,7 +1270,9 @@ cudaError_t preload_modes()
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 2>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 3>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 4>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 5>);
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 5>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 6>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 7>);
 }
 
 int resident_threads(int pdmax, int mode, int device, int blocks_per_sm)
