@@ -103,7 +103,7 @@ def method_ops_per_order(n: int) -> float:
 
 
 def dominance_ops_per_order(n: int, full: float) -> float:
-    """Integer operations per order of walk modes 5 to 7 (tm_tuning.unroll), where
+    """Integer operations per order of walk modes 5 to 8 (tm_tuning.unroll), where
     a fraction `full` of the prefixes had their 24 orders evaluated one by one
     (tm_plan_walk_counts) and the others took the closed forms.
 
@@ -140,7 +140,7 @@ def workload(rank: int = 0, name: str = "dkdt64x10"):
 
 def ops_per_order(b, full=None) -> float:
     """method_ops_per_order weighted by each group's orders (groups n >= 4);
-    with `full` (walk modes 5 to 7: the fraction of prefixes evaluated order by
+    with `full` (walk modes 5 to 8: the fraction of prefixes evaluated order by
     order, over the whole batch), dominance_ops_per_order instead."""
     f = (lambda n: method_ops_per_order(n)) if full is None else \
         (lambda n: dominance_ops_per_order(n, full))
@@ -150,7 +150,7 @@ def ops_per_order(b, full=None) -> float:
 
 def walk_basis(plan, tuning) -> tuple:
     """(fraction of prefixes evaluated order by order in the plan's last run,
-    or None outside walk modes 5 to 7; a one-line statement of the count's basis)."""
+    or None outside walk modes 5 to 8; a one-line statement of the count's basis)."""
     mode = int(tuning.get("unroll", 0))
     if mode < 5:
         return None, "max-plus suffix decomposition (see method_ops_per_order)"

@@ -189,9 +189,10 @@ int tm_plan_create(const int32_t* h_offsets, int G, tm_plan** plan_out);
  *                  shared memory (24 KB per block) instead of registers,
  *                  compiled for four resident blocks per SM; 7: as 6, with
  *                  the dominance vote and the closed forms of a level's
- *                  six prefixes in one pass (faster on batches of 10-task
- *                  groups, slower on 12-task and mixed ones);
- *                  0: default 2 */
+ *                  six prefixes in one pass and less unrolled code (faster
+ *                  on batches of 10-task groups, slower on 12-task ones);
+ *                  8: as 6 with 7's less unrolled code (faster on batches
+ *                  that mix group sizes); 0: default 2 */
 typedef struct tm_tuning {
     int32_t pdmax;
     int32_t fuse_finalize;
@@ -274,9 +275,9 @@ int tm_plan_set_timing(tm_plan* plan, void* event_before, void* event_after);
  * the 24 orders of the other four; Sec. 1's brute force over every order).
  * *prefixes: the prefixes one run walks, n! / 24 per group of n >= 4 tasks.
  * *full: how many of them had their 24 completions evaluated one by one;
- * under walk modes 5 to 7 (tm_tuning.unroll) the others took the closed
+ * under walk modes 5 to 8 (tm_tuning.unroll) the others took the closed
  * form of their minimum, maximum and sum; every other mode evaluates all of
- * them, and *full = *prefixes without a device read.  Modes 5 to 7 read a counter in
+ * them, and *full = *prefixes without a device read.  Modes 5 to 8 read a counter in
  * the plan's device memory (a synchronous copy): call it once the run has
  * finished (its stream synchronized).  Returns TM_OK, TM_EINVAL (a NULL
  * argument) or TM_ECUDA. */

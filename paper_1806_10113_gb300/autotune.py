@@ -27,7 +27,7 @@ CANDIDATES = {
     "blocks_per_sm": (0, 3),
     "item_cost": (4096, 16384, 65536),
     "chunks_per_thread": (1, 3, 6, 12),
-    "unroll": (1, 2, 3, 4, 5, 6, 7),
+    "unroll": (1, 2, 3, 4, 5, 6, 7, 8),
 }
 _lock = threading.Lock()
 

@@ -199,7 +199,7 @@ bool tuning_invalid(const tm_tuning& t)
     return (t.pdmax != 0 && (t.pdmax < 3 || t.pdmax > 5)) || t.fuse_finalize < 0 ||
            t.fuse_finalize > 2 || t.blocks_per_sm < 0 || t.item_cost < 0 ||
            t.item_cost > (1 << 20) || t.chunks_per_thread < 0 || t.chunks_per_thread > 64 ||
-           (t.fuse_finalize == 1 && t.chunks_per_thread > 1) || t.unroll < 0 || t.unroll > 7;
+           (t.fuse_finalize == 1 && t.chunks_per_thread > 1) || t.unroll < 0 || t.unroll > 8;
 }
 
 void free_plan(Plan& p)

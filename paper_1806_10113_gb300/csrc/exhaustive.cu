@@ -254,6 +254,10 @@ __device__ __noinline__ void finalize_group(int g, const GroupInfo& gi, const in
 // it, one warp per group.
 constexpr int kPrepMaxThreads = 512;
 
+}  // namespace
+
+// PrepArgs and Sink have external linkage: exhaustive_wide.cu's launchers
+// take them (both translation units compile this file).
 struct PrepArgs {
     const tm_task* tasks;
     const tm_device* devs;
@@ -269,6 +273,8 @@ struct PrepArgs {
     uint32_t* next;               // dynamic chunk counter to zero, or null
     unsigned long long* full;     // Plan::d_full, to zero (or null)
 };
+
+namespace {
 
 // Validation, GroupInfo, padded task table (and n <= 3 groups finished
 // outright) for the group at work position w, by one full warp: lane i
@@ -453,6 +459,8 @@ __device__ __forceinline__ unsigned long long worst_key(const Acc& a)
 
 // Where the enumeration threads report.  With done != null each group is
 // finalized by its last finishing thread.
+}  // namespace
+
 struct Sink {
     unsigned long long* acc;
     const GroupInfo* info;
@@ -462,8 +470,10 @@ struct Sink {
     const uint32_t* target;
     uint32_t* done;
     uint32_t one;   // always 1 (the leaves' multiply-add sum)
-    unsigned long long* full;   // Plan::d_full (walk mode 5), or null
+    unsigned long long* full;   // Plan::d_full (walk modes 5 to 8), or null
 };
+
+namespace {
 
 __device__ __forceinline__ void flush(const Acc& a, unsigned long long* acc, int g)
 {
@@ -586,7 +596,8 @@ __device__ __forceinline__ int first_completion(int32_t k, int32_t d, int32_t v,
 // as 5, with S's beta and gamma in shared memory instead of 48 registers,
 // the six prefixes of the straight-line level evaluated quad by quad of S's
 // orders (leaves6), compiled for four resident blocks per SM; 7 as 6, with
-// the six prefixes' vote and closed forms in one pass.
+// the six prefixes' vote and closed forms in one pass and leaves6's quads
+// as a loop (less hot code); 8 as 6 with that loop.
 __host__ __device__ constexpr bool mode_straight(int mode) { return mode != 2; }
 __host__ __device__ constexpr bool mode_fma_add(int mode) { return mode >= 3; }
 __host__ __device__ constexpr int mode_min_blocks(int mode)
@@ -596,6 +607,9 @@ __host__ __device__ constexpr int mode_min_blocks(int mode)
 __host__ __device__ constexpr bool mode_dominance(int mode) { return mode >= 5; }
 __host__ __device__ constexpr bool mode_smem_sfx(int mode) { return mode >= 6; }
 __host__ __device__ constexpr bool mode_one_pass(int mode) { return mode == 7; }
+__host__ __device__ constexpr bool mode_rolled(int mode) { return mode == 7 || mode == 8; }
+static_assert(mode_smem_sfx(8) && mode_rolled(8) && !mode_one_pass(8) && !mode_rolled(6),
+              "walk mode 8: mode 6 with the rolled quad loop");
 
 // One engine's path ends all 24 orders of S after a prefix with engine
 // times (k, d) in three cases, each with a closed form for the minimum, the
@@ -717,7 +731,7 @@ __device__ __forceinline__ void last_two(Eng st, int4 x, int4 y, const Sfx& S, A
 // order), quad by quad of S's orders, so that each int4 of beta and gamma is
 // read from shared memory once for the six.  Each prefix keeps its own
 // minimum and (SUM32) its own 32-bit sum, which fits as in leaves.
-template <bool SUM32>
+template <bool SUM32, bool ROLLED>
 __device__ __forceinline__ void leaves6(const Eng (&e)[6], const Sfx& S, Acc& a)
 {
     int32_t c0[6], mn[6];
@@ -729,7 +743,11 @@ __device__ __forceinline__ void leaves6(const Eng (&e)[6], const Sfx& S, Acc& a)
         sm[i] = 0u;
     }
     unsigned long long wide = 0;
-#pragma unroll
+    // ROLLED: a loop over the quads (the six prefixes' work per quad is
+    // straight-line already, and the loop keeps the hot code small, which
+    // pays on batches of many group sizes); else unrolled
+    constexpr int kQuadUnroll = ROLLED ? 1 : 6;
+#pragma unroll kQuadUnroll
     for (int r = 0; r < 6; ++r) {
         const int4 bq = S.sq[r * kEnumBlock], cq = S.sq[(6 + r) * kEnumBlock];
 #pragma unroll
@@ -836,7 +854,7 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
             a.walked += 6;
         } else {
             a.full += 6;
-            leaves6<SUM32>(e, S, a);
+            leaves6<SUM32, mode_rolled(MODE)>(e, S, a);
         }
     } else if constexpr (D == 3 && mode_dominance(MODE)) {
         // as below, with one dominance vote for all six prefixes: either all
@@ -886,7 +904,7 @@ __device__ __forceinline__ void dfs(Eng st, uint64_t rem, const int4* __restrict
         } else {
             a.full += 6;
             if constexpr (mode_smem_sfx(MODE)) {
-                leaves6<SUM32>(e, S, a);
+                leaves6<SUM32, mode_rolled(MODE)>(e, S, a);
             } else {
 #pragma unroll
                 for (int i = 0; i < 6; ++i) leaves<SUM32, MODE, false>(e[i].k, e[i].d, S, a);
@@ -1190,6 +1208,19 @@ __global__ void finalize_kernel(PrepArgs a, unsigned long long* __restrict__ acc
     if (gi.status == 0 && gi.n >= 4) finalize_group_warp(g, gi, a.tbl, acc, a.stats, a.status);
 }
 
+}  // namespace
+
+// Walk modes 6 to 8 of the enumeration kernel, compiled in their own
+// translation unit (exhaustive_wide.cu, this file with TM_ENUM_WIDE_MODES
+// defined) so that the two build in parallel: launch, occupancy (resident
+// blocks per SM), and module load for pdmax 3..5.
+cudaError_t enum_wide_launch(int pdmax, int mode, const Plan& p, const Sink& sink,
+                             const PrepArgs& heur, cudaStream_t stream, bool pdl);
+cudaError_t enum_wide_occupancy(int pdmax, int mode, int* per_sm);
+cudaError_t enum_wide_preload(int pdmax);
+
+namespace {
+
 // A launch configuration, with programmatic dependent launch if pdl.
 struct LaunchCfg {
     cudaLaunchConfig_t cfg{};
@@ -1230,6 +1261,8 @@ cudaError_t enum_occupancy(int* per_sm)
                                                          kEnumBlock, 0);
 }
 
+#ifndef TM_ENUM_WIDE_MODES
+
 template <int PDMAX>
 cudaError_t enum_occupancy_mode(int mode, int* per_sm)
 {
@@ -1239,8 +1272,7 @@ cudaError_t enum_occupancy_mode(int mode, int* per_sm)
     case 3: return enum_occupancy<PDMAX, 3>(per_sm);
     case 4: return enum_occupancy<PDMAX, 4>(per_sm);
     case 5: return enum_occupancy<PDMAX, 5>(per_sm);
-    case 6: return enum_occupancy<PDMAX, 6>(per_sm);
-    case 7: return enum_occupancy<PDMAX, 7>(per_sm);
+    case 6: case 7: case 8: return enum_wide_occupancy(PDMAX, mode, per_sm);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1255,8 +1287,7 @@ cudaError_t launch_enum_mode(const Plan& p, const Sink& sink, const PrepArgs& he
     case 3: return launch_enum<PDMAX, 3>(p, sink, heur, stream, pdl);
     case 4: return launch_enum<PDMAX, 4>(p, sink, heur, stream, pdl);
     case 5: return launch_enum<PDMAX, 5>(p, sink, heur, stream, pdl);
-    case 6: return launch_enum<PDMAX, 6>(p, sink, heur, stream, pdl);
-    case 7: return launch_enum<PDMAX, 7>(p, sink, heur, stream, pdl);
+    case 6: case 7: case 8: return enum_wide_launch(PDMAX, p.unroll, p, sink, heur, stream, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1271,8 +1302,7 @@ cudaError_t preload_modes()
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 3>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 4>)) != cudaSuccess) return e;
     if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 5>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 6>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, enum_kernel<PDMAX, 7>);
+    return enum_wide_preload(PDMAX);
 }
 
 int resident_threads(int pdmax, int mode, int device, int blocks_per_sm)
@@ -1415,5 +1445,54 @@ cudaError_t launch_exhaustive(const Plan& p, const tm_task* d_tasks, const tm_de
     }
     return e;
 }
+
+#else   // TM_ENUM_WIDE_MODES: the launchers of walk modes 6 to 8
+
+}  // namespace
+
+cudaError_t enum_wide_launch(int pdmax, int mode, const Plan& p, const Sink& sink,
+                             const PrepArgs& heur, cudaStream_t stream, bool pdl)
+{
+#define TM_WIDE_CASE(PD, M) \
+    case (PD) * 16 + (M): return launch_enum<PD, M>(p, sink, heur, stream, pdl);
+    switch (pdmax * 16 + mode) {
+    TM_WIDE_CASE(3, 6) TM_WIDE_CASE(3, 7) TM_WIDE_CASE(3, 8)
+    TM_WIDE_CASE(4, 6) TM_WIDE_CASE(4, 7) TM_WIDE_CASE(4, 8)
+    TM_WIDE_CASE(5, 6) TM_WIDE_CASE(5, 7) TM_WIDE_CASE(5, 8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef TM_WIDE_CASE
+}
+
+cudaError_t enum_wide_occupancy(int pdmax, int mode, int* per_sm)
+{
+#define TM_WIDE_CASE(PD, M) \
+    case (PD) * 16 + (M): return enum_occupancy<PD, M>(per_sm);
+    switch (pdmax * 16 + mode) {
+    TM_WIDE_CASE(3, 6) TM_WIDE_CASE(3, 7) TM_WIDE_CASE(3, 8)
+    TM_WIDE_CASE(4, 6) TM_WIDE_CASE(4, 7) TM_WIDE_CASE(4, 8)
+    TM_WIDE_CASE(5, 6) TM_WIDE_CASE(5, 7) TM_WIDE_CASE(5, 8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef TM_WIDE_CASE
+}
+
+cudaError_t enum_wide_preload(int pdmax)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    switch (pdmax) {
+#define TM_WIDE_LOAD(PD)                                                                    \
+    case PD:                                                                                \
+        if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PD, 6>)) != cudaSuccess) return e; \
+        if ((e = cudaFuncGetAttributes(&fa, enum_kernel<PD, 7>)) != cudaSuccess) return e; \
+        return cudaFuncGetAttributes(&fa, enum_kernel<PD, 8>);
+    TM_WIDE_LOAD(3) TM_WIDE_LOAD(4) TM_WIDE_LOAD(5)
+#undef TM_WIDE_LOAD
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+#endif  // TM_ENUM_WIDE_MODES
 
 }  // namespace tmgpu

@@ -320,7 +320,8 @@ class Tuning(ctypes.Structure):
     additions on the FMA pipe, 4 as 3 at four blocks per SM, 5 as 3 with the closed
     form for prefixes whose completions one engine's path ends, 6 as 5 with the
     suffix constants in shared memory at four blocks per SM, 7 as 6 with the vote and
-    the closed forms in one pass); 0 = default."""
+    the closed forms in one pass and a rolled quad loop, 8 as 6 with that loop);
+    0 = default."""
     _fields_ = [("pdmax", ctypes.c_int32), ("fuse_finalize", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("item_cost", ctypes.c_int32),
                 ("chunks_per_thread", ctypes.c_int32), ("unroll", ctypes.c_int32)]

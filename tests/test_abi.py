@@ -119,7 +119,7 @@ def test_tuning_layout_and_rejection_on_host(tm):
     import ctypes
     assert ctypes.sizeof(tm.Tuning) == 24
     for kw in ({"pdmax": 6}, {"pdmax": 2}, {"fuse_finalize": 3}, {"chunks_per_thread": 65},
-               {"fuse_finalize": 1, "chunks_per_thread": 2}, {"unroll": 8}, {"unroll": -1},
+               {"fuse_finalize": 1, "chunks_per_thread": 2}, {"unroll": 9}, {"unroll": -1},
                {"item_cost": (1 << 20) + 1}):
         with pytest.raises(tm.TMError) as e:
             tm.tm_set_default_tuning(**kw)

@@ -201,10 +201,10 @@ def test_exhaustive_full_size_sixty_four_groups(tm):
     ("big_uniform", dict(pdmax=4, fuse_finalize=2, unroll=5)),
 ])
 def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
-    """Walk modes 5 to 7 (closed forms for prefixes whose completions one
+    """Walk modes 5 to 8 (closed forms for prefixes whose completions one
     engine's path ends; 6 with the suffix constants in shared memory and the
     six prefixes of a straight-line level evaluated together; 7 with their
-    vote and closed forms in one pass) against the
+    vote and closed forms in one pass; 7 and 8 with a rolled loop) against the
     oracle's full enumeration, whatever the tuner picks elsewhere: the
     benchmark's 64 x 10 workload (all 128 x 10! orders), 2048 ragged groups,
     and tie-heavy groups (durations 0..3, where every closed form meets equal
@@ -223,7 +223,7 @@ def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
         b = inputs.random_groups(28, [9] * 6, hi=60_000_000)
     ref = oracle.exhaustive_batch(b.tasks, b.offsets, b.dma)
     ref_orders, ref_ms = oracle.heuristic_batch(b.tasks, b.offsets, b.dma)
-    for mode in (5, 6, 7):
+    for mode in (5, 6, 7, 8):
         t = dict(tuning, unroll=mode)
         stats, orders, hms, _ = scheduled_as_benched(tm, b, t)
         for g in range(b.G):
@@ -233,7 +233,7 @@ def test_dominance_walk_mode_full_oracle(tm, workload, tuning):
 
 def test_walk_counts(tm):
     """tm_plan_walk_counts: n!/24 prefixes per group; every prefix evaluated
-    order by order outside walk modes 5 to 7; under them, some (the benchmark's
+    order by order outside walk modes 5 to 8; under them, some (the benchmark's
     dominant-transfer groups under two DMA engines mix the engines' paths)
     but not all; and none where the DtH engine's path ends every order."""
     import torch
@@ -256,11 +256,11 @@ def test_walk_counts(tm):
     pre5, full5 = run(b, 5)
     assert pre3 == pre5 == 128 * math.factorial(10) // 24 and full3 == pre3
     assert 0 < full5 < pre5
-    for mode in (6, 7):
+    for mode in (6, 7, 8):
         pre6, full6 = run(b, mode)
         assert pre6 == pre5 and 0 < full6 < pre6
     dth = inputs.make_batch([[[1, 1, 1_000_000]] * 8] * 6, [2, 1] * 3)
-    for mode in (5, 6, 7):
+    for mode in (5, 6, 7, 8):
         pre, full = run(dth, mode)
         assert pre == 6 * math.factorial(8) // 24 and full == 0
 
@@ -479,7 +479,9 @@ def test_schedule_batch_dev_reports_invalid_groups(tm):
                                     dict(pdmax=4, unroll=6, chunks_per_thread=3),
                                     dict(pdmax=5, unroll=6, item_cost=1, blocks_per_sm=1),
                                     dict(pdmax=5, unroll=7), dict(pdmax=3, unroll=7),
-                                    dict(pdmax=4, unroll=7, chunks_per_thread=3)])
+                                    dict(pdmax=4, unroll=7, chunks_per_thread=3),
+                                    dict(pdmax=5, unroll=8), dict(pdmax=3, unroll=8),
+                                    dict(pdmax=4, unroll=8, chunks_per_thread=3)])
 def test_every_tuning_gives_identical_results(tm, tuning):
     """Work split, prefix depth and finalize placement change no result."""
     import torch
