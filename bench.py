@@ -272,10 +272,16 @@ def bus_id_of(device_index: int) -> str | None:
 # ---- roofline inputs from the committed ncu summary --------------------------------
 
 def kernel_source_hash() -> str:
+    """Hash of the enumeration kernel's sources with comments and blank lines
+    left out, so that a comment edit keeps the profiled traffic valid."""
     h = hashlib.sha256()
     for f in ("exhaustive.cu", "tm_device.cuh", "tm_internal.h"):
-        with open(os.path.join(ROOT, "paper_1806_10113_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1806_10113_gb300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -429,8 +429,8 @@ struct Acc {
     // keep the lowest-rank occurrence.
     int32_t imin, imax;
     uint32_t imin_at, imax_at, walked;
-    // Walk mode 5: prefixes of the thread's whole range evaluated order by
-    // order (not reset per group).
+    // Walk modes 5 to 8: prefixes of the thread's whole range evaluated
+    // order by order (not reset per group).
     uint32_t full;
     __device__ __forceinline__ void reset()
     {
@@ -541,7 +541,7 @@ __device__ __forceinline__ void flush_final(Acc& a, const Sink& k, int g)
 
 // Suffix constants of the current S, in registers.  The extremes, the
 // bounds of gamma - beta and the 32-bit sums serve the dominance test of
-// walk mode 5 (dominated()).
+// walk modes 5 to 8 (dominated()).
 struct Sfx {
     int32_t b[24], c[24];
     int32_t alpha, bmax, cmax;
@@ -655,7 +655,7 @@ __device__ __forceinline__ void note_prefix(int32_t pmin, int32_t pmax, Acc& a)
     a.walked += 1;
 }
 
-// CHECK (walk mode 5): take the closed form when dominated() holds on every
+// CHECK (walk modes 5 to 8): take the closed form when dominated() holds on every
 // active lane of the warp, so that the warp's lanes stay on one path.
 template <bool SUM32, int MODE, bool CHECK = mode_dominance(MODE)>
 __device__ __forceinline__ void leaves(int32_t k, int32_t d, const Sfx& S, Acc& a)

@@ -124,7 +124,7 @@ struct Plan {
     uint32_t* d_done = nullptr;           // [kDoneStride G]
     uint32_t* d_next = nullptr;           // dynamic chunk counter
     // Prefixes of the last run whose 24 completions were evaluated order by
-    // order (walk mode 5 counts them; the others evaluate every prefix so);
+    // order (walk modes 5 to 8 count them; the others evaluate every prefix so);
     // zeroed by the prep kernel; in d_next's 256-byte piece.
     unsigned long long* d_full = nullptr;
     cudaEvent_t ev_before = nullptr;      // optional timing hook
